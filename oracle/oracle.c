@@ -1,0 +1,434 @@
+/*
+ * Plain, slow, obviously-correct CPU oracle for sparse matrix-vector
+ * multiplication in CRS and JDS storage (Schubert, Hager & Fehske,
+ * "Performance limitations for sparse matrix-vector multiplications on
+ * current multicore environments", Sect. 2).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes
+ * or calls this file; only the test-suite, the smoke check and the CPU
+ * baseline of the benchmark do.  It shares no code, header or constant with
+ * the CUDA path.
+ *
+ * Conventions: 0-based int32 indices, FP64 values, sequential loops in the
+ * order the paper writes them.  Build with -ffp-contract=off so that every
+ * "a + b*c" is a rounded multiply followed by a rounded add, exactly as the
+ * listings read.  fma() appears only where an exact product split is wanted
+ * (the accurate reference), never as contraction.
+ *
+ * Readings of points the paper leaves open:
+ *   - resvec starts from zero unless `accumulate` is set (the listings only
+ *     show the update "resvec = resvec + ...").
+ *   - The JDS row sort is stable: equal row lengths keep ascending original
+ *     row order; empty rows end up last.
+ *   - Entries keep their CRS storage order inside a row when shifted left
+ *     (slot d of a row is its d-th stored entry).
+ *   - Blocks for NBJDS / RBJDS / SOJDS are runs of b consecutive permuted
+ *     rows, the last one partial; RBJDS stores a block diagonal by diagonal.
+ *   - NUJDS with N_j not a multiple of u: the last group has fewer diagonals.
+ *   - SOJDS: greedy nearest-column rule, see orc_sojds_build.  The paper fixes
+ *     no rule (its storage figure is not available): parity unpinned.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define DIAGLEN(jd, d) ((int64_t)(jd)[(d) + 1] - (int64_t)(jd)[(d)])
+
+/* ------------------------------------------------------------------------
+ * CRS  (Sect. 2, CRS kernel: for each row i, for j in row i,
+ *       resvec(i) = resvec(i) + val(j) * invec(col_idx(j)))
+ * ---------------------------------------------------------------------- */
+void orc_crs_spmv(int64_t n_rows, const int32_t *row_ptr, const int32_t *col_idx,
+                  const double *val, const double *invec, double *resvec, int accumulate)
+{
+    for (int64_t i = 0; i < n_rows; ++i) {
+        double r = accumulate ? resvec[i] : 0.0;
+        for (int64_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j)
+            r = r + val[j] * invec[col_idx[j]];
+        resvec[i] = r;
+    }
+}
+
+/* The same loop in single precision (values, vector and sum all float). */
+void orc_crs_spmv_f32(int64_t n_rows, const int32_t *row_ptr, const int32_t *col_idx,
+                      const float *val, const float *invec, float *resvec, int accumulate)
+{
+    for (int64_t i = 0; i < n_rows; ++i) {
+        float r = accumulate ? resvec[i] : 0.0f;
+        for (int64_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j)
+            r = r + val[j] * invec[col_idx[j]];
+        resvec[i] = r;
+    }
+}
+
+/* Sect. 4: the paper's best shared-memory setting is the CRS loop with an
+ * OpenMP static schedule over rows (first-touch placed arrays).  Same
+ * per-row arithmetic as orc_crs_spmv, so the results are bit-identical. */
+void orc_crs_spmv_omp(int64_t n_rows, const int32_t *row_ptr, const int32_t *col_idx,
+                      const double *val, const double *invec, double *resvec, int accumulate)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n_rows; ++i) {
+        double r = accumulate ? resvec[i] : 0.0;
+        for (int64_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j)
+            r = r + val[j] * invec[col_idx[j]];
+        resvec[i] = r;
+    }
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Multiple right-hand sides: X and Y row-major (n x k, leading dims ldx, ldy);
+ * column c of Y is the CRS loop applied to column c of X. */
+void orc_crs_spmm(int64_t n_rows, const int32_t *row_ptr, const int32_t *col_idx,
+                  const double *val, int64_t k, const double *X, int64_t ldx,
+                  double *Y, int64_t ldy, int accumulate)
+{
+    for (int64_t i = 0; i < n_rows; ++i)
+        for (int64_t c = 0; c < k; ++c) {
+            double r = accumulate ? Y[i * ldy + c] : 0.0;
+            for (int64_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j)
+                r = r + val[j] * X[(int64_t)col_idx[j] * ldx + c];
+            Y[i * ldy + c] = r;
+        }
+}
+
+/* ------------------------------------------------------------------------
+ * Accurate reference for y = A x (and y += A x): each product is split
+ * exactly, p + e = a*x with e = fma(a, x, -p), and all terms are summed in
+ * double-double with Knuth's TwoSum -- the "Dot2" scheme of Ogita, Rump &
+ * Oishi (SIAM J. Sci. Comput. 26, 2005).  Its error is at most
+ * u|y| + gamma_n^2 sum|a||x| (u = 2^-53), i.e. essentially correctly
+ * rounded.  absrow[i] = sum_j |a_ij||x_j| feeds the test tolerance.
+ * ---------------------------------------------------------------------- */
+static inline void two_sum(double a, double b, double *s, double *e)
+{
+    double t = a + b;
+    double z = t - a;
+    *e = (a - (t - z)) + (b - z);
+    *s = t;
+}
+
+void orc_crs_spmv_exact(int64_t n_rows, const int32_t *row_ptr, const int32_t *col_idx,
+                        const double *val, const double *invec, double *resvec,
+                        double *absrow, int accumulate)
+{
+    for (int64_t i = 0; i < n_rows; ++i) {
+        double s = accumulate ? resvec[i] : 0.0, c = 0.0;
+        double a = accumulate ? fabs(resvec[i]) : 0.0;
+        for (int64_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) {
+            double p = val[j] * invec[col_idx[j]];
+            double e = fma(val[j], invec[col_idx[j]], -p);
+            double err;
+            two_sum(s, p, &s, &err);
+            c = c + (err + e);
+            a = a + fabs(val[j]) * fabs(invec[col_idx[j]]);
+        }
+        resvec[i] = s + c;
+        if (absrow) absrow[i] = a;
+    }
+}
+
+/* Accurate A^T g: per output column the same Dot2 accumulation, with the
+ * terms visited in CRS storage order. */
+void orc_crs_spmv_t_exact(int64_t n_rows, int64_t n_cols, const int32_t *row_ptr,
+                          const int32_t *col_idx, const double *val, const double *g,
+                          double *out, double *abscol)
+{
+    double *c = (double *)calloc((size_t)(n_cols > 0 ? n_cols : 1), sizeof(double));
+    for (int64_t j = 0; j < n_cols; ++j) { out[j] = 0.0; if (abscol) abscol[j] = 0.0; }
+    for (int64_t i = 0; i < n_rows; ++i)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            int64_t j = col_idx[k];
+            double p = val[k] * g[i];
+            double e = fma(val[k], g[i], -p);
+            double err;
+            two_sum(out[j], p, &out[j], &err);
+            c[j] = c[j] + (err + e);
+            if (abscol) abscol[j] = abscol[j] + fabs(val[k]) * fabs(g[i]);
+        }
+    for (int64_t j = 0; j < n_cols; ++j) out[j] = out[j] + c[j];
+    free(c);
+}
+
+/* ------------------------------------------------------------------------
+ * Adjoint and value gradient (the transpose of the CRS sum).
+ * ---------------------------------------------------------------------- */
+
+/* dx = A^T g by a serial scatter over the stored entries. */
+void orc_crs_spmv_t(int64_t n_rows, int64_t n_cols, const int32_t *row_ptr,
+                    const int32_t *col_idx, const double *val, const double *g,
+                    double *dx, int accumulate)
+{
+    if (!accumulate)
+        for (int64_t j = 0; j < n_cols; ++j) dx[j] = 0.0;
+    for (int64_t i = 0; i < n_rows; ++i)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+            dx[col_idx[k]] = dx[col_idx[k]] + val[k] * g[i];
+}
+
+/* dval_k = g[row_k] * x[col_k] for every stored entry k (CRS order):
+ * the derivative of g . (A x) with respect to val_k. */
+void orc_dval(int64_t n_rows, const int32_t *row_ptr, const int32_t *col_idx,
+              const double *g, const double *x, double *dval, int accumulate)
+{
+    for (int64_t i = 0; i < n_rows; ++i)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            double d = g[i] * x[col_idx[k]];
+            dval[k] = accumulate ? dval[k] + d : d;
+        }
+}
+
+/* ------------------------------------------------------------------------
+ * JDS construction (Sect. 2): permute rows (and, in symmetric mode, columns)
+ * so that row length decreases with row index, shift every row's entries to
+ * the left and store the resulting jagged diagonals one after another.
+ *
+ *   (i)   len_i = row_ptr[i+1] - row_ptr[i]
+ *   (ii)  stable sort by decreasing length: perm[new] = old, iperm[old] = new
+ *   (iii) N_j = max len; diagonal d holds the rows with len > d, so
+ *         jd_ptr[d+1] - jd_ptr[d] = #{i : len_i > d}
+ *   (iv)  val_jds[jd_ptr[d] + r] = val[row_ptr[perm[r]] + d]
+ *   (v)   col_jds = iperm[col] (symmetric: A_{p(i),p(j)}) or col (row-only)
+ *
+ * jd_ptr must hold max_len+1 entries.  Returns N_j, or -1 when symmetric
+ * mode is asked for a non-square matrix.
+ * ---------------------------------------------------------------------- */
+int64_t orc_max_row_len(int64_t n_rows, const int32_t *row_ptr)
+{
+    int64_t m = 0;
+    for (int64_t i = 0; i < n_rows; ++i) {
+        int64_t l = (int64_t)row_ptr[i + 1] - row_ptr[i];
+        if (l > m) m = l;
+    }
+    return m;
+}
+
+int64_t orc_jds_build(int64_t n_rows, int64_t n_cols, const int32_t *row_ptr,
+                      const int32_t *col_idx, const double *val, int symmetric,
+                      int32_t *perm, int32_t *iperm, int32_t *jd_ptr,
+                      int32_t *col_jds, double *val_jds)
+{
+    if (symmetric && n_rows != n_cols) return -1;
+    int64_t nj = orc_max_row_len(n_rows, row_ptr);
+
+    /* (ii) counting sort on length, longest first, ties in row order */
+    int64_t *count = (int64_t *)calloc((size_t)(nj + 2), sizeof(int64_t));
+    int64_t *start = (int64_t *)calloc((size_t)(nj + 2), sizeof(int64_t));
+    for (int64_t i = 0; i < n_rows; ++i) count[row_ptr[i + 1] - row_ptr[i]]++;
+    int64_t pos = 0;
+    for (int64_t l = nj; l >= 0; --l) { start[l] = pos; pos += count[l]; }
+    for (int64_t i = 0; i < n_rows; ++i) {
+        int64_t l = (int64_t)row_ptr[i + 1] - row_ptr[i];
+        perm[start[l]++] = (int32_t)i;
+    }
+    for (int64_t r = 0; r < n_rows; ++r) iperm[perm[r]] = (int32_t)r;
+
+    /* (iii) diagonal d has #{len > d} entries */
+    jd_ptr[0] = 0;
+    for (int64_t d = 0; d < nj; ++d) {
+        int64_t rows_longer = 0;
+        for (int64_t l = d + 1; l <= nj; ++l) rows_longer += count[l];
+        jd_ptr[d + 1] = (int32_t)(jd_ptr[d] + rows_longer);
+    }
+
+    /* (iv), (v) shift left and store diagonal after diagonal */
+    for (int64_t d = 0; d < nj; ++d)
+        for (int64_t r = 0; r < DIAGLEN(jd_ptr, d); ++r) {
+            int64_t src = (int64_t)row_ptr[perm[r]] + d;
+            val_jds[jd_ptr[d] + r] = val[src];
+            col_jds[jd_ptr[d] + r] = symmetric ? iperm[col_idx[src]] : col_idx[src];
+        }
+    free(count);
+    free(start);
+    return nj;
+}
+
+/* JDS kernel (Sect. 2, JDS listing): diagonal after diagonal, every row of
+ * the diagonal updated, resvec making one round trip per diagonal. */
+void orc_jds_spmv(int64_t n_rows, int64_t n_diag, const int32_t *jd_ptr,
+                  const int32_t *col_jds, const double *val_jds, const double *invec,
+                  double *resvec, int accumulate)
+{
+    if (!accumulate)
+        for (int64_t i = 0; i < n_rows; ++i) resvec[i] = 0.0;
+    for (int64_t d = 0; d < n_diag; ++d) {
+        int64_t len = DIAGLEN(jd_ptr, d), off = jd_ptr[d];
+        for (int64_t i = 0; i < len; ++i)
+            resvec[i] = resvec[i] + val_jds[off + i] * invec[col_jds[off + i]];
+    }
+}
+
+/* NBJDS (Sect. 2, standard blocking): the diagonals are cut into blocks of
+ * `block` rows; one block of resvec is finished for every diagonal that has
+ * entries in it before moving on, skipping through val / col_idx. */
+void orc_nbjds_spmv(int64_t n_rows, int64_t n_diag, const int32_t *jd_ptr,
+                    const int32_t *col_jds, const double *val_jds, int64_t block,
+                    const double *invec, double *resvec, int accumulate)
+{
+    if (!accumulate)
+        for (int64_t i = 0; i < n_rows; ++i) resvec[i] = 0.0;
+    for (int64_t b0 = 0; b0 < n_rows; b0 += block) {
+        int64_t b1 = b0 + block < n_rows ? b0 + block : n_rows;
+        for (int64_t d = 0; d < n_diag && DIAGLEN(jd_ptr, d) > b0; ++d) {
+            int64_t end = DIAGLEN(jd_ptr, d) < b1 ? DIAGLEN(jd_ptr, d) : b1;
+            for (int64_t i = b0; i < end; ++i)
+                resvec[i] = resvec[i] + val_jds[jd_ptr[d] + i] * invec[col_jds[jd_ptr[d] + i]];
+        }
+    }
+}
+
+/* NUJDS (Sect. 2, outer-loop unrolling): every resvec element is updated by
+ * u diagonals at once.  The last group holds the N_j mod u remaining ones. */
+void orc_nujds_spmv(int64_t n_rows, int64_t n_diag, const int32_t *jd_ptr,
+                    const int32_t *col_jds, const double *val_jds, int64_t u,
+                    const double *invec, double *resvec, int accumulate)
+{
+    if (!accumulate)
+        for (int64_t i = 0; i < n_rows; ++i) resvec[i] = 0.0;
+    for (int64_t d0 = 0; d0 < n_diag; d0 += u) {
+        int64_t d1 = d0 + u < n_diag ? d0 + u : n_diag;
+        for (int64_t i = 0; i < DIAGLEN(jd_ptr, d0); ++i) {
+            double t = resvec[i];
+            for (int64_t d = d0; d < d1 && i < DIAGLEN(jd_ptr, d); ++d)
+                t = t + val_jds[jd_ptr[d] + i] * invec[col_jds[jd_ptr[d] + i]];
+            resvec[i] = t;
+        }
+    }
+}
+
+/* RBJDS layout (Sect. 2): the elements of each block of `block` permuted rows
+ * are stored consecutively, diagonal by diagonal inside the block.
+ * blk_ptr[k] is the first element of block k (n_blocks+1 entries). */
+void orc_rbjds_build(int64_t n_rows, int64_t n_diag, const int32_t *jd_ptr,
+                     const int32_t *col_jds, const double *val_jds, int64_t block,
+                     int32_t *blk_ptr, int32_t *col_rb, double *val_rb)
+{
+    int64_t pos = 0, k = 0;
+    for (int64_t b0 = 0; b0 < n_rows; b0 += block, ++k) {
+        int64_t b1 = b0 + block < n_rows ? b0 + block : n_rows;
+        blk_ptr[k] = (int32_t)pos;
+        for (int64_t d = 0; d < n_diag && DIAGLEN(jd_ptr, d) > b0; ++d) {
+            int64_t end = DIAGLEN(jd_ptr, d) < b1 ? DIAGLEN(jd_ptr, d) : b1;
+            for (int64_t i = b0; i < end; ++i, ++pos) {
+                val_rb[pos] = val_jds[jd_ptr[d] + i];
+                col_rb[pos] = col_jds[jd_ptr[d] + i];
+            }
+        }
+    }
+    blk_ptr[k] = (int32_t)pos;
+}
+
+/* RBJDS kernel: one contiguous sweep through each block's elements. */
+void orc_rbjds_spmv(int64_t n_rows, int64_t n_diag, const int32_t *jd_ptr,
+                    const int32_t *blk_ptr, const int32_t *col_rb, const double *val_rb,
+                    int64_t block, const double *invec, double *resvec, int accumulate)
+{
+    if (!accumulate)
+        for (int64_t i = 0; i < n_rows; ++i) resvec[i] = 0.0;
+    int64_t k = 0;
+    for (int64_t b0 = 0; b0 < n_rows; b0 += block, ++k) {
+        int64_t b1 = b0 + block < n_rows ? b0 + block : n_rows;
+        int64_t pos = blk_ptr[k];
+        for (int64_t d = 0; d < n_diag && DIAGLEN(jd_ptr, d) > b0; ++d) {
+            int64_t end = DIAGLEN(jd_ptr, d) < b1 ? DIAGLEN(jd_ptr, d) : b1;
+            for (int64_t i = b0; i < end; ++i, ++pos)
+                resvec[i] = resvec[i] + val_rb[pos] * invec[col_rb[pos]];
+        }
+    }
+}
+
+/* SOJDS (Sect. 2): inside each block the entries of a row are re-ordered so
+ * that down each block column (slot d) invec is read with stride one, or as
+ * close to it as possible.  Rule used here (the paper fixes none):
+ *   - the first row of a block keeps its order;
+ *   - for every later row r, slots d = 0, 1, ... are filled in turn with the
+ *     not yet placed entry of row r whose column c minimises
+ *     |c - (c_prev(d) + 1)|, c_prev(d) being the column now in slot d of row
+ *     r-1; ties go to the smaller column, then to the earlier slot.
+ * Output is in RBJDS layout (same blk_ptr).  Plain O(len^2) search per row. */
+void orc_sojds_build(int64_t n_rows, int64_t n_diag, const int32_t *jd_ptr,
+                     const int32_t *col_jds, const double *val_jds, int64_t block,
+                     int32_t *blk_ptr, int32_t *col_so, double *val_so)
+{
+    /* row length of permuted row r = number of diagonals longer than r */
+    int64_t maxlen = n_diag;
+    int32_t *prev_col = (int32_t *)malloc((size_t)(maxlen > 0 ? maxlen : 1) * sizeof(int32_t));
+    int32_t *cur_col = (int32_t *)malloc((size_t)(maxlen > 0 ? maxlen : 1) * sizeof(int32_t));
+    double *cur_val = (double *)malloc((size_t)(maxlen > 0 ? maxlen : 1) * sizeof(double));
+    char *used = (char *)malloc((size_t)(maxlen > 0 ? maxlen : 1));
+    int64_t pos = 0, k = 0;
+    for (int64_t b0 = 0; b0 < n_rows; b0 += block, ++k) {
+        int64_t b1 = b0 + block < n_rows ? b0 + block : n_rows;
+        blk_ptr[k] = (int32_t)pos;
+        /* block-local element offset of slot d is the count of the block's
+         * entries in diagonals before d */
+        int64_t nslots = 0;
+        while (nslots < n_diag && DIAGLEN(jd_ptr, nslots) > b0) ++nslots;
+        int64_t *slot_off = (int64_t *)malloc((size_t)(nslots + 1) * sizeof(int64_t));
+        slot_off[0] = 0;
+        for (int64_t d = 0; d < nslots; ++d) {
+            int64_t end = DIAGLEN(jd_ptr, d) < b1 ? DIAGLEN(jd_ptr, d) : b1;
+            slot_off[d + 1] = slot_off[d] + (end - b0);
+        }
+        for (int64_t r = b0; r < b1; ++r) {
+            int64_t len = 0;
+            while (len < n_diag && DIAGLEN(jd_ptr, len) > r) ++len;
+            for (int64_t d = 0; d < len; ++d) {
+                cur_col[d] = col_jds[jd_ptr[d] + r];
+                cur_val[d] = val_jds[jd_ptr[d] + r];
+                used[d] = 0;
+            }
+            for (int64_t d = 0; d < len; ++d) {
+                int64_t pick;
+                if (r == b0) {
+                    pick = d;
+                } else {
+                    int64_t target = (int64_t)prev_col[d] + 1;
+                    pick = -1;
+                    for (int64_t e = 0; e < len; ++e) {
+                        if (used[e]) continue;
+                        if (pick < 0) { pick = e; continue; }
+                        int64_t de = llabs((int64_t)cur_col[e] - target);
+                        int64_t dp = llabs((int64_t)cur_col[pick] - target);
+                        if (de < dp || (de == dp && cur_col[e] < cur_col[pick])) pick = e;
+                    }
+                }
+                used[pick] = 1;
+                int64_t dst = pos + slot_off[d] + (r - b0);
+                col_so[dst] = cur_col[pick];
+                val_so[dst] = cur_val[pick];
+                prev_col[d] = cur_col[pick];
+            }
+        }
+        pos += slot_off[nslots];
+        free(slot_off);
+    }
+    blk_ptr[k] = (int32_t)pos;
+    free(prev_col);
+    free(cur_col);
+    free(cur_val);
+    free(used);
+}
+
+/* Vector basis change for the permuted (JDS) basis: out[r] = in[perm[r]]
+ * (to the permuted basis) or out[perm[r]] = in[r] (back). */
+void orc_permute(int64_t n, const int32_t *perm, const double *in, double *out, int to_permuted)
+{
+    for (int64_t r = 0; r < n; ++r) {
+        if (to_permuted) out[r] = in[perm[r]];
+        else out[perm[r]] = in[r];
+    }
+}

@@ -1,0 +1,455 @@
+"""Pins for the CPU oracle: each checks it against something other than
+itself -- numpy dense products, exact rational arithmetic, closed forms, the
+paper's stated special cases and a hand-worked example."""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_0910_4836_gb300 import synth as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def golden_matrix():
+    g = json.load(open(os.path.join(GOLDEN, "jds_5x5.json")))
+    n = g["n"]
+    rows, cols, vals = [], [], []
+    for i, cs in enumerate(g["rows"]):
+        for j in cs:
+            rows.append(i)
+            cols.append(j)
+            vals.append(10 * (i + 1) + (j + 1))
+    return g, S.from_coo(n, n, rows, cols, vals)
+
+
+def permuted_crs(A, J):
+    """CRS of P A P^T (rows in JDS order, entries in their CRS order,
+    columns renumbered), built with numpy only."""
+    lens = A.row_lengths()[J.perm]
+    rp = np.zeros(A.n_rows + 1, np.int64)
+    np.cumsum(lens, out=rp[1:])
+    src = np.concatenate([np.arange(A.row_ptr[p], A.row_ptr[p + 1]) for p in J.perm]) \
+        if A.nnz else np.zeros(0, np.int64)
+    col = A.col[src]
+    if J.symmetric:
+        col = J.iperm[col]
+    return S.CRS(A.n_rows, A.n_cols, rp.astype(np.int32), col.astype(np.int32), A.val[src])
+
+
+# ------------------------------------------------------------- CRS ------
+
+@pytest.mark.parametrize("shape,seed", [((1, 1), 0), ((17, 23), 1), ((120, 120), 2),
+                                        ((300, 77), 3), ((64, 300), 4)])
+def test_crs_vs_dense(shape, seed):
+    A = S.small_random(*shape, seed, density=0.1, empty_rows=0.1)
+    x = S.vector(A.n_cols, seed)
+    D = A.to_dense()
+    y = O.crs_spmv(A, x)
+    ye, s = O.crs_spmv_exact(A, x)
+    ref = D @ x
+    bound = 1e-14 * (np.abs(D) @ np.abs(x)) + 1e-300
+    assert np.all(np.abs(y - ref) <= bound)
+    assert np.all(np.abs(ye - ref) <= bound)
+    np.testing.assert_allclose(s, np.abs(D) @ np.abs(x), rtol=1e-13)
+
+
+def test_crs_accumulate_is_listing_update():
+    A = S.small_random(50, 40, 5, density=0.2)
+    x = S.vector(40, 5)
+    y0 = S.vector(50, 6)
+    y = O.crs_spmv(A, x, y0, accumulate=True)
+    np.testing.assert_allclose(y, y0 + A.to_dense() @ x, rtol=0, atol=1e-13)
+    ye, _ = O.crs_spmv_exact(A, x, y0, accumulate=True)
+    exact = [float(Fraction(y0[i]) + sum(Fraction(v) * Fraction(x[c]) for v, c in
+                                         zip(A.val[A.row_ptr[i]:A.row_ptr[i + 1]],
+                                             A.col[A.row_ptr[i]:A.row_ptr[i + 1]])))
+             for i in range(50)]
+    assert np.array_equal(ye, np.array(exact))
+
+
+def test_exact_oracle_is_correctly_rounded_on_cancellation():
+    # rows built to cancel catastrophically: naive sums lose every digit
+    rng_rows = []
+    vals = []
+    cols = []
+    for i in range(40):
+        big = S.uniform(7, 1, np.arange(i * 8, i * 8 + 8), 1e10, 1e12)
+        small = S.uniform(7, 2, np.arange(i * 8, i * 8 + 8), -1, 1)
+        v = np.concatenate([big, -big, small])
+        vals.extend(v)
+        cols.extend(range(24))
+        rng_rows.extend([i] * 24)
+    A = S.from_coo(40, 24, rng_rows, cols, vals, dedupe=False)
+    x = np.concatenate([np.ones(8), np.ones(8), np.full(8, 0.5)])
+    y, _ = O.crs_spmv_exact(A, x)
+    for i in range(40):
+        sl = slice(A.row_ptr[i], A.row_ptr[i + 1])
+        exact = float(sum(Fraction(v) * Fraction(x[c]) for v, c in zip(A.val[sl], A.col[sl])))
+        fs = math.fsum([float(v) * x[c] for v, c in zip(A.val[sl], A.col[sl])])
+        assert y[i] == exact
+        # x is 1 or 1/2, so every product is exact and fsum (correctly
+        # rounded summation) is a second, library, pin on the same value
+        assert fs == exact
+
+
+def test_identity_and_diagonal_bit_exact():
+    n = 257
+    x = S.vector(n, 11)
+    eye = S.from_coo(n, n, np.arange(n), np.arange(n), np.ones(n))
+    assert np.array_equal(O.crs_spmv(eye, x), x)
+    d = S.vector(n, 12, lo=-3, hi=3)
+    D = S.from_coo(n, n, np.arange(n), np.arange(n), d)
+    assert np.array_equal(O.crs_spmv(D, x), d * x)
+
+
+def test_integer_inputs_exact_and_order_free():
+    A = S.integer_values(S.random_rows(400, 13, 1, 60), 13, 1024)
+    x = S.int_vector(400, 13, 1024)
+    Ai = A.to_dense().astype(np.int64)
+    ref = (Ai @ x.astype(np.int64)).astype(np.float64)
+    assert np.array_equal(O.crs_spmv(A, x), ref)
+    assert np.array_equal(O.crs_spmv_exact(A, x)[0], ref)
+    assert np.array_equal(O.crs_spmv_omp(A, x), ref)
+
+
+def test_omp_bit_identical_to_serial():
+    A = S.zipf_rows(20000, 5, lmax=500)
+    x = S.vector(A.n_cols, 5)
+    assert np.array_equal(O.crs_spmv_omp(A, x), O.crs_spmv(A, x))
+
+
+def test_f32_loop_matches_numpy_float32_for_short_rows():
+    A = S.laplace2d(16, 16)
+    x = S.int_vector(256, 3, 100)
+    y = O.crs_spmv_f32(A, x)
+    ref = (A.to_dense() @ x).astype(np.float32)
+    assert np.array_equal(y, ref)
+
+
+def test_spmm_columns_are_spmv():
+    A = S.small_random(90, 70, 14, density=0.1)
+    X = np.stack([S.vector(70, 20 + c) for c in range(5)], axis=1)
+    Y = O.crs_spmm(A, X)
+    np.testing.assert_allclose(Y, A.to_dense() @ X, rtol=0, atol=1e-13)
+    for c in range(5):
+        assert np.array_equal(Y[:, c], O.crs_spmv(A, X[:, c]))
+
+
+# ------------------------------------------------- Laplacian closed forms --
+
+def test_laplace_constant_and_linear_vectors():
+    nx = ny = 64
+    A = S.laplace2d(nx, ny)
+    assert A.n_rows == 4096 and A.nnz == 20224
+    gx, gy = np.arange(4096) % nx, np.arange(4096) // nx
+    missing = (gx == 0).astype(int) + (gx == nx - 1) + (gy == 0) + (gy == ny - 1)
+    assert np.array_equal(O.crs_spmv(A, np.ones(4096)), missing.astype(float))
+    lin = 3.0 * gx + 5.0 * gy + 1.0
+    y = O.crs_spmv(A, lin)
+    interior = missing == 0
+    assert np.all(y[interior] == 0.0)
+
+
+@pytest.mark.parametrize("p,q", [(1, 1), (3, 7), (64, 1), (20, 33)])
+def test_laplace_eigenvectors(p, q):
+    A = S.laplace2d(64, 64)
+    i, j = np.arange(4096) % 64 + 1, np.arange(4096) // 64 + 1
+    # reduce p*i mod 130 first so every angle carries only one rounding
+    v = np.sin(np.pi * ((p * i) % 130) / 65) * np.sin(np.pi * ((q * j) % 130) / 65)
+    lam = 4 - 2 * np.cos(p * np.pi / 65) - 2 * np.cos(q * np.pi / 65)
+    y, s = O.crs_spmv_exact(A, v)
+    # the eigen-relation holds to the rounding of v itself (about 8 u |v| per row)
+    assert np.all(np.abs(y - lam * v) <= 1e-14 * s + 1e-15)
+
+
+# ------------------------------------------------------------- JDS ------
+
+def test_golden_jds_hand_example():
+    g, A = golden_matrix()
+    assert np.array_equal(O.crs_spmv(A, np.array(g["x"], float)), np.array(g["y"], float))
+    J = O.jds_build(A, symmetric=True)
+    assert J.perm.tolist() == g["perm"]
+    assert J.iperm.tolist() == g["iperm"]
+    assert J.jd_ptr.tolist() == g["jd_ptr"]
+    assert J.val.tolist() == g["val_jds"]
+    assert J.col.tolist() == g["col_jds_symmetric"]
+    xp = O.permute(J.perm, np.array(g["x"], float))
+    assert xp.tolist() == g["x_permuted"]
+    assert O.jds_spmv(J, xp).tolist() == g["y_permuted"]
+    R = O.jds_build(A, symmetric=False)
+    assert R.col.tolist() == g["col_jds_row_only"]
+    assert O.jds_spmv(R, np.array(g["x"], float)).tolist() == g["y_permuted"]
+    bp, c, v = O.rbjds_build(J, g["rbjds_block"])
+    assert bp.tolist() == g["rbjds_blk_ptr"]
+    assert v.tolist() == g["rbjds_val"]
+    assert c.tolist() == g["rbjds_col_symmetric"]
+    assert O.rbjds_spmv(J, bp, c, v, 2, xp).tolist() == g["y_permuted"]
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: S.small_random(200, 200, 21, density=0.05, empty_rows=0.2),
+    lambda: S.laplace2d(20, 20),
+    lambda: S.zipf_rows(3000, 22, lmax=300),
+    lambda: S.hh_like(2000, 23),
+])
+def test_jds_build_structure(maker):
+    A = maker()
+    lens = A.row_lengths()
+    for sym in (True, False):
+        J = O.jds_build(A, symmetric=sym)
+        # perm is a permutation, iperm its inverse
+        assert np.array_equal(np.sort(J.perm), np.arange(A.n_rows))
+        assert np.array_equal(J.iperm[J.perm], np.arange(A.n_rows))
+        # lengths non-increasing; equal lengths keep original order
+        pl = lens[J.perm]
+        assert np.all(np.diff(pl) <= 0)
+        same = np.diff(pl) == 0
+        assert np.all(np.diff(J.perm)[same] > 0)
+        # closed form: diagLen(d) = #{i : len_i > d}
+        nj = int(lens.max()) if A.n_rows else 0
+        assert J.n_diag == nj
+        expect = np.array([(lens > d).sum() for d in range(nj)])
+        assert np.array_equal(J.diag_len(), expect)
+        # round trip: every JDS entry maps back to the CRS entry it came from
+        rows_back = []
+        cols_back = []
+        vals_back = []
+        for d in range(nj):
+            for r in range(J.diag_len()[d]):
+                k = J.jd_ptr[d] + r
+                rows_back.append(J.perm[r])
+                cols_back.append(J.perm[J.col[k]] if sym else J.col[k])
+                vals_back.append(J.val[k])
+        B = S.from_coo(A.n_rows, A.n_cols, rows_back, cols_back, vals_back, dedupe=False)
+        assert np.array_equal(B.row_ptr, A.row_ptr)
+        assert np.array_equal(B.col, A.col)
+        assert np.array_equal(B.val, A.val)
+
+
+def test_jds_symmetric_rejects_rectangular():
+    A = S.small_random(30, 40, 3)
+    with pytest.raises(ValueError):
+        O.jds_build(A, symmetric=True)
+    J = O.jds_build(A, symmetric=False)
+    x = S.vector(40, 3)
+    y = O.permute(J.perm, O.jds_spmv(J, x), to_permuted=False)
+    np.testing.assert_allclose(y, A.to_dense() @ x, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("sym", [True, False])
+def test_jds_family_equals_crs_in_permuted_basis(sym):
+    """JDS / NBJDS / NUJDS / RBJDS all add each row's entries in slot order
+    from zero, so they are bit-identical to CRS on P A P^T; NUJDS with
+    u = N_j is stated to be exactly that (Sect. 2), RBJDS with block 1 is
+    row-by-row access and JDS is NBJDS with block = N (Sect. 3.2)."""
+    A = S.hh_like(5000, 31)
+    x = S.vector(A.n_cols, 31)
+    J = O.jds_build(A, symmetric=sym)
+    P = permuted_crs(A, J)
+    xp = O.permute(J.perm, x) if sym else x
+    ref = O.crs_spmv(P, xp)
+    assert np.array_equal(O.jds_spmv(J, xp), ref)
+    assert np.array_equal(O.nujds_spmv(J, xp, J.n_diag), ref)
+    for u in (1, 2, 3, 4, 8):
+        assert np.array_equal(O.nujds_spmv(J, xp, u), ref)
+    assert np.array_equal(O.nbjds_spmv(J, xp, A.n_rows), O.jds_spmv(J, xp))
+    for b in (1, 7, 128, 1000):
+        assert np.array_equal(O.nbjds_spmv(J, xp, b), ref)
+        bp, c, v = O.rbjds_build(J, b)
+        assert np.array_equal(O.rbjds_spmv(J, bp, c, v, b, xp), ref)
+    bp, c, v = O.rbjds_build(J, 1)
+    assert np.array_equal(bp, P.row_ptr)
+    assert np.array_equal(c, P.col)
+    assert np.array_equal(v, P.val)
+    # and the un-permuted result is A x
+    y = O.permute(J.perm, ref, to_permuted=False)
+    ye, s = O.crs_spmv_exact(A, x)
+    assert np.all(np.abs(y - ye) <= 1e-14 * s)
+
+
+def test_jds_integer_bit_exact_unpermuted():
+    A = S.integer_values(S.zipf_rows(5000, 41, lmax=2000), 41, 1024)
+    x = S.int_vector(A.n_cols, 41, 1024)
+    ref = O.crs_spmv(A, x)
+    J = O.jds_build(A, True)
+    y = O.permute(J.perm, O.jds_spmv(J, O.permute(J.perm, x)), to_permuted=False)
+    assert np.array_equal(y, ref)
+
+
+def test_empty_and_degenerate():
+    Z = S.CRS(5, 5, np.zeros(6, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    assert np.array_equal(O.crs_spmv(Z, np.ones(5)), np.zeros(5))
+    J = O.jds_build(Z)
+    assert J.n_diag == 0 and np.array_equal(J.perm, np.arange(5))
+    assert np.array_equal(O.jds_spmv(J, np.ones(5)), np.zeros(5))
+    one = S.from_coo(1, 1, [0], [0], [2.5])
+    assert O.crs_spmv(one, np.array([4.0]))[0] == 10.0
+    long_row = S.from_coo(3, 5000, [1] * 5000, np.arange(5000), np.ones(5000))
+    y = O.crs_spmv(long_row, np.ones(5000))
+    assert y.tolist() == [0.0, 5000.0, 0.0]
+
+
+# ------------------------------------------------------------ SOJDS -----
+
+def test_sojds_is_row_permutation_and_same_product():
+    A = S.hh_like(3000, 51)
+    x = S.vector(A.n_cols, 51)
+    J = O.jds_build(A, True)
+    xp = O.permute(J.perm, x)
+    for b in (1, 16, 100):
+        bp, c, v = O.rbjds_build(J, b)
+        bs, cs, vs = O.sojds_build(J, b)
+        assert np.array_equal(bp, bs)
+        # each row keeps its multiset of (col, val): compare per row
+        lens = A.row_lengths()[J.perm]
+        for k in range(len(bp) - 1):
+            b0 = k * b
+            rows = np.arange(b0, min(b0 + b, A.n_rows))
+            seg_r = np.concatenate([rows[: (lens[rows] > d).sum()] for d in range(lens[b0])]) \
+                if lens[b0] else np.zeros(0, int)
+            sl = slice(bp[k], bp[k + 1])
+            for r in rows:
+                m = seg_r == r
+                a = sorted(zip(c[sl][m], v[sl][m]))
+                s = sorted(zip(cs[sl][m], vs[sl][m]))
+                assert a == s
+        y = O.rbjds_spmv(J, bs, cs, vs, b, xp)
+        ref, sabs = O.crs_spmv_exact(permuted_crs(A, J), xp)
+        assert np.all(np.abs(y - ref) <= 1e-14 * sabs)
+
+
+def test_sojds_restores_unit_stride_on_shuffled_tridiagonal():
+    """Closed case: interior rows of a tridiagonal matrix have columns
+    {i-1, i, i+1}; with each row's entries stored in a shuffled order, the
+    greedy rule must give stride exactly one down every block column."""
+    n = 400
+    rows, cols = [], []
+    for i in range(n):
+        cs = [c for c in (i - 1, i, i + 1) if 0 <= c < n]
+        order = np.argsort(S.uniform01(61, 1, np.arange(3 * i, 3 * i + len(cs))))
+        for o in order:
+            rows.append(i)
+            cols.append(cs[o])
+    # unsorted entry order inside rows: build CRS directly, no sorting
+    rp = np.zeros(n + 1, np.int32)
+    np.cumsum(np.bincount(rows, minlength=n), out=rp[1:])
+    A = S.CRS(n, n, rp, np.array(cols, np.int32), np.arange(len(cols), dtype=float))
+    # row-only permutation keeps the original column numbers, so the interior
+    # rows (all of length 3, kept in order by the stable sort) stay banded
+    J = O.jds_build(A, False)
+    b = 50
+    bs, cs, vs = O.sojds_build(J, b)
+    lens = A.row_lengths()[J.perm]
+    nb = len(bs) - 1
+    for k in range(nb):
+        b0, b1 = k * b, min(k * b + b, n)
+        if not np.all(lens[b0:b1] == 3):
+            continue
+        block = cs[bs[k]:bs[k + 1]].reshape(3, b1 - b0)   # slot-major, 3 full slots
+        assert np.all(np.diff(block, axis=1) == 1)
+
+
+# ------------------------------------------------ adjoint and gradients --
+
+def test_adjoint_identity_and_transpose():
+    A = S.small_random(150, 90, 71, density=0.08)
+    g = S.vector(150, 71)
+    x = S.vector(90, 72)
+    at = O.crs_spmv_t(A, g)
+    np.testing.assert_allclose(at, A.to_dense().T @ g, rtol=0, atol=1e-14)
+    lhs = math.fsum(O.crs_spmv_t_exact(A, g)[0] * x)
+    rhs = math.fsum(g * O.crs_spmv_exact(A, x)[0])
+    assert abs(lhs - rhs) <= 1e-13 * math.fsum(np.abs(g) * (np.abs(A.to_dense()) @ np.abs(x)))
+    # integer values: scatter adjoint == CRS of the explicit transpose, bit-exact
+    Ai = S.integer_values(A, 71, 1000)
+    gi = S.int_vector(150, 72, 1000)
+    rid = Ai.row_ids()
+    T = S.from_coo(90, 150, Ai.col, rid, Ai.val)
+    assert np.array_equal(O.crs_spmv_t(Ai, gi), O.crs_spmv(T, gi))
+    assert np.array_equal(O.crs_spmv_t_exact(Ai, gi)[0], O.crs_spmv(T, gi))
+
+
+def test_dval_is_gradient_of_bilinear_form():
+    A = S.small_random(40, 30, 81, density=0.2)
+    g = S.vector(40, 81)
+    x = S.vector(30, 82)
+    dv = O.dval(A, g, x)
+    rid = A.row_ids()
+    assert np.array_equal(dv, g[rid] * x[A.col])
+    # central difference of f(val) = g . (A x); f is linear in val, so the
+    # difference quotient is exact up to rounding
+    h = 1e-3
+    for k in range(0, A.nnz, max(A.nnz // 25, 1)):
+        vp, vm = A.val.copy(), A.val.copy()
+        vp[k] += h
+        vm[k] -= h
+        fp = math.fsum(g * O.crs_spmv(S.CRS(40, 30, A.row_ptr, A.col, vp), x))
+        fm = math.fsum(g * O.crs_spmv(S.CRS(40, 30, A.row_ptr, A.col, vm), x))
+        assert abs((fp - fm) / (2 * h) - dv[k]) <= 1e-9
+
+
+def test_power_gradient_finite_differences():
+    A = S.stencil27(6, 4)
+    x = S.vector(A.n_cols, 4)
+    m = 3
+    L, dv, dx = O.power_loss_grad(A, x, m)
+
+    def loss(val, xx):
+        B = S.CRS(A.n_rows, A.n_cols, A.row_ptr, A.col, val)
+        return float(np.dot(O.power_forward(B, xx, m)[-1], O.power_forward(B, xx, m)[-1]))
+
+    h = 1e-6
+    for t in range(4):
+        dvec = S.uniform(4, 90 + t, np.arange(A.nnz), -1, 1)
+        fd = (loss(A.val + h * dvec, x) - loss(A.val - h * dvec, x)) / (2 * h)
+        an = float(np.dot(dv, dvec))
+        assert abs(fd - an) <= 1e-6 * abs(an)
+        dxv = S.uniform(4, 95 + t, np.arange(A.n_cols), -1, 1)
+        fd = (loss(A.val, x + h * dxv) - loss(A.val, x - h * dxv)) / (2 * h)
+        an = float(np.dot(dx, dxv))
+        assert abs(fd - an) <= 1e-6 * abs(an)
+
+
+def test_power_gradient_closed_form_symmetric():
+    """For symmetric A, d||A^m x||^2/dx = 2 A^{2m} x."""
+    A = S.stencil27(6, 4, symmetric_values=True)
+    D = A.to_dense()
+    assert np.array_equal(D, D.T)
+    x = S.vector(A.n_cols, 5)
+    m = 4
+    _, _, dx = O.power_loss_grad(A, x, m)
+    ref = 2 * O.power_forward(A, x, 2 * m)[-1]
+    np.testing.assert_allclose(dx, ref, rtol=1e-12, atol=1e-15)
+
+
+# -------------------------------------------------------- generators ----
+
+def test_generator_shapes():
+    A = S.hh_like(20000, 1)
+    D = A.to_dense() if A.n_rows <= 2000 else None
+    assert D is None
+    lens = A.row_lengths()
+    # at this small size the far band offsets (up to 262144) mostly fall off
+    # the matrix; the full 6e6 workload gives about 13 per row
+    assert 7 <= lens.mean() <= 15
+    # symmetric pattern and values
+    T = S.from_coo(A.n_cols, A.n_rows, A.col, A.row_ids(), A.val)
+    assert np.array_equal(T.row_ptr, A.row_ptr) and np.array_equal(T.col, A.col)
+    assert np.array_equal(T.val, A.val)
+    Z = S.zipf_rows(200000, 2)
+    assert 5.3 <= Z.nnz / Z.n_rows <= 5.7
+    assert Z.row_lengths().max() <= 5000
+    assert S.stencil27(10).nnz == 28 ** 3
+    assert S.laplace2d().nnz == 20224
+    # rows come out column-sorted
+    for M in (A, Z):
+        d = np.diff(M.col.astype(np.int64))
+        starts = M.row_ptr[1:-1]
+        mask = np.ones(len(d), bool)
+        mask[starts[(starts > 0) & (starts <= len(d))] - 1] = False
+        assert np.all(d[mask] > 0)
