@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark: FP64 sparse matrix-vector multiplication y = A x on GB300.
+
+Workload (one step = one SpMVM over the whole matrix, the hot path of the
+paper's Sect. 2 CRS kernel): the synthetic Holstein-Hubbard-like matrix,
+N = 6,000,000 rows, symmetric, banded plus 20% scattered entries, about 13
+entries per row (see paper_0910_4836_gb300/synth.py, hh_like).  The matrix
+(about 1 GB) is resident in HBM like an operator inside an eigen-solver; x
+and y are the step's input and output.
+
+Prints ONE JSON line.  --impl reference times the CPU oracle instead (the
+paper's best CPU setting: CRS with an OpenMP static schedule).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpMVM GFlop/s & HBM GB/s vs roofline; batched & fwd+bwd speedup vs plain"
+WORKLOAD = "hh_like N=6,000,000 FP64 CRS SpMVM (symmetric banded + 20% scattered, ~13 nnz/row)"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--config", type=int, default=1, choices=[1, 2, 4])
+    p.add_argument("--kernel", default="auto", help="auto | tiled | vector")
+    p.add_argument("--no-formats", action="store_true", help="skip the per-format table")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def make_workload(cfg):
+    from paper_0910_4836_gb300 import synth as S
+    A = S.config(cfg)
+    x = S.vector(A.n_cols, cfg)
+    return A, x
+
+
+def algorithmic_bytes(n_rows, n_cols, nnz, vbytes=8):
+    # val + col streamed once, row_ptr once, x read at least once, y written once
+    return vbytes * nnz + 4 * nnz + 4 * (n_rows + 1) + vbytes * n_cols + vbytes * n_rows
+
+
+# ------------------------------------------------------------- clocks ------
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join("/tmp", f"gbspmv_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": reasons,
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()),
+                                   default=None)}
+
+
+# ---------------------------------------------------------- distributed ----
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_0910_4836_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.startswith("crs") or f.endswith(".cuh"):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# capture, keyed by the hash of the CRS kernel sources it was taken on; a
+# different hash means the kernel changed since and traffic is reported null.
+NCU_TRAFFIC = {}
+
+
+# --------------------------------------------------------------- ours ------
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    import paper_0910_4836_gb300 as g
+    from paper_0910_4836_gb300 import CRSMatrix, JDSMatrix  # noqa: F401
+    g.build()
+
+    A, x_host = make_workload(args.config)
+    M = CRSMatrix.from_host(A, device=dev, dtype=torch.float64)
+    x = torch.as_tensor(x_host).to(dev)
+    y = torch.empty(A.n_rows, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def time_launches(fn, reps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        for i in range(reps):
+            fn()
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        return [ev[i].elapsed_time(ev[i + 1]) for i in range(reps)]
+
+    # kernel choice: the tuned candidates, fastest over a few timed launches
+    candidates = []
+    if args.kernel in ("auto", "tiled"):
+        candidates += [("tiled", t) for t in (2048, 1024)]
+    if args.kernel in ("auto", "vector"):
+        candidates += [("vector", (l, r)) for l, r in ((8, 2), (8, 4), (16, 2), (4, 4))]
+    best = None
+    for kind, p in candidates:
+        if kind == "tiled":
+            M.prepare_tiled(p)
+        else:
+            M.set_kernel("vector", lanes=p[0], rows_per_warp=p[1])
+        t = statistics.median(time_launches(lambda: M.spmv(x, out=y), 5))
+        if best is None or t < best[0]:
+            best = (t, kind, p)
+    _, kind, p = best
+    if kind == "tiled":
+        M.prepare_tiled(p)
+    else:
+        M.set_kernel("vector", lanes=p[0], rows_per_warp=p[1])
+    kernel_desc = f"{kind} {p}"
+
+    def step():
+        M.spmv(x, out=y)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    with ClockSampler(torch.cuda.current_device() if world == 1 else local) as clk:
+        times = time_launches(step, args.steps)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / args.steps
+    flops = 2.0 * A.nnz
+    gflops = world * flops / (ms * 1e-3) / 1e9
+    alg = algorithmic_bytes(A.n_rows, A.n_cols, A.nnz)
+    gbs = alg / (ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    h = kernel_source_hash()
+    traffic = NCU_TRAFFIC.get((args.config, kind, str(p), h))
+
+    # end to end through the public API: pinned host x in, host y out
+    xh = torch.as_tensor(x_host).pin_memory()
+    yh = torch.empty(A.n_rows, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        x.copy_(xh, non_blocking=True)
+        M.spmv(x, out=y)
+        yh.copy_(y, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    et = time_launches(e2e_step, max(5, min(args.steps, 20)))
+    e2e_ms = sum(et) / len(et)
+
+    result = None
+    if rank == 0:
+        result = {
+            "metric": METRIC, "value": round(gflops, 2), "unit": "GFlop/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded SplitMix64; stand-in for the paper's Holstein-Hubbard matrix)",
+            "hbm_gbs": round(gbs, 1),
+            "config": {"workload": WORKLOAD, "config_index": args.config, "n_rows": A.n_rows,
+                       "nnz": A.nnz, "kernel": kernel_desc,
+                       "l2": "inputs larger than L2 (matrix ~1 GB), no flush",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(gbs / peak, 4), "traffic": traffic,
+                         "algorithmic_bytes": alg, "peak_source": f"{peak_kind} hbm_gbs (burst)",
+                         "kernel_source_hash": h},
+            "e2e": {"value": round(world * flops / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GFlop/s",
+                    "h2d_bytes_per_step": 8 * A.n_cols, "d2h_bytes_per_step": 8 * A.n_rows,
+                    "ms_per_step": round(e2e_ms, 4)},
+            "gpu_launches": args.steps * launches_per_step(kind),
+            "clocks": clk.summary(),
+        }
+        if not args.no_formats:
+            result["formats"] = format_table(M, A, x, time_launches, dev, peak)
+        result["cpu_baseline"] = cpu_baseline(A, x_host, args.cpu_seconds)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return result
+
+
+def launches_per_step(kind):
+    return 1
+
+
+def format_table(M, A, x, time_launches, dev, peak):
+    """GFlop/s of every storage scheme on the same matrix (the paper's
+    serial comparison, on GB300): median of 10 launches each."""
+    import torch
+    out = {}
+    flops = 2.0 * A.nnz
+    y = torch.empty(A.n_rows, dtype=torch.float64, device=dev)
+
+    def rec(name, fn, nbytes):
+        t = statistics.median(time_launches(fn, 10))
+        out[name] = {"gflops": round(flops / (t * 1e-3) / 1e9, 1),
+                     "gbs": round(nbytes / (t * 1e-3) / 1e9, 1), "ms": round(t, 4)}
+
+    alg = algorithmic_bytes(A.n_rows, A.n_cols, A.nnz)
+    for l, r in ((4, 4), (8, 2), (16, 2), (32, 1)):
+        M.set_kernel("vector", lanes=l, rows_per_warp=r)
+        rec(f"CRS vector l{l} r{r}", lambda: M.spmv(x, out=y), alg)
+    M.prepare_tiled(2048)
+    rec("CRS tiled 2048", lambda: M.spmv(x, out=y), alg)
+    jalg = 12 * A.nnz + 16 * A.n_rows  # permuted basis; jd_ptr is negligible
+    for perm in ("symmetric", "row_only"):
+        J = M.to_jds("JDS", perm)
+        xp = J.permute(x) if perm == "symmetric" else x
+        for fmt, b, u in (("JDS", 0, 0), ("NUJDS", 0, 4), ("NBJDS", 1024, 0), ("JDS_LITERAL", 0, 0)):
+            J.set_format(fmt, block=b, unroll=u)
+            rec(f"{fmt} {perm}" + (f" b={b}" if b else "") + (f" u={u}" if u else ""),
+                lambda: J.spmv(xp, out=y), jalg)
+        del J
+        for fmt in ("RBJDS", "SOJDS"):
+            R = M.to_jds(fmt, perm, block=1024)
+            rec(f"{fmt} {perm} b=1024", lambda: R.spmv(xp, out=y), jalg)
+            del R
+        torch.cuda.empty_cache()
+    return out
+
+
+# ------------------------------------------------------------ CPU side -----
+
+def cpu_baseline(A, x, seconds):
+    """The oracle's OpenMP static-schedule CRS loop on the host cores, on
+    the full matrix, repeated for about `seconds`."""
+    import oracle as O
+    y = np.zeros(A.n_rows)
+    O.crs_spmv_omp(A, x, y)  # first touch
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        O.crs_spmv_omp(A, x, y)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or reps >= 200:
+            break
+    per = el / reps
+    return {"value": round(2.0 * A.nnz / per / 1e9, 3), "unit": "GFlop/s",
+            "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"full matrix, {reps} SpMVMs with the OpenMP static CRS loop ({el:.1f} s)"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    A, x = make_workload(args.config)
+    import oracle as O
+    y = np.zeros(A.n_rows)
+    O.crs_spmv_omp(A, x, y)
+    for _ in range(max(args.warmup, 3)):
+        O.crs_spmv_omp(A, x, y)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.crs_spmv_omp(A, x, y)
+    el = time.perf_counter() - t0
+    per = el / args.steps
+    val = round(2.0 * A.nnz / per / 1e9, 3)
+    return {"metric": METRIC, "value": val, "unit": "GFlop/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(per * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "config_index": args.config, "n_rows": A.n_rows,
+                       "nnz": A.nnz, "kernel": "oracle CRS loop, OpenMP static schedule"},
+            "cpu_baseline": {"value": val, "unit": "GFlop/s", "cores": O.num_threads(),
+                             "kind": "oracle", "sample": f"full matrix, {args.steps} timed SpMVMs"},
+            "e2e": {"value": val, "unit": "GFlop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    res = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

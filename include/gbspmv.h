@@ -1,0 +1,336 @@
+/*
+ * gbspmv -- sparse matrix-vector multiplication on GB300 (sm_103a).
+ *
+ * C ABI of the library.  It implements y = A*x for a sparse A stored in the
+ * two schemes studied by Schubert, Hager & Fehske, "Performance limitations
+ * for sparse matrix-vector multiplications on current multicore
+ * environments" (Sect. 2): compressed row storage (CRS) and jagged diagonal
+ * storage (JDS) with its refinements NBJDS, RBJDS, NUJDS and SOJDS; plus
+ * multiple right-hand sides, the adjoint A^T*g, the per-entry value gradient,
+ * a batched persistent launch and an FP32 path with compensated sums.
+ *
+ * Conventions used by every entry point
+ *   - Indices are 0-based int32; sizes and counts are int64.
+ *   - Pointers named d_* are DEVICE pointers on the current CUDA device;
+ *     h_* are host pointers.  `stream` is a cudaStream_t passed as void*
+ *     (NULL = the legacy default stream).
+ *   - The library never allocates device memory: every device buffer is
+ *     allocated by the caller and only borrowed.  A handle keeps the
+ *     pointers it was given, so the caller must keep those buffers alive and
+ *     unchanged in shape until gbsp_destroy.  Values may be overwritten in
+ *     place between calls (e.g. by an optimiser) without rebuilding.
+ *   - Every entry point returns a gbsp_status and never throws.  Kernel
+ *     launches are asynchronous: a GBSP_OK return means the work was queued
+ *     on `stream`.  Device-side checks (validation, bounded waits) report
+ *     into a caller-provided int32 status word in device memory.
+ *   - All kernels are deterministic: the same inputs give bit-identical
+ *     outputs on every run (no floating-point atomics).
+ */
+#ifndef GBSPMV_H
+#define GBSPMV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbsp_mat *gbsp_handle;
+typedef struct gbsp_batch_s *gbsp_batch;
+
+typedef enum {
+    GBSP_OK = 0,
+    GBSP_ERR_ARG = -1,         /* bad argument: null pointer, negative size, misaligned, mismatch */
+    GBSP_ERR_MATRIX = -2,      /* malformed CRS: row_ptr not monotone, col out of range, nnz mismatch */
+    GBSP_ERR_CUDA = -3,        /* a CUDA runtime call failed (message: gbsp_last_error) */
+    GBSP_ERR_NOMEM = -4,       /* a caller buffer is smaller than the size the plan asked for */
+    GBSP_ERR_UNSUPPORTED = -5, /* valid request this handle / build cannot serve */
+    GBSP_ERR_TIMEOUT = -6      /* a bounded device-side wait gave up */
+} gbsp_status;
+
+typedef enum { GBSP_F64 = 0, GBSP_F32 = 1 } gbsp_dtype;
+
+/* Storage schemes (Sect. 2).  JDS, NBJDS and NUJDS share one storage
+ * pattern and differ in how the kernel walks it; RBJDS and SOJDS store each
+ * row block consecutively.  JDS_LITERAL is the paper's diagonal-after-
+ * diagonal loop with a result-vector round trip per diagonal. */
+typedef enum {
+    GBSP_CRS = 0,
+    GBSP_JDS = 1,
+    GBSP_NBJDS = 2,
+    GBSP_RBJDS = 3,
+    GBSP_NUJDS = 4,
+    GBSP_SOJDS = 5,
+    GBSP_JDS_LITERAL = 6
+} gbsp_format;
+
+/* Sect. 2: JDS permutes rows AND columns (A_{p(i),p(j)}), so all work runs in
+ * the permuted basis (SYMMETRIC, the paper's scheme; square matrices only).
+ * ROW_ONLY permutes rows only and keeps original column numbers (a
+ * GPU-friendly deviation that preserves the locality of x). */
+typedef enum { GBSP_PERM_SYMMETRIC = 0, GBSP_PERM_ROW_ONLY = 1 } gbsp_perm_mode;
+
+typedef enum { GBSP_OP_N = 0, GBSP_OP_T = 1 } gbsp_op;
+
+/* Basis of x and y for JDS-family handles.  PERMUTED: x is indexed like the
+ * stored columns (x_p = P x under SYMMETRIC, x itself under ROW_ONLY) and y
+ * comes out in permuted row order y_p = P y.  ORIGINAL: x and y in the
+ * user's numbering; the kernel gathers through perm on the fly. */
+typedef enum { GBSP_BASIS_PERMUTED = 0, GBSP_BASIS_ORIGINAL = 1 } gbsp_basis;
+
+/* Accumulation mode for FP32 handles.  PLAIN: float products and sums.
+ * COMPENSATED: per-row Dot2 (Ogita, Rump & Oishi 2005) -- exact products by
+ * fmaf, TwoSum accumulation, carried through the lane reduction; result
+ * rounded to float once.  FP64 handles ignore it. */
+typedef enum { GBSP_ACC_PLAIN = 0, GBSP_ACC_COMPENSATED = 1 } gbsp_accum;
+
+/* CRS kernel choice.  VECTOR: `lanes` threads of a warp per row, each warp
+ * working on `rows_per_warp` rows at a time (lanes * rows in flight).
+ * TILED: rows grouped into tiles of about `tile` (rows + entries), each
+ * tile's entries streamed through shared memory with bulk asynchronous
+ * copies; needs gbsp_crs_prepare.  AUTO picks from the row-length mean. */
+typedef enum { GBSP_KERNEL_AUTO = 0, GBSP_KERNEL_VECTOR = 1, GBSP_KERNEL_TILED = 2 } gbsp_kernel;
+
+typedef struct {
+    int32_t kernel;        /* gbsp_kernel */
+    int32_t lanes;         /* VECTOR: 1, 2, 4, 8, 16 or 32 (0 = auto) */
+    int32_t rows_per_warp; /* VECTOR: rows per lane group handled together, 1..8 (0 = auto) */
+    int32_t tile;          /* TILED: merge items (rows + entries) per tile, 256..8192 (0 = auto) */
+    int32_t rhs_tile;      /* SpMM: right-hand sides handled per pass, 1..16 (0 = auto) */
+    int32_t accum;         /* gbsp_accum (FP32 handles) */
+} gbsp_kernel_opts;
+
+/* ---------------------------------------------------------------- misc -- */
+
+/* Human-readable name of a status code (static storage). */
+const char *gbsp_status_string(gbsp_status s);
+
+/* Text of the last CUDA or argument error seen by the calling thread
+ * (thread-local, static storage, empty if none). */
+const char *gbsp_last_error(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int32_t gbsp_version(void);
+
+/* Release a matrix handle (never the borrowed buffers).  NULL is a no-op. */
+gbsp_status gbsp_destroy(gbsp_handle h);
+
+/* Copy a device status word to *h_out (synchronises `stream`). */
+gbsp_status gbsp_read_status(const int32_t *d_status, void *stream, int32_t *h_out);
+
+/* ----------------------------------------------------------------- CRS -- */
+
+/* Create a CRS handle (Sect. 2, "compressed row storage": val, col_idx and
+ * row_ptr, row i owning entries row_ptr[i] .. row_ptr[i+1]-1).
+ *   n_rows, n_cols >= 0, nnz >= 0 (nnz < 2^31).
+ *   d_row_ptr: int32[n_rows+1], d_col: int32[nnz], d_val: double[nnz]
+ *   (GBSP_F64) or float[nnz] (GBSP_F32).  d_col and d_val may be NULL only
+ *   when nnz == 0.  Entries inside a row may be in any column order.
+ * Borrowed pointers; nothing is read here (no device work).  Errors:
+ * GBSP_ERR_ARG on negative sizes, NULL pointers or a bad dtype. */
+gbsp_status gbsp_crs_create(int64_t n_rows, int64_t n_cols, int64_t nnz,
+                            const int32_t *d_row_ptr, const int32_t *d_col,
+                            const void *d_val, gbsp_dtype dtype, gbsp_handle *out);
+
+/* Check the CRS arrays on the device: row_ptr[0] == 0, row_ptr
+ * non-decreasing, row_ptr[n_rows] == nnz, 0 <= col < n_cols.  Writes 0 to
+ * *d_status when all hold, else a GBSP_ERR_MATRIX code (no trap, no abort).
+ * d_status: int32 in device memory.  Asynchronous on `stream`. */
+gbsp_status gbsp_crs_validate(gbsp_handle crs, int32_t *d_status, void *stream);
+
+/* Choose the kernel used by gbsp_spmv / gbsp_spmm for this CRS handle.
+ * Only fields that differ from 0 override the current choice.  Errors:
+ * GBSP_ERR_ARG for out-of-range values. */
+gbsp_status gbsp_set_kernel(gbsp_handle h, const gbsp_kernel_opts *opts);
+gbsp_status gbsp_get_kernel(gbsp_handle h, gbsp_kernel_opts *out);
+
+/* TILED kernel set-up: bytes of the tile table for `tile` merge items per
+ * tile (an int32 row index per tile boundary), and a device pass that fills
+ * it into caller memory (borrowed until destroy or the next prepare).
+ * The tile table is a pure function of row_ptr. */
+gbsp_status gbsp_crs_tile_bytes(gbsp_handle crs, int32_t tile, int64_t *bytes);
+gbsp_status gbsp_crs_prepare(gbsp_handle crs, int32_t tile, void *d_table, int64_t table_bytes,
+                             void *stream);
+
+/* ----------------------------------------------------- CRS -> JDS family -- */
+
+typedef struct {
+    int32_t format;     /* gbsp_format, one of the JDS family */
+    int32_t perm_mode;  /* gbsp_perm_mode */
+    int32_t block;      /* NBJDS / RBJDS / SOJDS: rows per block (>= 1; 0 = 256) */
+    int32_t unroll;     /* NUJDS: diagonals per step u (>= 1; 0 = 4) */
+} gbsp_jds_opts;
+
+typedef struct {
+    int64_t n_rows, n_cols, nnz;
+    int64_t n_diag;           /* N_j = longest row */
+    int64_t n_blocks;         /* RBJDS / SOJDS blocks, else 0 */
+    int64_t workspace_bytes;  /* scratch for gbsp_jds_build only */
+} gbsp_jds_sizes;
+
+/* Caller-allocated outputs of the conversion (device memory). */
+typedef struct {
+    int32_t *jd_ptr;   /* [n_diag+1] start of each jagged diagonal (Sect. 2 jd_ptr) */
+    int32_t *col;      /* [nnz] column indices in storage order */
+    void *val;         /* [nnz] values, same dtype as the CRS handle */
+    int32_t *perm;     /* [n_rows] perm[new] = old row */
+    int32_t *iperm;    /* [n_rows] iperm[old] = new row */
+    int32_t *blk_ptr;  /* [n_blocks+1] RBJDS / SOJDS only, else may be NULL */
+    void *workspace;   /* [workspace_bytes] scratch, free after the build completes */
+} gbsp_jds_buffers;
+
+/* Sizes for converting `crs` (Sect. 2 JDS construction).  Reads the row
+ * lengths on the device (d_scratch: at least 4 bytes of device memory used
+ * for the longest-row reduction) and SYNCHRONISES `stream` to learn N_j.
+ * Errors: GBSP_ERR_UNSUPPORTED for SYMMETRIC on a non-square matrix,
+ * GBSP_ERR_ARG for a format outside the JDS family. */
+gbsp_status gbsp_jds_plan(gbsp_handle crs, const gbsp_jds_opts *opts, int32_t *d_scratch,
+                          void *stream, gbsp_jds_sizes *out);
+
+/* Build the JDS-family arrays on the device and return a handle over them
+ * (borrowing `bufs`, except workspace).  Steps: row lengths; stable sort by
+ * decreasing length (ties keep original row order, empty rows last) giving
+ * perm / iperm; jd_ptr from #{rows with length > d}; entries shifted left
+ * (slot d = the row's d-th stored entry) and scattered diagonal by
+ * diagonal; columns renumbered by iperm under SYMMETRIC.  RBJDS re-lays
+ * each block of `block` permuted rows contiguously, diagonal-major;
+ * SOJDS additionally re-orders each row inside its block so that block
+ * columns read x with stride one where possible (nearest-column greedy:
+ * slot d of row r takes the unplaced entry whose column is closest to
+ * 1 + the column in slot d of row r-1, ties to the smaller column; the first
+ * row of a block keeps its order).  Output arrays are bit-exact functions of
+ * the input.  `bufs` sizes must match gbsp_jds_plan. */
+gbsp_status gbsp_jds_build(gbsp_handle crs, const gbsp_jds_opts *opts,
+                           const gbsp_jds_buffers *bufs, const gbsp_jds_sizes *sizes,
+                           void *stream, gbsp_handle *out);
+
+/* Switch a built JDS-family handle between the formats that share its
+ * storage pattern (JDS <-> NBJDS <-> NUJDS <-> JDS_LITERAL) and set block
+ * or unroll.  RBJDS / SOJDS handles accept only a block size equal to the
+ * one they were built with.  Errors: GBSP_ERR_UNSUPPORTED otherwise. */
+gbsp_status gbsp_jds_set_format(gbsp_handle jds, int32_t format, int32_t block, int32_t unroll);
+
+/* Read back the JDS-family shape (host-side, no device work). */
+gbsp_status gbsp_jds_info(gbsp_handle jds, gbsp_jds_sizes *out, gbsp_jds_opts *opts);
+
+/* Vector basis change (Sect. 2, "all further calculations are performed in
+ * this permuted basis"): dir 0 writes out[r] = in[perm[r]] (to permuted),
+ * dir 1 writes out[perm[r]] = in[r] (back).  k columns, row-major with
+ * leading dimension ld (>= k) for both.  n = n_rows of the handle. */
+gbsp_status gbsp_permute_vec(gbsp_handle jds, int32_t dir, int32_t k, const void *d_in,
+                             int64_t ld_in, void *d_out, int64_t ld_out, void *stream);
+
+/* ------------------------------------------------------------- products -- */
+
+/* y = op(A) x, or y += op(A) x when accumulate != 0 (the paper's listings
+ * update resvec in place; Sect. 2).  For CRS:
+ *   y_i = sum_{j=row_ptr[i]}^{row_ptr[i+1]-1} val_j x[col_j].
+ * For JDS-family handles the sum runs over the row's jagged-diagonal
+ * entries; `basis` chooses the vector numbering (see gbsp_basis).
+ * op = GBSP_OP_T needs a transpose attached (gbsp_transpose_build or
+ * gbsp_attach_transpose) and uses basis ORIGINAL.
+ * x: n_cols (op N) or n_rows (op T) elements of the handle's dtype, y the
+ * other size; both contiguous device vectors that must not overlap.
+ * Errors: GBSP_ERR_ARG (NULL, overlap), GBSP_ERR_UNSUPPORTED (op T without
+ * transpose, op T in the permuted basis), GBSP_ERR_CUDA (launch). */
+gbsp_status gbsp_spmv(gbsp_handle A, int32_t op, int32_t basis, int32_t accumulate,
+                      const void *d_x, void *d_y, void *stream);
+
+/* Y = op(A) X (+ Y) for k right-hand sides.  X and Y row-major: entry (i, c)
+ * at [i*ld + c], ld >= k.  Every stored entry of A is read once per pass of
+ * `rhs_tile` columns.  k = 1 with ld > 1 computes one strided column. */
+gbsp_status gbsp_spmm(gbsp_handle A, int32_t op, int32_t basis, int32_t k, const void *d_X,
+                      int64_t ldx, void *d_Y, int64_t ldy, int32_t accumulate, void *stream);
+
+/* ------------------------------------------------------- adjoint, dval -- */
+
+/* Transposed structure of a CRS handle: a CRS of A^T (n_cols rows) whose
+ * entries are listed per column of A in ascending entry order, plus
+ * tmap[t] = index in A of transposed entry t.  Values are gathered with
+ * gbsp_transpose_values (again whenever A's values change).  The result
+ * handle is attached to `crs` so that gbsp_spmv(crs, OP_T, ...) uses it.
+ *   bufs: t_row_ptr int32[n_cols+1], t_col int32[nnz] (= row of A),
+ *         t_val [nnz] of A's dtype, tmap int32[nnz], workspace. */
+typedef struct {
+    int32_t *t_row_ptr;
+    int32_t *t_col;
+    void *t_val;
+    int32_t *tmap;
+    void *workspace;
+} gbsp_transpose_buffers;
+
+gbsp_status gbsp_transpose_workspace(gbsp_handle crs, int64_t *bytes);
+gbsp_status gbsp_transpose_build(gbsp_handle crs, const gbsp_transpose_buffers *bufs,
+                                 int64_t workspace_bytes, void *stream, gbsp_handle *out);
+/* t_val[t] = val[tmap[t]] for the transpose built from `crs`. */
+gbsp_status gbsp_transpose_values(gbsp_handle crs, void *stream);
+
+/* Make `at` (any handle holding A^T, e.g. a JDS of the transpose) the one
+ * used for gbsp_spmv(A, OP_T, ...).  Borrowed; no checks of its content. */
+gbsp_status gbsp_attach_transpose(gbsp_handle A, gbsp_handle at);
+
+/* Value gradient of a CRS product: dval_k = g[row_k] * x[col_k] (the
+ * derivative of g.(A x) with respect to val_k), written (or added, if
+ * accumulate) in CRS entry order.  g: n_rows, x: n_cols, dval: nnz. */
+gbsp_status gbsp_dval(gbsp_handle crs, const void *d_g, const void *d_x, void *d_dval,
+                      int32_t accumulate, void *stream);
+
+/* Fused multi-step value gradient: dval_k (+)= sum_{t<m} G[row_k, t] *
+ * X[col_k, t], G (n_rows x m, ld ldg) and X (n_cols x m, ld ldx) row-major:
+ * one pass over the entries for m product pairs (iterated products A^m x). */
+gbsp_status gbsp_dval_multi(gbsp_handle crs, int32_t m, const void *d_G, int64_t ldg,
+                            const void *d_X, int64_t ldx, void *d_dval, int32_t accumulate,
+                            void *stream);
+
+/* -------------------------------------------------------------- batched -- */
+
+/* One item of a batch: Y_b = A_b X_b with k_b right-hand sides (row-major,
+ * leading dimensions ldx/ldy).  A_b is a CRS or JDS-family handle of
+ * either dtype; its current kernel options give the rows per warp and
+ * right-hand-side tile used inside the batch.  JDS items run in the
+ * permuted basis. */
+typedef struct {
+    gbsp_handle A;
+    int32_t k;
+    const void *X;
+    int64_t ldx;
+    void *Y;
+    int64_t ldy;
+} gbsp_batch_item;
+
+/* Bytes of the device work table for n items (work items of about
+ * `chunk` entries each; 0 = 4096). */
+gbsp_status gbsp_batch_plan(int32_t n, const gbsp_batch_item *items, int32_t chunk,
+                            int64_t *table_bytes);
+
+/* Write the work table into caller memory d_table (table_bytes from the
+ * plan) and return a batch object.  Synchronises `stream` once. */
+gbsp_status gbsp_batch_create(int32_t n, const gbsp_batch_item *items, int32_t chunk,
+                              void *d_table, int64_t table_bytes, void *stream,
+                              gbsp_batch *out);
+
+/* All items in one persistent launch: CTAs take work items from the table
+ * through a device counter (reset on `stream` first, so replays in a CUDA
+ * graph are safe).  d_status (may be NULL) receives GBSP_ERR_TIMEOUT if the
+ * kernel's bounded wait for its start flag ran out, else 0. */
+gbsp_status gbsp_batch_run(gbsp_batch b, int32_t *d_status, void *stream);
+gbsp_status gbsp_batch_destroy(gbsp_batch b);
+
+/* ------------------------------------------------------------ autotuner -- */
+
+/* Time the candidate kernels for `A` with k right-hand sides on the device
+ * (CUDA events on `stream`, a few repetitions each, X and Y are scratch
+ * vectors of the right sizes) and keep the fastest option set on the handle.
+ * For CRS handles the candidates are VECTOR with every lanes/rows_per_warp
+ * pair and TILED (when prepared); for JDS-family handles the formats sharing
+ * the handle's storage and their block/unroll values.  *best receives the
+ * choice and *best_ms its time.  Synchronises `stream`. */
+gbsp_status gbsp_autotune(gbsp_handle A, int32_t k, const void *d_X, void *d_Y, void *stream,
+                          gbsp_kernel_opts *best, float *best_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBSPMV_H */

@@ -1,0 +1,324 @@
+// CRS products (Sect. 2, CRS kernel: y_i = sum over row i of val_j x[col_j]).
+//
+// VECTOR: a warp is cut into groups of L lanes; each group owns one row at a
+// time and strides through its entries (lane l takes entries l, l+L, ...),
+// so a warp-wide load covers 32/L adjacent rows' entries contiguously.  Each
+// group keeps R rows in flight: the loads of all R rows are issued before
+// any product is formed, which is what keeps enough bytes in flight to
+// saturate HBM with short rows.  The partial sums are combined by a fixed
+// butterfly of warp shuffles.
+//
+// SpMM: lanes over right-hand sides -- a group of KT lanes owns one row and
+// lane c accumulates column c of the RHS tile, so each entry (val, col) is
+// read once per tile and X's row slice is read as one contiguous segment.
+#include <algorithm>
+
+#include "accum.cuh"
+#include "internal.cuh"
+
+namespace gbsp {
+
+constexpr int kThreads = 256;
+
+template <int VM, int L, int R>
+__global__ void __launch_bounds__(kThreads)
+crs_vector_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
+                  const int32_t *__restrict__ col, const typename ValT<VM>::T *__restrict__ val,
+                  const typename ValT<VM>::T *__restrict__ x, int64_t ldx,
+                  typename ValT<VM>::T *__restrict__ y, int64_t ldy, int accumulate) {
+    typedef typename ValT<VM>::T T;
+    constexpr int G = 32 / L;
+    constexpr int RW = G * R;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / L, gl = lane % L;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * RW; base < n_rows; base += nwarp * RW) {
+        int k0[R], k1[R];
+        int len = 0;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int64_t r = base + i * G + grp;
+            k0[i] = 0;
+            k1[i] = 0;
+            if (r < n_rows) {
+                k0[i] = __ldg(row_ptr + r);
+                k1[i] = __ldg(row_ptr + r + 1);
+            }
+            len = max(len, k1[i] - k0[i]);
+        }
+        Acc<VM> acc[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) acc[i].init();
+        for (int j = gl; j < len; j += L) {
+            int c[R];
+            T v[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const int k = k0[i] + j;
+                const bool ok = k < k1[i];
+                c[i] = ok ? ld_stream(col + k) : -1;
+                v[i] = ok ? ld_stream(val + k) : T(0);
+            }
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+                if (c[i] >= 0) acc[i].add(v[i], ld_vec(x + (int64_t)c[i] * ldx));
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) group_reduce<L, VM>(acc[i]);
+        if (gl == 0) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const int64_t r = base + i * G + grp;
+                if (r < n_rows) {
+                    if (accumulate) acc[i].add_value(y[r * ldy]);
+                    y[r * ldy] = acc[i].result();
+                }
+            }
+        }
+    }
+}
+
+template <int VM, int KT>
+__global__ void __launch_bounds__(kThreads)
+crs_spmm_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
+                const int32_t *__restrict__ col, const typename ValT<VM>::T *__restrict__ val,
+                const typename ValT<VM>::T *__restrict__ X, int64_t ldx,
+                typename ValT<VM>::T *__restrict__ Y, int64_t ldy, int k, int c0, int accumulate) {
+    typedef typename ValT<VM>::T T;
+    constexpr int G = 32 / KT;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / KT, c = lane % KT;
+    const int cc = c0 + c;
+    const bool active = cc < k;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp * G + grp; r - grp < n_rows; r += nwarp * G) {
+        if (r >= n_rows) continue;
+        const int k0 = __ldg(row_ptr + r), k1 = __ldg(row_ptr + r + 1);
+        Acc<VM> acc;
+        acc.init();
+        int j = k0;
+        for (; j + 4 <= k1; j += 4) {
+            int ci[4];
+            T vi[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                ci[u] = __ldg(col + j + u);
+                vi[u] = __ldg(val + j + u);
+            }
+            if (active) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc.add(vi[u], ld_vec(X + (int64_t)ci[u] * ldx + cc));
+            }
+        }
+        for (; j < k1; ++j) {
+            const int ci = __ldg(col + j);
+            const T vi = __ldg(val + j);
+            if (active) acc.add(vi, ld_vec(X + (int64_t)ci * ldx + cc));
+        }
+        if (active) {
+            T *yp = Y + r * ldy + cc;
+            if (accumulate) acc.add_value(*yp);
+            *yp = acc.result();
+        }
+    }
+}
+
+// dval_k (+)= sum_{t<m} G[row_k, t] X[col_k, t]  (m = 1: g[row] x[col]).
+template <typename T, int L>
+__global__ void __launch_bounds__(kThreads)
+crs_dval_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
+                const int32_t *__restrict__ col, int m, const T *__restrict__ G, int64_t ldg,
+                const T *__restrict__ X, int64_t ldx, T *__restrict__ dval, int accumulate) {
+    constexpr int NG = 32 / L;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / L, gl = lane % L;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp * NG + grp; r - grp < n_rows; r += nwarp * NG) {
+        if (r >= n_rows) continue;
+        const int k0 = __ldg(row_ptr + r), k1 = __ldg(row_ptr + r + 1);
+        for (int kk = k0 + gl; kk < k1; kk += L) {
+            const int64_t cj = ld_stream(col + kk);
+            T s = T(0);
+            for (int t = 0; t < m; ++t) s = fma(__ldg(G + r * ldg + t), __ldg(X + cj * ldx + t), s);
+            dval[kk] = accumulate ? dval[kk] + s : s;
+        }
+    }
+}
+
+__global__ void crs_validate_kernel(int64_t n_rows, int64_t n_cols, int64_t nnz,
+                                    const int32_t *__restrict__ row_ptr,
+                                    const int32_t *__restrict__ col, int32_t *status) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false;
+    if (tid == 0 && (row_ptr[0] != 0 || (int64_t)row_ptr[n_rows] != nnz)) bad = true;
+    for (int64_t i = tid; i < n_rows; i += stride)
+        if (row_ptr[i + 1] < row_ptr[i]) bad = true;
+    for (int64_t k = tid; k < nnz; k += stride) {
+        const int32_t c = col[k];
+        if (c < 0 || (int64_t)c >= n_cols) bad = true;
+    }
+    if (bad) *status = (int32_t)GBSP_ERR_MATRIX;
+}
+
+// ------------------------------------------------------------------ host --
+
+static int grid_for(int64_t warps_needed) {
+    const int64_t blocks = ceil_div(warps_needed, kThreads / 32);
+    const int64_t cap = (int64_t)num_sms() * 8 * 4;  // four waves of full occupancy
+    return (int)std::max<int64_t>(1, std::min(blocks, cap));
+}
+
+template <int VM, int L>
+static void launch_vector_R(const Mat &A, const VecArgs &v, int R, cudaStream_t s) {
+    typedef typename ValT<VM>::T T;
+    const int64_t rw = (32 / L) * R;
+    const int grid = grid_for(ceil_div(A.n_rows, rw));
+    auto *val = static_cast<const T *>(A.val);
+    auto *x = static_cast<const T *>(v.x);
+    auto *y = static_cast<T *>(v.y);
+    switch (R) {
+        case 1:
+            crs_vector_kernel<VM, L, 1><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, val, x,
+                                                                  v.ldx, y, v.ldy, v.accumulate);
+            break;
+        case 2:
+            crs_vector_kernel<VM, L, 2><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, val, x,
+                                                                  v.ldx, y, v.ldy, v.accumulate);
+            break;
+        default:
+            crs_vector_kernel<VM, L, 4><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, val, x,
+                                                                  v.ldx, y, v.ldy, v.accumulate);
+            break;
+    }
+}
+
+template <int VM>
+static void launch_vector(const Mat &A, const VecArgs &v, cudaStream_t s) {
+    const int R = A.kopt.rows_per_warp;
+    switch (A.kopt.lanes) {
+        case 1: launch_vector_R<VM, 1>(A, v, R, s); break;
+        case 2: launch_vector_R<VM, 2>(A, v, R, s); break;
+        case 4: launch_vector_R<VM, 4>(A, v, R, s); break;
+        case 8: launch_vector_R<VM, 8>(A, v, R, s); break;
+        case 16: launch_vector_R<VM, 16>(A, v, R, s); break;
+        default: launch_vector_R<VM, 32>(A, v, R, s); break;
+    }
+}
+
+template <int VM>
+static void launch_spmm(const Mat &A, const VecArgs &v, cudaStream_t s) {
+    typedef typename ValT<VM>::T T;
+    int kt = A.kopt.rhs_tile > 0 ? A.kopt.rhs_tile : 16;
+    kt = std::min(kt, 32);
+    // lanes per row: the power of two covering min(k, tile)
+    int cols = std::min<int>(v.k, kt);
+    int KT = 2;
+    while (KT < cols) KT <<= 1;
+    auto *val = static_cast<const T *>(A.val);
+    auto *X = static_cast<const T *>(v.x);
+    auto *Y = static_cast<T *>(v.y);
+    const int grid = grid_for(ceil_div(A.n_rows, 32 / KT));
+    for (int c0 = 0; c0 < v.k; c0 += KT) {
+        switch (KT) {
+            case 2:
+                crs_spmm_kernel<VM, 2><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, val, X,
+                                                                 v.ldx, Y, v.ldy, v.k, c0, v.accumulate);
+                break;
+            case 4:
+                crs_spmm_kernel<VM, 4><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, val, X,
+                                                                 v.ldx, Y, v.ldy, v.k, c0, v.accumulate);
+                break;
+            case 8:
+                crs_spmm_kernel<VM, 8><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, val, X,
+                                                                 v.ldx, Y, v.ldy, v.k, c0, v.accumulate);
+                break;
+            case 16:
+                crs_spmm_kernel<VM, 16><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, val, X,
+                                                                  v.ldx, Y, v.ldy, v.k, c0, v.accumulate);
+                break;
+            default:
+                crs_spmm_kernel<VM, 32><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, val, X,
+                                                                  v.ldx, Y, v.ldy, v.k, c0, v.accumulate);
+                break;
+        }
+    }
+}
+
+void crs_default_opts(Mat &A) {
+    const double mean = A.n_rows > 0 ? (double)A.nnz / (double)A.n_rows : 0.0;
+    int lanes = 1;
+    while (lanes < 32 && lanes < mean) lanes <<= 1;
+    if (lanes > 1 && lanes >= 2 * mean) lanes >>= 1;
+    A.kopt.kernel = GBSP_KERNEL_VECTOR;
+    A.kopt.lanes = lanes;
+    A.kopt.rows_per_warp = lanes >= 16 ? 2 : 4;
+    A.kopt.tile = 2048;
+    A.kopt.rhs_tile = 16;
+    A.kopt.accum = A.dtype == GBSP_F32 ? GBSP_ACC_COMPENSATED : GBSP_ACC_PLAIN;
+}
+
+gbsp_status crs_tiled_launch(const Mat &A, const VecArgs &v, cudaStream_t s);
+
+gbsp_status crs_launch(const Mat &A, const VecArgs &v, cudaStream_t s) {
+    if (A.n_rows == 0) return GBSP_OK;
+    const int vm = A.dtype == GBSP_F64 ? VM_F64
+                   : (A.kopt.accum == GBSP_ACC_COMPENSATED ? VM_F32C : VM_F32);
+    if (v.k == 1 && A.kopt.kernel == GBSP_KERNEL_TILED && A.tile_rows != nullptr)
+        return crs_tiled_launch(A, v, s);
+    if (v.k == 1) {
+        if (vm == VM_F64) launch_vector<VM_F64>(A, v, s);
+        else if (vm == VM_F32) launch_vector<VM_F32>(A, v, s);
+        else launch_vector<VM_F32C>(A, v, s);
+    } else {
+        if (vm == VM_F64) launch_spmm<VM_F64>(A, v, s);
+        else if (vm == VM_F32) launch_spmm<VM_F32>(A, v, s);
+        else launch_spmm<VM_F32C>(A, v, s);
+    }
+    GBSP_LAUNCH_CHECK("crs product kernel");
+    return GBSP_OK;
+}
+
+gbsp_status crs_validate_launch(const Mat &A, int32_t *d_status, cudaStream_t s) {
+    GBSP_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int32_t), s));
+    const int64_t work = std::max(A.n_rows, A.nnz);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, kThreads),
+                                                                 (int64_t)num_sms() * 8));
+    crs_validate_kernel<<<grid, kThreads, 0, s>>>(A.n_rows, A.n_cols, A.nnz, A.row_ptr, A.col,
+                                                  d_status);
+    GBSP_LAUNCH_CHECK("crs_validate_kernel");
+    return GBSP_OK;
+}
+
+template <typename T>
+static void launch_dval(const Mat &A, int32_t m, const void *G, int64_t ldg, const void *X,
+                        int64_t ldx, void *dval, int32_t accumulate, cudaStream_t s) {
+    const int L = A.kopt.lanes >= 8 ? 8 : (A.kopt.lanes >= 4 ? 4 : 1);
+    const int grid = grid_for(ceil_div(A.n_rows, 32 / L));
+    auto *g = static_cast<const T *>(G);
+    auto *x = static_cast<const T *>(X);
+    auto *d = static_cast<T *>(dval);
+    if (L == 8)
+        crs_dval_kernel<T, 8><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, m, g, ldg, x,
+                                                        ldx, d, accumulate);
+    else if (L == 4)
+        crs_dval_kernel<T, 4><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, m, g, ldg, x,
+                                                        ldx, d, accumulate);
+    else
+        crs_dval_kernel<T, 1><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, m, g, ldg, x,
+                                                        ldx, d, accumulate);
+}
+
+gbsp_status crs_dval_launch(const Mat &A, int32_t m, const void *G, int64_t ldg, const void *X,
+                            int64_t ldx, void *dval, int32_t accumulate, cudaStream_t s) {
+    if (A.n_rows == 0 || A.nnz == 0) return GBSP_OK;
+    if (A.dtype == GBSP_F64) launch_dval<double>(A, m, G, ldg, X, ldx, dval, accumulate, s);
+    else launch_dval<float>(A, m, G, ldg, X, ldx, dval, accumulate, s);
+    GBSP_LAUNCH_CHECK("crs_dval_kernel");
+    return GBSP_OK;
+}
+
+}  // namespace gbsp

@@ -1,0 +1,121 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/gbspmv.h"
+
+namespace gbsp {
+
+enum HandleKind { KIND_CRS = 0, KIND_JDS = 1 };
+
+struct Mat {
+    int kind = KIND_CRS;
+    int64_t n_rows = 0, n_cols = 0, nnz = 0;
+    int dtype = GBSP_F64;
+    int device = 0;
+
+    // CRS arrays (CRS handles) / col+val in storage order (JDS handles)
+    const int32_t *row_ptr = nullptr;
+    const int32_t *col = nullptr;
+    const void *val = nullptr;
+
+    // kernel options
+    gbsp_kernel_opts kopt{};
+
+    // TILED CRS tile table
+    const int32_t *tile_rows = nullptr;
+    int64_t n_tiles = 0;
+    int32_t tile = 0;
+
+    // JDS family
+    int format = GBSP_CRS;
+    int perm_mode = GBSP_PERM_SYMMETRIC;
+    int32_t block = 0, unroll = 0;
+    int32_t built_block = 0;  // block size the RBJDS/SOJDS layout was built with
+    int64_t n_diag = 0, n_blocks = 0;
+    const int32_t *jd_ptr = nullptr, *perm = nullptr, *iperm = nullptr, *blk_ptr = nullptr;
+    std::vector<int32_t> h_jd_ptr;  // host copy, read back once at build (literal launches)
+
+    // transposed structure (CRS handle built by gbsp_transpose_build)
+    const int32_t *tmap = nullptr;  // set on the transpose handle itself
+    const Mat *transpose_src = nullptr;  // the CRS this transpose was built from
+    Mat *transpose = nullptr;        // attached handle used for OP_T
+    bool owns_transpose = false;
+};
+
+// error reporting ---------------------------------------------------------
+void set_error(const char *fmt, ...);
+gbsp_status cuda_status(cudaError_t e, const char *what);
+
+#define GBSP_CUDA(call)                                             \
+    do {                                                            \
+        cudaError_t e__ = (call);                                   \
+        if (e__ != cudaSuccess) return gbsp::cuda_status(e__, #call); \
+    } while (0)
+
+#define GBSP_LAUNCH_CHECK(what)                                          \
+    do {                                                                 \
+        cudaError_t e__ = cudaGetLastError();                            \
+        if (e__ != cudaSuccess) return gbsp::cuda_status(e__, what);     \
+    } while (0)
+
+inline gbsp_status arg_error(const char *msg) {
+    set_error("%s", msg);
+    return GBSP_ERR_ARG;
+}
+
+inline int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+    }
+    return sms;
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// launchers implemented in crs.cu -----------------------------------------
+struct VecArgs {
+    const void *x;
+    void *y;
+    int64_t ldx, ldy;   // row-major leading dims (1 for plain vectors)
+    int32_t k;          // right-hand sides
+    int32_t accumulate;
+    const int32_t *x_perm;   // optional: x index = x_perm[col]
+    const int32_t *y_perm;   // optional: y row = y_perm[row]
+};
+
+gbsp_status crs_launch(const Mat &A, const VecArgs &v, cudaStream_t s);
+gbsp_status crs_prepare_tiles(Mat &A, int32_t tile, int32_t *table, cudaStream_t s);
+gbsp_status crs_validate_launch(const Mat &A, int32_t *d_status, cudaStream_t s);
+gbsp_status crs_dval_launch(const Mat &A, int32_t m, const void *G, int64_t ldg, const void *X,
+                            int64_t ldx, void *dval, int32_t accumulate, cudaStream_t s);
+void crs_default_opts(Mat &A);
+
+// jds.cu ----------------------------------------------------------------
+gbsp_status jds_launch(const Mat &A, const VecArgs &v, cudaStream_t s);
+gbsp_status permute_launch(const Mat &A, int32_t dir, int32_t k, const void *in, int64_t ld_in,
+                           void *out, int64_t ld_out, cudaStream_t s);
+
+// convert.cu ------------------------------------------------------------
+gbsp_status jds_plan_impl(const Mat &A, const gbsp_jds_opts &o, int32_t *d_scratch,
+                          cudaStream_t s, gbsp_jds_sizes *out);
+gbsp_status jds_build_impl(const Mat &A, const gbsp_jds_opts &o, const gbsp_jds_buffers &b,
+                           const gbsp_jds_sizes &sz, cudaStream_t s, Mat *J);
+gbsp_status transpose_workspace_impl(const Mat &A, int64_t *bytes);
+gbsp_status transpose_build_impl(const Mat &A, const gbsp_transpose_buffers &b, int64_t ws_bytes,
+                                 cudaStream_t s, Mat *T);
+gbsp_status transpose_values_impl(const Mat &T, cudaStream_t s);
+
+}  // namespace gbsp
+
+struct gbsp_mat : gbsp::Mat {};

@@ -1,0 +1,312 @@
+// JDS-family products (Sect. 2, JDS kernel and its refinements).
+//
+// Storage: jagged diagonal d holds permuted rows 0 .. diagLen(d)-1 at
+// positions jd_ptr[d] + r, so a warp of consecutive rows reads each diagonal
+// as one contiguous segment.  Every kernel below gives each thread whole
+// rows and adds a row's entries in slot order d = 0, 1, ... with an FMA
+// chain starting from zero, so all JDS-family kernels return bit-identical
+// results for the same storage pattern.
+//
+//   JDS_LITERAL  one launch per jagged diagonal; resvec makes a round trip
+//                through memory per diagonal, as the paper's loop does.
+//   JDS          one thread per row walks the diagonals; resvec stays in a
+//                register (written once).
+//   NUJDS        the same walk, u diagonals per step: the u loads of a step
+//                are issued together (outer-loop unrolling, Sect. 2).
+//   NBJDS        a CTA owns a block of `block` rows and walks only the
+//                diagonals that have entries in it, each thread holding R
+//                rows' sums in registers (blocking, Sect. 2).
+//   RBJDS/SOJDS  like NBJDS, but the block's entries are stored
+//                consecutively (diagonal-major inside the block), so a CTA
+//                streams one contiguous chunk.
+#include <algorithm>
+#include <vector>
+
+#include "accum.cuh"
+#include "internal.cuh"
+
+namespace gbsp {
+
+struct JdsArgs {
+    int64_t n_rows, n_diag;
+    const int32_t *jd_ptr, *col, *blk_ptr;
+    const void *val;
+    const void *x;
+    void *y;
+    int64_t ldx, ldy;
+    int32_t k, c0;
+    int32_t accumulate;
+    int32_t block;
+    const int32_t *x_perm;  // x index = x_perm[col] (ORIGINAL basis, symmetric storage)
+    const int32_t *y_perm;  // y row = y_perm[r]      (ORIGINAL basis)
+};
+
+__device__ __forceinline__ int64_t xidx(const int32_t *x_perm, int32_t c) {
+    return x_perm ? (int64_t)__ldg(x_perm + c) : (int64_t)c;
+}
+
+template <int VM>
+__device__ __forceinline__ void store_row(const JdsArgs &a, int64_t r, int c, Acc<VM> &acc) {
+    typedef typename ValT<VM>::T T;
+    const int64_t row = a.y_perm ? (int64_t)__ldg(a.y_perm + r) : r;
+    T *yp = static_cast<T *>(a.y) + row * a.ldy + c;
+    if (a.accumulate) acc.add_value(*yp);
+    *yp = acc.result();
+}
+
+// JDS (U = 1) and NUJDS (U > 1): one thread per permuted row.
+template <int VM, int U>
+__global__ void __launch_bounds__(256) jds_row_kernel(JdsArgs a) {
+    typedef typename ValT<VM>::T T;
+    const T *__restrict__ val = static_cast<const T *>(a.val);
+    const T *__restrict__ x = static_cast<const T *>(a.x);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.n_rows; r += stride) {
+        Acc<VM> acc;
+        acc.init();
+        int32_t st = __ldg(a.jd_ptr);
+        for (int64_t d0 = 0; d0 < a.n_diag; d0 += U) {
+            int32_t e[U + 1];
+            e[0] = st;
+#pragma unroll
+            for (int j = 0; j < U; ++j)
+                e[j + 1] = (d0 + j < a.n_diag) ? __ldg(a.jd_ptr + d0 + j + 1) : e[j];
+            if (e[1] - e[0] <= r) break;  // row r has no entry in diagonal d0
+            int c[U];
+            T v[U];
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const bool ok = e[j + 1] - e[j] > r;
+                c[j] = ok ? ld_stream(a.col + e[j] + r) : -1;
+                v[j] = ok ? ld_stream(val + e[j] + r) : T(0);
+            }
+#pragma unroll
+            for (int j = 0; j < U; ++j)
+                if (c[j] >= 0) acc.add(v[j], ld_vec(x + xidx(a.x_perm, c[j]) * a.ldx));
+            st = e[U];
+        }
+        store_row<VM>(a, r, 0, acc);
+    }
+}
+
+// NBJDS (CONTIG = false) and RBJDS / SOJDS (CONTIG = true): a CTA per row
+// block, R rows per thread in flight; KT > 1 gives KT right-hand sides per
+// thread (SpMM, then R = 1).
+template <int VM, bool CONTIG, int R, int KT>
+__global__ void __launch_bounds__(256) jds_block_kernel(JdsArgs a) {
+    typedef typename ValT<VM>::T T;
+    const T *__restrict__ val = static_cast<const T *>(a.val);
+    const T *__restrict__ x = static_cast<const T *>(a.x);
+    const int64_t n_blocks = ceil_div_dev(a.n_rows, a.block);
+    for (int64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
+        const int64_t b0 = blk * a.block;
+        const int64_t b1 = min(b0 + (int64_t)a.block, a.n_rows);
+        const int64_t cbase = CONTIG ? (int64_t)__ldg(a.blk_ptr + blk) : 0;
+        for (int64_t c0 = b0; c0 < b1; c0 += (int64_t)blockDim.x * R) {
+            int64_t rr[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) rr[i] = c0 + threadIdx.x + (int64_t)i * blockDim.x;
+            Acc<VM> acc[R][KT];
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+#pragma unroll
+                for (int q = 0; q < KT; ++q) acc[i][q].init();
+            int32_t st = __ldg(a.jd_ptr);
+            int64_t off = cbase;
+            for (int64_t d = 0; d < a.n_diag; ++d) {
+                const int32_t en = __ldg(a.jd_ptr + d + 1);
+                const int64_t dl = en - st;
+                if (dl <= b0) break;  // no entries of this block in diagonal d
+                int c[R];
+                T v[R];
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const bool ok = rr[i] < b1 && rr[i] < dl;
+                    const int64_t kk = CONTIG ? off + (rr[i] - b0) : (int64_t)st + rr[i];
+                    c[i] = ok ? ld_stream(a.col + kk) : -1;
+                    v[i] = ok ? ld_stream(val + kk) : T(0);
+                }
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    if (c[i] < 0) continue;
+                    const T *xr = x + xidx(a.x_perm, c[i]) * a.ldx + a.c0;
+#pragma unroll
+                    for (int q = 0; q < KT; ++q)
+                        if (KT == 1 || a.c0 + q < a.k) acc[i][q].add(v[i], ld_vec(xr + q));
+                }
+                if (CONTIG) off += min(b1, dl) - b0;
+                st = en;
+            }
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                if (rr[i] >= b1) continue;
+#pragma unroll
+                for (int q = 0; q < KT; ++q)
+                    if (KT == 1 || a.c0 + q < a.k) store_row<VM>(a, rr[i], a.c0 + q, acc[i][q]);
+            }
+        }
+    }
+}
+
+// JDS_LITERAL: the paper's loop, one launch per diagonal d:
+//   resvec(i) = resvec(i) + val(off+i) * invec(col_idx(off+i)), i < diagLen(d).
+template <typename T>
+__global__ void jds_literal_kernel(int64_t len, int32_t off, const int32_t *__restrict__ col,
+                                   const T *__restrict__ val, const T *__restrict__ x, int64_t ldx,
+                                   T *__restrict__ y, int64_t ldy, const int32_t *x_perm,
+                                   const int32_t *y_perm) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    const int64_t row = y_perm ? (int64_t)__ldg(y_perm + i) : i;
+    T *yp = y + row * ldy;
+    *yp = fma(ld_stream(val + off + i), ld_vec(x + xidx(x_perm, ld_stream(col + off + i)) * ldx), *yp);
+}
+
+template <typename T>
+__global__ void zero_rows_kernel(int64_t n, T *y, int64_t ldy, int k) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * k) return;
+    y[(i / k) * ldy + (i % k)] = T(0);
+}
+
+// Basis change: dir 0 out[r] = in[perm[r]], dir 1 out[perm[r]] = in[r].
+template <typename T>
+__global__ void permute_kernel(int64_t n, int k, const int32_t *__restrict__ perm, int dir,
+                               const T *__restrict__ in, int64_t ld_in, T *__restrict__ out,
+                               int64_t ld_out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * k) return;
+    const int64_t r = i / k, c = i % k;
+    const int64_t p = __ldg(perm + r);
+    if (dir == 0) out[r * ld_out + c] = in[p * ld_in + c];
+    else out[p * ld_out + c] = in[r * ld_in + c];
+}
+
+// ------------------------------------------------------------------ host --
+
+static int row_grid(int64_t rows) {
+    const int64_t blocks = ceil_div(rows, 256);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)num_sms() * 8 * 16));
+}
+
+template <int VM, int U>
+static void launch_row(const JdsArgs &a, cudaStream_t s) {
+    jds_row_kernel<VM, U><<<row_grid(a.n_rows), 256, 0, s>>>(a);
+}
+
+template <int VM, bool CONTIG>
+static void launch_block(const JdsArgs &a, int KT, cudaStream_t s) {
+    const int64_t nb = ceil_div(a.n_rows, a.block);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)num_sms() * 8 * 16));
+    // CTA width: the block size rounded up to a warp, at most 256 threads
+    const int threads = (int)std::min<int64_t>(256, std::max<int64_t>(32, ceil_div(a.block, 32) * 32));
+    if (KT > 1) {
+        switch (KT) {
+            case 2: jds_block_kernel<VM, CONTIG, 1, 2><<<grid, threads, 0, s>>>(a); break;
+            case 4: jds_block_kernel<VM, CONTIG, 1, 4><<<grid, threads, 0, s>>>(a); break;
+            case 8: jds_block_kernel<VM, CONTIG, 1, 8><<<grid, threads, 0, s>>>(a); break;
+            default: jds_block_kernel<VM, CONTIG, 1, 16><<<grid, threads, 0, s>>>(a); break;
+        }
+        return;
+    }
+    const int64_t R = std::min<int64_t>(8, ceil_div(a.block, threads));
+    if (R <= 1) jds_block_kernel<VM, CONTIG, 1, 1><<<grid, threads, 0, s>>>(a);
+    else if (R <= 2) jds_block_kernel<VM, CONTIG, 2, 1><<<grid, threads, 0, s>>>(a);
+    else if (R <= 4) jds_block_kernel<VM, CONTIG, 4, 1><<<grid, threads, 0, s>>>(a);
+    else jds_block_kernel<VM, CONTIG, 8, 1><<<grid, threads, 0, s>>>(a);
+}
+
+template <int VM>
+static gbsp_status launch_family(const Mat &A, JdsArgs a, cudaStream_t s) {
+    typedef typename ValT<VM>::T T;
+    const int fmt = A.format;
+    if (a.k > 1 || fmt == GBSP_NBJDS || fmt == GBSP_RBJDS || fmt == GBSP_SOJDS) {
+        const bool contig = fmt == GBSP_RBJDS || fmt == GBSP_SOJDS;
+        if (!contig && fmt != GBSP_NBJDS) a.block = 256;  // JDS / NUJDS walked per 256-row block
+        int KT = 1;
+        if (a.k > 1) {
+            const int tile = A.kopt.rhs_tile > 0 ? std::min(A.kopt.rhs_tile, 16) : 16;
+            const int cols = std::min(a.k, tile);
+            KT = 2;
+            while (KT < cols) KT <<= 1;
+        }
+        for (int c0 = 0; c0 < a.k; c0 += KT) {
+            a.c0 = c0;
+            if (contig) launch_block<VM, true>(a, KT, s);
+            else launch_block<VM, false>(a, KT, s);
+        }
+        return GBSP_OK;
+    }
+    if (fmt == GBSP_JDS_LITERAL) {
+        if (!a.accumulate) {
+            // resvec starts at zero; rows are written through y_perm's image,
+            // which is every row, so zero the whole output
+            const int64_t n = a.n_rows;
+            zero_rows_kernel<T><<<(unsigned)ceil_div(std::max<int64_t>(n, 1), 256), 256, 0, s>>>(
+                n, static_cast<T *>(a.y), a.ldy, 1);
+        }
+        for (int64_t d = 0; d < A.n_diag; ++d) {
+            const int64_t len = A.h_jd_ptr[d + 1] - A.h_jd_ptr[d];
+            if (len <= 0) break;
+            jds_literal_kernel<T><<<(unsigned)ceil_div(len, 256), 256, 0, s>>>(
+                len, A.h_jd_ptr[d], a.col, static_cast<const T *>(a.val), static_cast<const T *>(a.x),
+                a.ldx, static_cast<T *>(a.y), a.ldy, a.x_perm, a.y_perm);
+        }
+        return GBSP_OK;
+    }
+    const int u = fmt == GBSP_NUJDS ? A.unroll : 1;
+    if (u <= 1) launch_row<VM, 1>(a, s);
+    else if (u <= 2) launch_row<VM, 2>(a, s);
+    else if (u <= 4) launch_row<VM, 4>(a, s);
+    else if (u <= 8) launch_row<VM, 8>(a, s);
+    else launch_row<VM, 16>(a, s);
+    return GBSP_OK;
+}
+
+gbsp_status jds_launch(const Mat &A, const VecArgs &v, cudaStream_t s) {
+    if (A.n_rows == 0) return GBSP_OK;
+    JdsArgs a{};
+    a.n_rows = A.n_rows;
+    a.n_diag = A.n_diag;
+    a.jd_ptr = A.jd_ptr;
+    a.col = A.col;
+    a.blk_ptr = A.blk_ptr;
+    a.val = A.val;
+    a.x = v.x;
+    a.y = v.y;
+    a.ldx = v.ldx;
+    a.ldy = v.ldy;
+    a.k = v.k;
+    a.c0 = 0;
+    a.accumulate = v.accumulate;
+    a.block = A.format == GBSP_RBJDS || A.format == GBSP_SOJDS ? A.built_block
+                                                                 : std::max(A.block, 1);
+    a.x_perm = v.x_perm;
+    a.y_perm = v.y_perm;
+    gbsp_status st;
+    if (A.dtype == GBSP_F64) st = launch_family<VM_F64>(A, a, s);
+    else if (A.kopt.accum == GBSP_ACC_COMPENSATED) st = launch_family<VM_F32C>(A, a, s);
+    else st = launch_family<VM_F32>(A, a, s);
+    if (st != GBSP_OK) return st;
+    GBSP_LAUNCH_CHECK("jds product kernel");
+    return GBSP_OK;
+}
+
+gbsp_status permute_launch(const Mat &A, int32_t dir, int32_t k, const void *in, int64_t ld_in,
+                           void *out, int64_t ld_out, cudaStream_t s) {
+    const int64_t n = A.n_rows * (int64_t)k;
+    if (n == 0) return GBSP_OK;
+    const unsigned grid = (unsigned)ceil_div(n, 256);
+    if (A.dtype == GBSP_F64)
+        permute_kernel<double><<<grid, 256, 0, s>>>(A.n_rows, k, A.perm, dir,
+                                                    static_cast<const double *>(in), ld_in,
+                                                    static_cast<double *>(out), ld_out);
+    else
+        permute_kernel<float><<<grid, 256, 0, s>>>(A.n_rows, k, A.perm, dir,
+                                                   static_cast<const float *>(in), ld_in,
+                                                   static_cast<float *>(out), ld_out);
+    GBSP_LAUNCH_CHECK("permute_kernel");
+    return GBSP_OK;
+}
+
+}  // namespace gbsp

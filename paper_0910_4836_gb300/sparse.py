@@ -1,0 +1,293 @@
+"""Python classes over the C ABI (argument marshalling only).
+
+Every product, conversion and gradient runs in the CUDA library; these
+classes only allocate device memory with torch, keep the borrowed tensors
+alive for as long as the C handles use them, and pass pointers and the
+current torch stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib as L
+
+_DT = {torch.float64: L.F64, torch.float32: L.F32}
+
+
+def _vp(t: torch.Tensor | None) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream: torch.cuda.Stream | None = None) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need_cuda(t: torch.Tensor, name: str, dtype=None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    return t.contiguous()
+
+
+def _ld(t: torch.Tensor) -> int:
+    return t.stride(0) if t.dim() == 2 else 1
+
+
+class _Handle:
+    """Owns one C handle; destroyed with the Python object."""
+
+    def __init__(self):
+        self._h = ctypes.c_void_p()
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def __del__(self):
+        try:
+            if self._h:
+                L.load().gbsp_destroy(self._h)
+                self._h = ctypes.c_void_p()
+        except Exception:
+            pass
+
+
+class _Product(_Handle):
+    n_rows: int
+    n_cols: int
+    dtype: torch.dtype
+
+    def _vec_out(self, rows: int, k: int | None, like: torch.Tensor) -> torch.Tensor:
+        shape = (rows,) if k is None else (rows, k)
+        return torch.empty(shape, dtype=self.dtype, device=like.device)
+
+    def spmm(self, X: torch.Tensor, out: torch.Tensor | None = None, accumulate: bool = False,
+             transpose: bool = False, basis: int = L.BASIS_PERMUTED, stream=None) -> torch.Tensor:
+        """Y = op(A) X for row-major X (n x k); a 1-D X is a single vector."""
+        if not X.is_cuda or X.dtype != self.dtype:
+            raise ValueError(f"X must be a CUDA tensor of dtype {self.dtype}")
+        if X.dim() == 1 or X.stride(-1) != 1:
+            X = X.contiguous()
+        vec = X.dim() == 1
+        k = 1 if vec else X.shape[1]
+        rows_in, rows_out = (self.n_rows, self.n_cols) if transpose else (self.n_cols, self.n_rows)
+        if X.shape[0] != rows_in:
+            raise ValueError(f"x has {X.shape[0]} rows, expected {rows_in}")
+        if out is None:
+            out = (torch.zeros if accumulate else torch.empty)(
+                (rows_out,) if vec else (rows_out, k), dtype=self.dtype, device=X.device)
+        elif out.shape[0] != rows_out or out.dtype != self.dtype:
+            raise ValueError("out has the wrong shape or dtype")
+        L.check(L.load().gbsp_spmm(self._h, L.OP_T if transpose else L.OP_N, basis, k, _vp(X),
+                                   _ld(X), _vp(out), _ld(out), int(accumulate), _stream(stream)),
+                "gbsp_spmm")
+        return out
+
+    def spmv(self, x: torch.Tensor, out: torch.Tensor | None = None, accumulate: bool = False,
+             transpose: bool = False, basis: int = L.BASIS_PERMUTED, stream=None) -> torch.Tensor:
+        """y = op(A) x (or y += op(A) x)."""
+        if x.dim() != 1:
+            raise ValueError("spmv takes a 1-D vector; use spmm for several")
+        return self.spmm(x, out, accumulate, transpose, basis, stream)
+
+    def set_kernel(self, kernel: str = "vector", lanes: int = 0, rows_per_warp: int = 0,
+                   tile: int = 0, rhs_tile: int = 0, compensated: bool | None = None) -> None:
+        o = L.KernelOpts()
+        L.check(L.load().gbsp_get_kernel(self._h, ctypes.byref(o)), "gbsp_get_kernel")
+        accum = o.accum if compensated is None else (L.ACC_COMPENSATED if compensated else L.ACC_PLAIN)
+        o = L.KernelOpts(L.KERNELS[kernel], lanes, rows_per_warp, tile, rhs_tile, accum)
+        L.check(L.load().gbsp_set_kernel(self._h, ctypes.byref(o)), "gbsp_set_kernel")
+
+    def kernel_opts(self) -> dict:
+        o = L.KernelOpts()
+        L.check(L.load().gbsp_get_kernel(self._h, ctypes.byref(o)), "gbsp_get_kernel")
+        return {f: getattr(o, f) for f, _ in L.KernelOpts._fields_}
+
+    def autotune(self, k: int = 1, stream=None) -> tuple[dict, float]:
+        """Time the candidate kernels on this matrix and keep the fastest."""
+        dev = self._device
+        X = torch.zeros((self.n_cols,) if k == 1 else (self.n_cols, k), dtype=self.dtype, device=dev)
+        Y = torch.zeros((self.n_rows,) if k == 1 else (self.n_rows, k), dtype=self.dtype, device=dev)
+        best = L.KernelOpts()
+        ms = ctypes.c_float()
+        L.check(L.load().gbsp_autotune(self._h, k, _vp(X), _vp(Y), _stream(stream),
+                                       ctypes.byref(best), ctypes.byref(ms)), "gbsp_autotune")
+        return {f: getattr(best, f) for f, _ in L.KernelOpts._fields_}, ms.value
+
+
+class CRSMatrix(_Product):
+    """A CRS matrix on the GPU (Sect. 2): row_ptr (int32, n_rows+1), col
+    (int32, nnz), val (float64 or float32, nnz), all borrowed by the C
+    handle and kept alive here."""
+
+    def __init__(self, row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, n_cols: int):
+        super().__init__()
+        self.row_ptr = _need_cuda(row_ptr, "row_ptr", torch.int32)
+        self.col = _need_cuda(col, "col", torch.int32)
+        self.val = _need_cuda(val, "val")
+        if self.val.dtype not in _DT:
+            raise ValueError("val must be float64 or float32")
+        self.dtype = self.val.dtype
+        self.n_rows = self.row_ptr.numel() - 1
+        self.n_cols = int(n_cols)
+        self.nnz = self.col.numel()
+        if self.val.numel() != self.nnz:
+            raise ValueError("col and val lengths differ")
+        self._device = self.row_ptr.device
+        self._tile_table = None
+        self._transpose = None
+        self._tbufs = None
+        L.check(L.load().gbsp_crs_create(self.n_rows, self.n_cols, self.nnz, _vp(self.row_ptr),
+                                         _vp(self.col), _vp(self.val), _DT[self.dtype],
+                                         ctypes.byref(self._h)), "gbsp_crs_create")
+
+    @classmethod
+    def from_host(cls, A, device="cuda", dtype=torch.float64) -> "CRSMatrix":
+        """From any object with n_rows, n_cols, row_ptr, col, val (numpy)."""
+        return cls(torch.as_tensor(A.row_ptr, dtype=torch.int32).to(device),
+                   torch.as_tensor(A.col, dtype=torch.int32).to(device),
+                   torch.as_tensor(A.val).to(device=device, dtype=dtype), A.n_cols)
+
+    def validate(self, stream=None) -> int:
+        """0 if the CRS arrays are well formed, else GBSP_ERR_MATRIX (-2)."""
+        st = torch.empty(1, dtype=torch.int32, device=self._device)
+        L.check(L.load().gbsp_crs_validate(self._h, _vp(st), _stream(stream)), "gbsp_crs_validate")
+        out = ctypes.c_int32()
+        L.check(L.load().gbsp_read_status(_vp(st), _stream(stream), ctypes.byref(out)),
+                "gbsp_read_status")
+        return out.value
+
+    def prepare_tiled(self, tile: int = 2048, stream=None) -> None:
+        """Build the tile table of the TILED kernel and select that kernel."""
+        nb = ctypes.c_int64()
+        L.check(L.load().gbsp_crs_tile_bytes(self._h, tile, ctypes.byref(nb)), "gbsp_crs_tile_bytes")
+        self._tile_table = torch.empty(nb.value // 4, dtype=torch.int32, device=self._device)
+        L.check(L.load().gbsp_crs_prepare(self._h, tile, _vp(self._tile_table), nb.value,
+                                          _stream(stream)), "gbsp_crs_prepare")
+        self.set_kernel("tiled")
+
+    def to_jds(self, fmt: str = "JDS", perm: str = "symmetric", block: int = 256, unroll: int = 4,
+               stream=None) -> "JDSMatrix":
+        return JDSMatrix(self, fmt, perm, block, unroll, stream)
+
+    def transpose(self, stream=None) -> "CRSMatrix":
+        """Build the transposed structure (a CRS of A^T with its entry map)
+        and attach it, so spmv(..., transpose=True) computes A^T g."""
+        lib = L.load()
+        dev = self._device
+        ws = ctypes.c_int64()
+        L.check(lib.gbsp_transpose_workspace(self._h, ctypes.byref(ws)), "gbsp_transpose_workspace")
+        t_row_ptr = torch.empty(self.n_cols + 1, dtype=torch.int32, device=dev)
+        t_col = torch.empty(self.nnz, dtype=torch.int32, device=dev)
+        t_val = torch.empty(self.nnz, dtype=self.dtype, device=dev)
+        tmap = torch.empty(self.nnz, dtype=torch.int32, device=dev)
+        work = torch.empty(max(ws.value, 1), dtype=torch.uint8, device=dev)
+        bufs = L.TransposeBuffers(_vp(t_row_ptr).value, _vp(t_col).value, _vp(t_val).value,
+                                  _vp(tmap).value, _vp(work).value)
+        T = CRSMatrix.__new__(CRSMatrix)
+        _Handle.__init__(T)
+        L.check(lib.gbsp_transpose_build(self._h, ctypes.byref(bufs), ws.value, _stream(stream),
+                                         ctypes.byref(T._h)), "gbsp_transpose_build")
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        del work
+        T.row_ptr, T.col, T.val, T.tmap = t_row_ptr, t_col, t_val, tmap
+        T.dtype, T.n_rows, T.n_cols, T.nnz = self.dtype, self.n_cols, self.n_rows, self.nnz
+        T._device, T._tile_table, T._transpose, T._tbufs = dev, None, None, None
+        T._source = self
+        self._transpose = T
+        return T
+
+    def attach_transpose(self, at: "_Product") -> None:
+        L.check(L.load().gbsp_attach_transpose(self._h, at.handle), "gbsp_attach_transpose")
+        self._transpose = at
+
+    def refresh_transpose_values(self, stream=None) -> None:
+        """Re-gather A^T's values after A's values changed in place."""
+        L.check(L.load().gbsp_transpose_values(self._h, _stream(stream)), "gbsp_transpose_values")
+
+    def dval(self, g: torch.Tensor, x: torch.Tensor, out: torch.Tensor | None = None,
+             accumulate: bool = False, stream=None) -> torch.Tensor:
+        """dval_k = g[row_k] * x[col_k] (+= if accumulate)."""
+        g = _need_cuda(g, "g", self.dtype)
+        x = _need_cuda(x, "x", self.dtype)
+        if out is None:
+            out = (torch.zeros if accumulate else torch.empty)(self.nnz, dtype=self.dtype, device=g.device)
+        L.check(L.load().gbsp_dval(self._h, _vp(g), _vp(x), _vp(out), int(accumulate),
+                                   _stream(stream)), "gbsp_dval")
+        return out
+
+    def dval_multi(self, G: torch.Tensor, X: torch.Tensor, out: torch.Tensor | None = None,
+                   accumulate: bool = False, stream=None) -> torch.Tensor:
+        """dval_k = sum_t G[row_k, t] X[col_k, t] for row-major G, X."""
+        if G.stride(-1) != 1 or X.stride(-1) != 1:
+            raise ValueError("G and X must be row-major")
+        m = G.shape[1]
+        if X.shape[1] != m:
+            raise ValueError("G and X need the same number of columns")
+        if out is None:
+            out = (torch.zeros if accumulate else torch.empty)(self.nnz, dtype=self.dtype, device=G.device)
+        L.check(L.load().gbsp_dval_multi(self._h, m, _vp(G), G.stride(0), _vp(X), X.stride(0),
+                                         _vp(out), int(accumulate), _stream(stream)),
+                "gbsp_dval_multi")
+        return out
+
+
+class JDSMatrix(_Product):
+    """A JDS-family matrix built on the GPU from a CRS matrix (Sect. 2).
+
+    fmt: JDS, NBJDS, NUJDS, RBJDS, SOJDS or JDS_LITERAL; perm: 'symmetric'
+    (rows and columns permuted, the paper's scheme) or 'row_only'."""
+
+    def __init__(self, A: CRSMatrix, fmt="JDS", perm="symmetric", block=256, unroll=4, stream=None):
+        super().__init__()
+        lib = L.load()
+        dev = A._device
+        self.dtype, self.n_rows, self.n_cols, self.nnz = A.dtype, A.n_rows, A.n_cols, A.nnz
+        self._device = dev
+        opts = L.JdsOpts(L.FORMATS[fmt], L.PERM[perm], block, unroll)
+        sizes = L.JdsSizes()
+        scratch = torch.empty(16, dtype=torch.int32, device=dev)
+        L.check(lib.gbsp_jds_plan(A.handle, ctypes.byref(opts), _vp(scratch), _stream(stream),
+                                  ctypes.byref(sizes)), "gbsp_jds_plan")
+        self.n_diag = sizes.n_diag
+        self.n_blocks = sizes.n_blocks
+        self.jd_ptr = torch.empty(sizes.n_diag + 1, dtype=torch.int32, device=dev)
+        self.col = torch.empty(A.nnz, dtype=torch.int32, device=dev)
+        self.val = torch.empty(A.nnz, dtype=A.dtype, device=dev)
+        self.perm = torch.empty(A.n_rows, dtype=torch.int32, device=dev)
+        self.iperm = torch.empty(A.n_rows, dtype=torch.int32, device=dev)
+        self.blk_ptr = (torch.empty(sizes.n_blocks + 1, dtype=torch.int32, device=dev)
+                        if fmt in ("RBJDS", "SOJDS") else None)
+        work = torch.empty(max(sizes.workspace_bytes, 1), dtype=torch.uint8, device=dev)
+        bufs = L.JdsBuffers(_vp(self.jd_ptr).value, _vp(self.col).value, _vp(self.val).value,
+                            _vp(self.perm).value, _vp(self.iperm).value, _vp(self.blk_ptr).value,
+                            _vp(work).value)
+        L.check(lib.gbsp_jds_build(A.handle, ctypes.byref(opts), ctypes.byref(bufs),
+                                   ctypes.byref(sizes), _stream(stream), ctypes.byref(self._h)),
+                "gbsp_jds_build")
+        del work  # the build synchronised the stream
+        self.fmt, self.perm_mode, self.block, self.unroll = fmt, perm, block, unroll
+        self.symmetric = perm == "symmetric"
+
+    def set_format(self, fmt: str, block: int = 0, unroll: int = 0) -> None:
+        L.check(L.load().gbsp_jds_set_format(self._h, L.FORMATS[fmt], block, unroll),
+                "gbsp_jds_set_format")
+        self.fmt = fmt
+        self.block = block or self.block
+        self.unroll = unroll or self.unroll
+
+    def permute(self, v: torch.Tensor, back: bool = False, stream=None) -> torch.Tensor:
+        """v -> P v (row order of the JDS basis), or back with back=True."""
+        v = _need_cuda(v, "v", self.dtype)
+        k = 1 if v.dim() == 1 else v.shape[1]
+        out = torch.empty_like(v)
+        L.check(L.load().gbsp_permute_vec(self._h, int(back), k, _vp(v), _ld(v), _vp(out), _ld(out),
+                                          _stream(stream)), "gbsp_permute_vec")
+        return out
+
+    def spmv_original(self, x: torch.Tensor, out=None, accumulate=False, stream=None):
+        return self.spmv(x, out, accumulate, basis=L.BASIS_ORIGINAL, stream=stream)

@@ -1,0 +1,181 @@
+"""JDS family on the GPU: conversion arrays bit-exact against the oracle's
+builder (Sect. 2 JDS construction, RBJDS / SOJDS layouts) and products
+against the oracle's JDS loops."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from gpu_util import adversarial_matrices, assert_close64, crs, dev, host
+from paper_0910_4836_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    import paper_0910_4836_gb300 as g
+    g.build()
+
+
+MATS = [
+    lambda: S.laplace2d(),
+    lambda: S.hh_like(100_000, 21),
+    lambda: S.zipf_rows(60_000, 22, lmax=5000),
+    lambda: S.small_random(500, 500, 23, density=0.02, empty_rows=0.3),
+]
+
+
+def check_arrays(J, Oj, fmt, block):
+    assert np.array_equal(host(J.perm), Oj.perm)
+    assert np.array_equal(host(J.iperm), Oj.iperm)
+    assert np.array_equal(host(J.jd_ptr), Oj.jd_ptr)
+    if fmt in ("RBJDS", "SOJDS"):
+        bp, c, v = (O.rbjds_build if fmt == "RBJDS" else O.sojds_build)(Oj, block)
+        assert np.array_equal(host(J.blk_ptr), bp)
+        assert np.array_equal(host(J.col), c)
+        assert np.array_equal(host(J.val).view(np.int64), v.view(np.int64))
+    else:
+        assert np.array_equal(host(J.col), Oj.col)
+        assert np.array_equal(host(J.val).view(np.int64), Oj.val.view(np.int64))
+
+
+@pytest.mark.parametrize("mi", range(len(MATS)))
+@pytest.mark.parametrize("perm", ["symmetric", "row_only"])
+def test_conversion_bit_exact(mi, perm):
+    A = MATS[mi]()
+    M = crs(A)
+    Oj = O.jds_build(A, symmetric=perm == "symmetric")
+    for fmt, block in [("JDS", 256), ("RBJDS", 256), ("RBJDS", 1000), ("SOJDS", 128),
+                       ("SOJDS", 1000)]:
+        J = M.to_jds(fmt, perm, block=block)
+        assert J.n_diag == Oj.n_diag
+        check_arrays(J, Oj, fmt, block)
+
+
+def test_golden_example_on_gpu():
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "jds_5x5.json")))
+    rows, cols, vals = [], [], []
+    for i, cs in enumerate(g["rows"]):
+        for j in cs:
+            rows.append(i)
+            cols.append(j)
+            vals.append(10 * (i + 1) + (j + 1))
+    A = S.from_coo(5, 5, rows, cols, vals)
+    J = crs(A).to_jds("JDS", "symmetric")
+    assert host(J.perm).tolist() == g["perm"]
+    assert host(J.jd_ptr).tolist() == g["jd_ptr"]
+    assert host(J.col).tolist() == g["col_jds_symmetric"]
+    assert host(J.val).tolist() == g["val_jds"]
+    xp = dev(np.array(g["x_permuted"], float))
+    for fmt in ("JDS", "NBJDS", "NUJDS", "JDS_LITERAL"):
+        J.set_format(fmt, block=2, unroll=2)
+        assert host(J.spmv(xp)).tolist() == g["y_permuted"]
+    R = crs(A).to_jds("RBJDS", "symmetric", block=g["rbjds_block"])
+    assert host(R.blk_ptr).tolist() == g["rbjds_blk_ptr"]
+    assert host(R.val).tolist() == g["rbjds_val"]
+    assert host(R.spmv(xp)).tolist() == g["y_permuted"]
+
+
+def variants():
+    yield "JDS", 0, 0
+    yield "JDS_LITERAL", 0, 0
+    for u in (2, 3, 4, 8, 16):
+        yield "NUJDS", 0, u
+    for b in (32, 100, 256, 1000, 2048, 5000):
+        yield "NBJDS", b, 0
+
+
+@pytest.mark.parametrize("mi", range(len(MATS)))
+def test_products_permuted_and_original(mi):
+    A = MATS[mi]()
+    x = S.vector(A.n_cols, 31 + mi)
+    ref, s = O.crs_spmv_exact(A, x)
+    M = crs(A)
+    for perm in ("symmetric", "row_only"):
+        Oj = O.jds_build(A, symmetric=perm == "symmetric")
+        xp = O.permute(Oj.perm, x) if perm == "symmetric" else x
+        ref_p = O.permute(Oj.perm, ref)
+        s_p = O.permute(Oj.perm, s)
+        J = M.to_jds("JDS", perm)
+        xd, xpd = dev(x), dev(xp)
+        first = None
+        for fmt, b, u in variants():
+            J.set_format(fmt, block=b, unroll=u)
+            yp = host(J.spmv(xpd))
+            assert_close64(yp, ref_p, s_p, f"{perm} {fmt} b={b} u={u} permuted")
+            yo = host(J.spmv_original(xd))
+            assert_close64(yo, ref, s, f"{perm} {fmt} b={b} u={u} original")
+            # every JDS-family kernel adds a row in slot order: identical bits
+            if first is None:
+                first = yp
+            assert np.array_equal(yp.view(np.int64), first.view(np.int64)), fmt
+        for fmt, b in [("RBJDS", 256), ("RBJDS", 1000), ("RBJDS", 1), ("SOJDS", 256)]:
+            R = M.to_jds(fmt, perm, block=b)
+            yp = host(R.spmv(xpd))
+            assert_close64(yp, ref_p, s_p, f"{perm} {fmt} b={b}")
+            if fmt == "RBJDS":
+                assert np.array_equal(yp.view(np.int64), first.view(np.int64))
+            assert_close64(host(R.spmv_original(xd)), ref, s, f"{perm} {fmt} original")
+
+
+def test_integer_bit_exact_against_literal_loop():
+    A = S.integer_values(S.zipf_rows(40_000, 41, lmax=3000), 41, 1024)
+    x = S.int_vector(A.n_cols, 41, 1024)
+    M = crs(A)
+    Oj = O.jds_build(A, True)
+    xp = O.permute(Oj.perm, x)
+    ref = O.jds_spmv(Oj, xp)
+    J = M.to_jds("JDS", "symmetric")
+    xpd = dev(xp)
+    for fmt, b, u in variants():
+        J.set_format(fmt, block=b, unroll=u)
+        assert np.array_equal(host(J.spmv(xpd)), ref), fmt
+    for fmt in ("RBJDS", "SOJDS"):
+        assert np.array_equal(host(M.to_jds(fmt, "symmetric", block=500).spmv(xpd)), ref), fmt
+    # unpermuted result equals CRS
+    assert np.array_equal(host(J.spmv_original(dev(x))), O.crs_spmv(A, x))
+
+
+def test_permute_roundtrip_and_rectangular():
+    A = S.small_random(300, 77, 51, density=0.1, empty_rows=0.2)
+    M = crs(A)
+    J = M.to_jds("JDS", "row_only")
+    x = S.vector(77, 51)
+    ref, s = O.crs_spmv_exact(A, x)
+    assert_close64(host(J.spmv_original(dev(x))), ref, s, "rect original")
+    v = dev(S.vector(300, 52))
+    assert torch.equal(J.permute(J.permute(v), back=True), v)
+    from paper_0910_4836_gb300 import GbspError
+    with pytest.raises(GbspError):
+        M.to_jds("JDS", "symmetric")
+
+
+def test_jds_spmm():
+    A = S.hh_like(60_000, 61)
+    X = np.stack([S.vector(A.n_cols, 70 + c) for c in range(16)], axis=1)
+    Yref, Sref = O.crs_spmm_exact(A, X)
+    M = crs(A)
+    for fmt in ("JDS", "NBJDS", "RBJDS", "SOJDS"):
+        J = M.to_jds(fmt, "symmetric", block=512)
+        for k in (4, 5, 16):
+            Y = host(J.spmm(dev(X[:, :k].copy()), basis=1))
+            for c in range(k):
+                assert_close64(Y[:, c], Yref[:, c], Sref[:, c], f"{fmt} k={k} col {c}")
+
+
+@pytest.mark.parametrize("idx", range(8))
+def test_adversarial(idx):
+    A = adversarial_matrices()[idx]
+    perm = "symmetric" if A.n_rows == A.n_cols else "row_only"
+    x = S.vector(A.n_cols, 80 + idx)
+    ref, s = O.crs_spmv_exact(A, x)
+    M = crs(A)
+    Oj = O.jds_build(A, symmetric=perm == "symmetric")
+    for fmt, b in [("JDS", 0), ("NUJDS", 0), ("NBJDS", 64), ("RBJDS", 64), ("SOJDS", 64),
+                   ("JDS_LITERAL", 0)]:
+        J = M.to_jds(fmt, perm, block=b or 256)
+        check_arrays(J, Oj, fmt, b or 256)
+        assert_close64(host(J.spmv_original(dev(x))), ref, s, f"{A.name} {fmt}")
