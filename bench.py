@@ -297,8 +297,9 @@ def format_table(M, A, x, time_launches, dev, peak):
     for l, r in ((4, 4), (8, 2), (16, 2), (32, 1)):
         M.set_kernel("vector", lanes=l, rows_per_warp=r)
         rec(f"CRS vector l{l} r{r}", lambda: M.spmv(x, out=y), alg)
-    M.prepare_tiled(2048)
-    rec("CRS tiled 2048", lambda: M.spmv(x, out=y), alg)
+    for t in (1024, 2048):
+        M.prepare_tiled(t)
+        rec(f"CRS tiled {t}", lambda: M.spmv(x, out=y), alg)
     jalg = 12 * A.nnz + 16 * A.n_rows  # permuted basis; jd_ptr is negligible
     for perm in ("symmetric", "row_only"):
         J = M.to_jds("JDS", perm)

@@ -87,18 +87,24 @@ typedef enum { GBSP_ACC_PLAIN = 0, GBSP_ACC_COMPENSATED = 1 } gbsp_accum;
 
 /* CRS kernel choice.  VECTOR: `lanes` threads of a warp per row, each warp
  * working on `rows_per_warp` rows at a time (lanes * rows in flight).
- * TILED: rows grouped into tiles of about `tile` (rows + entries), each
- * tile's entries streamed through shared memory with bulk asynchronous
- * copies; needs gbsp_crs_prepare.  AUTO picks from the row-length mean. */
+ * TILED: rows grouped into tiles of `tile` merge items (rows + entries);
+ * a persistent CTA streams its tiles' val, col and row_ptr slices into
+ * shared memory with bulk asynchronous copies (a producer warp, mbarrier
+ * stages) and sums each row with one thread, rows sorted by length inside
+ * the tile so that the lanes of a warp do equal work; needs
+ * gbsp_crs_prepare.  AUTO picks from the row-length mean. */
 typedef enum { GBSP_KERNEL_AUTO = 0, GBSP_KERNEL_VECTOR = 1, GBSP_KERNEL_TILED = 2 } gbsp_kernel;
 
 typedef struct {
     int32_t kernel;        /* gbsp_kernel */
     int32_t lanes;         /* VECTOR: 1, 2, 4, 8, 16 or 32 (0 = auto) */
     int32_t rows_per_warp; /* VECTOR: rows per lane group handled together, 1..8 (0 = auto) */
-    int32_t tile;          /* TILED: merge items (rows + entries) per tile, 256..8192 (0 = auto) */
+    int32_t tile;          /* TILED: merge items (rows + entries) per tile, 1024 or 2048 (0 = auto) */
     int32_t rhs_tile;      /* SpMM: right-hand sides handled per pass, 1..16 (0 = auto) */
     int32_t accum;         /* gbsp_accum (FP32 handles) */
+    int32_t format;        /* JDS-family handles: walk in use (read only; set with gbsp_jds_set_format) */
+    int32_t block;         /* NBJDS rows per block (read only) */
+    int32_t unroll;        /* NUJDS diagonals per step (read only) */
 } gbsp_kernel_opts;
 
 /* ---------------------------------------------------------------- misc -- */
@@ -119,6 +125,12 @@ gbsp_status gbsp_destroy(gbsp_handle h);
 /* Copy a device status word to *h_out (synchronises `stream`). */
 gbsp_status gbsp_read_status(const int32_t *d_status, void *stream, int32_t *h_out);
 
+/* Give a handle a device status word (int32, caller memory, NULL to clear).
+ * Kernels with bounded waits (the TILED pipeline) store GBSP_ERR_TIMEOUT
+ * there if a wait exceeds its limit (2 s) instead of hanging; the caller
+ * resets it to 0.  Without a word such a timeout is silent. */
+gbsp_status gbsp_set_status_word(gbsp_handle h, int32_t *d_status);
+
 /* ----------------------------------------------------------------- CRS -- */
 
 /* Create a CRS handle (Sect. 2, "compressed row storage": val, col_idx and
@@ -133,6 +145,12 @@ gbsp_status gbsp_crs_create(int64_t n_rows, int64_t n_cols, int64_t nnz,
                             const int32_t *d_row_ptr, const int32_t *d_col,
                             const void *d_val, gbsp_dtype dtype, gbsp_handle *out);
 
+/* Point a CRS or JDS-family handle at new values (same pattern, same dtype,
+ * d_val borrowed like the original).  Host-side only: no device work.  For
+ * a JDS-family handle built with a value map (gbsp_jds_buffers.vmap) use
+ * gbsp_jds_values to re-gather its values instead. */
+gbsp_status gbsp_set_values(gbsp_handle h, const void *d_val);
+
 /* Check the CRS arrays on the device: row_ptr[0] == 0, row_ptr
  * non-decreasing, row_ptr[n_rows] == nnz, 0 <= col < n_cols.  Writes 0 to
  * *d_status when all hold, else a GBSP_ERR_MATRIX code (no trap, no abort).
@@ -145,10 +163,13 @@ gbsp_status gbsp_crs_validate(gbsp_handle crs, int32_t *d_status, void *stream);
 gbsp_status gbsp_set_kernel(gbsp_handle h, const gbsp_kernel_opts *opts);
 gbsp_status gbsp_get_kernel(gbsp_handle h, gbsp_kernel_opts *out);
 
-/* TILED kernel set-up: bytes of the tile table for `tile` merge items per
- * tile (an int32 row index per tile boundary), and a device pass that fills
- * it into caller memory (borrowed until destroy or the next prepare).
- * The tile table is a pure function of row_ptr. */
+/* TILED kernel set-up: bytes of the tile table for `tile` (1024 or 2048)
+ * merge items per tile (the first row of every tile, then 16 bytes of
+ * offsets per tile), and a device pass that fills it into caller memory
+ * (16-byte aligned; borrowed until destroy or the next prepare).  The table
+ * is a pure function of row_ptr.  TILED reads the matrix with bulk copies,
+ * so gbsp_crs_prepare returns GBSP_ERR_ARG unless row_ptr, col and val are
+ * 16-byte aligned. */
 gbsp_status gbsp_crs_tile_bytes(gbsp_handle crs, int32_t tile, int64_t *bytes);
 gbsp_status gbsp_crs_prepare(gbsp_handle crs, int32_t tile, void *d_table, int64_t table_bytes,
                              void *stream);
@@ -178,6 +199,8 @@ typedef struct {
     int32_t *iperm;    /* [n_rows] iperm[old] = new row */
     int32_t *blk_ptr;  /* [n_blocks+1] RBJDS / SOJDS only, else may be NULL */
     void *workspace;   /* [workspace_bytes] scratch, free after the build completes */
+    int32_t *vmap;     /* optional [nnz]: CRS entry index of every stored entry, kept by the
+                          handle for gbsp_jds_values (NULL: not built) */
 } gbsp_jds_buffers;
 
 /* Sizes for converting `crs` (Sect. 2 JDS construction).  Reads the row
@@ -210,6 +233,12 @@ gbsp_status gbsp_jds_build(gbsp_handle crs, const gbsp_jds_opts *opts,
  * or unroll.  RBJDS / SOJDS handles accept only a block size equal to the
  * one they were built with.  Errors: GBSP_ERR_UNSUPPORTED otherwise. */
 gbsp_status gbsp_jds_set_format(gbsp_handle jds, int32_t format, int32_t block, int32_t unroll);
+
+/* Re-gather a JDS-family handle's values from CRS-ordered values d_src_val
+ * (nnz entries, the handle's dtype): val[i] = d_src_val[vmap[i]].  For
+ * values that change while the pattern stays (training, time stepping).
+ * Errors: GBSP_ERR_UNSUPPORTED if the handle was built without vmap. */
+gbsp_status gbsp_jds_values(gbsp_handle jds, const void *d_src_val, void *stream);
 
 /* Read back the JDS-family shape (host-side, no device work). */
 gbsp_status gbsp_jds_info(gbsp_handle jds, gbsp_jds_sizes *out, gbsp_jds_opts *opts);
@@ -271,14 +300,17 @@ gbsp_status gbsp_transpose_values(gbsp_handle crs, void *stream);
 gbsp_status gbsp_attach_transpose(gbsp_handle A, gbsp_handle at);
 
 /* Value gradient of a CRS product: dval_k = g[row_k] * x[col_k] (the
- * derivative of g.(A x) with respect to val_k), written (or added, if
- * accumulate) in CRS entry order.  g: n_rows, x: n_cols, dval: nnz. */
+ * derivative of g.(A x) with respect to val_k), written (or added with one
+ * fused multiply-add, if accumulate) in CRS entry order.  g: n_rows,
+ * x: n_cols, dval: nnz. */
 gbsp_status gbsp_dval(gbsp_handle crs, const void *d_g, const void *d_x, void *d_dval,
                       int32_t accumulate, void *stream);
 
-/* Fused multi-step value gradient: dval_k (+)= sum_{t<m} G[row_k, t] *
- * X[col_k, t], G (n_rows x m, ld ldg) and X (n_cols x m, ld ldx) row-major:
- * one pass over the entries for m product pairs (iterated products A^m x). */
+/* Fused multi-step value gradient: d = (accumulate ? dval_k : 0), then
+ * d = fma(G[row_k, t], X[col_k, t], d) for t = 0 .. m-1, with G (n_rows x m,
+ * ld ldg) and X (n_cols x m, ld ldx) row-major: one pass over the entries
+ * for m product pairs of an iterated product A^m x.  The fixed order makes
+ * the result independent of how the t range is split over calls. */
 gbsp_status gbsp_dval_multi(gbsp_handle crs, int32_t m, const void *d_G, int64_t ldg,
                             const void *d_X, int64_t ldx, void *d_dval, int32_t accumulate,
                             void *stream);
@@ -304,17 +336,30 @@ typedef struct {
 gbsp_status gbsp_batch_plan(int32_t n, const gbsp_batch_item *items, int32_t chunk,
                             int64_t *table_bytes);
 
-/* Write the work table into caller memory d_table (table_bytes from the
- * plan) and return a batch object.  Synchronises `stream` once. */
+/* Write the work table into caller memory d_table (256-byte aligned,
+ * table_bytes from the plan) and return a batch object.  Reads each
+ * matrix's row pointers back to the host once and synchronises `stream`.
+ * d_ready (may be NULL): an int32 flag in device or host-mapped memory;
+ * when given, every launch first waits until it is non-zero -- set by the
+ * host or by work finished earlier on the stream, never by a kernel
+ * running at the same time -- for at most 1 s. */
 gbsp_status gbsp_batch_create(int32_t n, const gbsp_batch_item *items, int32_t chunk,
-                              void *d_table, int64_t table_bytes, void *stream,
-                              gbsp_batch *out);
+                              void *d_table, int64_t table_bytes, const int32_t *d_ready,
+                              void *stream, gbsp_batch *out);
 
 /* All items in one persistent launch: CTAs take work items from the table
- * through a device counter (reset on `stream` first, so replays in a CUDA
- * graph are safe).  d_status (may be NULL) receives GBSP_ERR_TIMEOUT if the
- * kernel's bounded wait for its start flag ran out, else 0. */
+ * through a device counter (reset by a memset on `stream` first, so the
+ * memset + kernel pair can be captured in a CUDA graph and replayed).
+ * Items are written, never accumulated.  CRS items use the VECTOR
+ * arithmetic of their handle (lanes per row), JDS-family items their
+ * thread-per-row walk, so each result is bit-identical to gbsp_spmm of the
+ * same handle with the VECTOR / JDS kernel.  d_status (may be NULL)
+ * receives GBSP_ERR_TIMEOUT if the wait for d_ready ran out (the launch then
+ * does no work); the caller resets it. */
 gbsp_status gbsp_batch_run(gbsp_batch b, int32_t *d_status, void *stream);
+
+/* Number of work items and persistent CTAs of a batch (host-side). */
+gbsp_status gbsp_batch_info(gbsp_batch b, int64_t *n_work, int32_t *grid);
 gbsp_status gbsp_batch_destroy(gbsp_batch b);
 
 /* ------------------------------------------------------------ autotuner -- */

@@ -31,7 +31,8 @@ KERNELS = {"auto": 0, "vector": 1, "tiled": 2}
 
 class KernelOpts(ctypes.Structure):
     _fields_ = [("kernel", c_i32), ("lanes", c_i32), ("rows_per_warp", c_i32), ("tile", c_i32),
-                ("rhs_tile", c_i32), ("accum", c_i32)]
+                ("rhs_tile", c_i32), ("accum", c_i32), ("format", c_i32), ("block", c_i32),
+                ("unroll", c_i32)]
 
 
 class JdsOpts(ctypes.Structure):
@@ -45,7 +46,7 @@ class JdsSizes(ctypes.Structure):
 
 class JdsBuffers(ctypes.Structure):
     _fields_ = [("jd_ptr", c_vp), ("col", c_vp), ("val", c_vp), ("perm", c_vp), ("iperm", c_vp),
-                ("blk_ptr", c_vp), ("workspace", c_vp)]
+                ("blk_ptr", c_vp), ("workspace", c_vp), ("vmap", c_vp)]
 
 
 class TransposeBuffers(ctypes.Structure):
@@ -67,8 +68,11 @@ SIGNATURES = {
     "gbsp_version": (c_i32, []),
     "gbsp_destroy": (c_i32, [c_vp]),
     "gbsp_read_status": (c_i32, [c_vp, c_vp, P(c_i32)]),
+    "gbsp_set_status_word": (c_i32, [c_vp, c_vp]),
     "gbsp_crs_create": (c_i32, [c_i64, c_i64, c_i64, c_vp, c_vp, c_vp, c_i32, P(c_vp)]),
     "gbsp_crs_validate": (c_i32, [c_vp, c_vp, c_vp]),
+    "gbsp_set_values": (c_i32, [c_vp, c_vp]),
+    "gbsp_jds_values": (c_i32, [c_vp, c_vp, c_vp]),
     "gbsp_set_kernel": (c_i32, [c_vp, P(KernelOpts)]),
     "gbsp_get_kernel": (c_i32, [c_vp, P(KernelOpts)]),
     "gbsp_crs_tile_bytes": (c_i32, [c_vp, c_i32, P(c_i64)]),
@@ -89,6 +93,7 @@ SIGNATURES = {
     "gbsp_batch_plan": (c_i32, [c_i32, P(BatchItem), c_i32, P(c_i64)]),
     "gbsp_batch_create": (c_i32, [c_i32, P(BatchItem), c_i32, c_vp, c_i64, c_vp, c_vp, P(c_vp)]),
     "gbsp_batch_run": (c_i32, [c_vp, c_vp, c_vp]),
+    "gbsp_batch_info": (c_i32, [c_vp, P(c_i64), P(c_i32)]),
     "gbsp_batch_destroy": (c_i32, [c_vp]),
     "gbsp_autotune": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp, P(KernelOpts), P(c_f32)]),
 }

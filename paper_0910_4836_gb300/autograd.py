@@ -1,0 +1,159 @@
+"""Differentiable sparse products (argument marshalling over the C ABI).
+
+``spmv(pattern, val, x)`` is y = A x with A's values ``val`` (CRS entry
+order) and x both differentiable; the backward pass runs the library's
+kernels: dx = A^T g on the transposed structure (a CRS of A^T, or a JDS of
+A^T -- the "transposed JDS" form), and dval_k = g[row_k] x[col_k].
+
+``power_apply(pattern, val, x, m, checkpoint)`` is A^m x for iterated
+products as in the eigensolvers the paper is about (Sect. 1): the forward
+pass stores x_t only every `checkpoint` steps; the backward pass recomputes
+each segment from its checkpoint, runs g_{t-1} = A^T g_t down the segment
+and adds the segment's value gradient sum_t g_t[row] x_{t-1}[col] with ONE
+fused pass over the entries (gbsp_dval_multi).  The fused kernel adds the
+terms for t = m, m-1, ..., 1 in that order into one running sum, so the
+gradients are bit-identical for every checkpoint interval.
+"""
+from __future__ import annotations
+
+import torch
+
+from .sparse import CRSMatrix
+
+
+class Pattern:
+    """Sparsity pattern (row_ptr, col on the GPU) plus the kernels' set-up:
+    the product handle and, built once, the transposed structure.
+
+    adjoint: "crs" runs A^T g with the CRS kernels of the transposed
+    structure, "jds" with a JDS (row-only permutation) of it."""
+
+    def __init__(self, row_ptr: torch.Tensor, col: torch.Tensor, n_cols: int, dtype=torch.float64,
+                 adjoint: str = "crs", tiled: bool = False):
+        self.row_ptr = row_ptr.contiguous()
+        self.col = col.contiguous()
+        self.n_rows = self.row_ptr.numel() - 1
+        self.n_cols = int(n_cols)
+        self.nnz = self.col.numel()
+        self.dtype = dtype
+        self.adjoint = adjoint
+        dummy = torch.zeros(max(self.nnz, 1), dtype=dtype, device=self.row_ptr.device)[: self.nnz]
+        self.A = CRSMatrix(self.row_ptr, self.col, dummy, self.n_cols)
+        if tiled:
+            self.A.prepare_tiled(1024)
+        self.AT = None
+        self.JT = None
+        self._vals_version = None
+
+    @classmethod
+    def from_host(cls, A, device="cuda", dtype=torch.float64, **kw) -> "Pattern":
+        return cls(torch.as_tensor(A.row_ptr, dtype=torch.int32).to(device),
+                   torch.as_tensor(A.col, dtype=torch.int32).to(device), A.n_cols, dtype, **kw)
+
+    def bind(self, val: torch.Tensor) -> CRSMatrix:
+        """Point the product handle at `val`."""
+        if val.dtype != self.dtype or val.numel() != self.nnz:
+            raise ValueError("values do not match the pattern")
+        self.A.set_values(val.detach())
+        return self.A
+
+    def adjoint_op(self, val: torch.Tensor):
+        """Handle computing A^T g for the bound values (built on first use,
+        values re-gathered whenever `val` changed)."""
+        self.bind(val)
+        if self.AT is None:
+            self.AT = self.A.transpose()
+            if self.adjoint == "jds":
+                self.JT = self.AT.to_jds("NUJDS", "row_only", unroll=4, value_map=True)
+        key = (val.data_ptr(), val._version)
+        if self._vals_version != key:
+            self.A.refresh_transpose_values()
+            if self.JT is not None:
+                self.JT.refresh_values(self.AT.val)
+            self._vals_version = key
+        return self.JT if self.JT is not None else self.AT
+
+    def apply_t(self, val: torch.Tensor, g: torch.Tensor, out=None) -> torch.Tensor:
+        """A^T g for 1-D g or an (n, 1) column view (with `out` likewise)."""
+        return self.adjoint_op(val).spmm(g, out=out, basis=1)
+
+
+class SpMVFunction(torch.autograd.Function):
+    """y = A(val) x; gradients for val (per stored entry) and x."""
+
+    @staticmethod
+    def forward(ctx, val, x, pattern: Pattern):
+        ctx.pattern = pattern
+        ctx.save_for_backward(val, x)
+        return pattern.bind(val).spmv(x.detach().contiguous())
+
+    @staticmethod
+    def backward(ctx, gy):
+        val, x = ctx.saved_tensors
+        p = ctx.pattern
+        gy = gy.contiguous()
+        dval = dx = None
+        if ctx.needs_input_grad[0]:
+            dval = p.bind(val).dval(gy, x.detach().contiguous())
+        if ctx.needs_input_grad[1]:
+            dx = p.apply_t(val, gy)
+        return dval, dx, None
+
+
+def spmv(pattern: Pattern, val: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
+    return SpMVFunction.apply(val, x, pattern)
+
+
+class PowerFunction(torch.autograd.Function):
+    """x_m = A^m x with checkpointed recomputation in the backward pass."""
+
+    @staticmethod
+    def forward(ctx, val, x, pattern: Pattern, m: int, c: int):
+        A = pattern.bind(val)
+        cur = x.detach().contiguous()
+        ckpts = [cur]
+        for t in range(1, m + 1):
+            cur = A.spmv(cur)
+            if t % c == 0 and t < m:
+                ckpts.append(cur)
+        ctx.pattern, ctx.m, ctx.c = pattern, m, c
+        ctx.save_for_backward(val, *ckpts)
+        return cur
+
+    @staticmethod
+    def backward(ctx, gm):
+        val, *ckpts = ctx.saved_tensors
+        p, m, c = ctx.pattern, ctx.m, ctx.c
+        A = p.bind(val)
+        n = p.n_rows
+        dev, dt = gm.device, gm.dtype
+        dval = torch.zeros(p.nnz, dtype=dt, device=dev) if ctx.needs_input_grad[0] else None
+        g = gm.contiguous()
+        for seg in range((m - 1) // c, -1, -1):
+            t0 = seg * c
+            w = min(t0 + c, m) - t0
+            # X[:, i] = x_{t1-1-i}: recomputed from the checkpoint x_{t0}
+            X = torch.empty((n, w), dtype=dt, device=dev)
+            X[:, w - 1] = ckpts[seg]
+            for j in range(1, w):
+                A.spmm(X[:, w - j:w - j + 1], out=X[:, w - 1 - j:w - j])
+            # G[:, i] = g_{t1-i}, i.e. g_{t-1} = A^T g_t down the segment
+            G = torch.empty((n, w), dtype=dt, device=dev)
+            G[:, 0] = g
+            for i in range(1, w):
+                p.apply_t(val, G[:, i - 1:i], out=G[:, i:i + 1])
+            if dval is not None:
+                # terms g_t[row] x_{t-1}[col] for t = t1, t1-1, ..., t0+1
+                A.dval_multi(G, X, out=dval, accumulate=True)
+            g = p.apply_t(val, G[:, w - 1:w]).reshape(n)
+            A = p.bind(val)
+        return dval, (g if ctx.needs_input_grad[1] else None), None, None, None
+
+
+def power_apply(pattern: Pattern, val: torch.Tensor, x: torch.Tensor, m: int,
+                checkpoint: int = 1) -> torch.Tensor:
+    """A^m x, differentiable in val and x, with x_t stored every
+    `checkpoint` steps."""
+    if m < 1 or checkpoint < 1:
+        raise ValueError("m and checkpoint must be >= 1")
+    return PowerFunction.apply(val, x, pattern, int(m), int(checkpoint))

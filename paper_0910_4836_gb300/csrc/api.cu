@@ -35,6 +35,20 @@ static bool overlap(const void *a, size_t na, const void *b, size_t nb) {
     return pa < pb + nb && pb < pa + na;
 }
 
+// Strided k-column blocks X (ldx) and Y (ldy): they overlap if their byte
+// spans meet and, for equal leading dimensions, their columns coincide
+// modulo ld (interleaved columns of one row-major block are disjoint).
+static bool blocks_overlap(const void *x, size_t xb, int64_t ldx, const void *y, size_t yb, int64_t ldy,
+                           int32_t k, int dtype) {
+    if (!overlap(x, xb, y, yb)) return false;
+    const int64_t es = (int64_t)(dtype == GBSP_F64 ? 8 : 4);
+    const int64_t diff = static_cast<const char *>(y) - static_cast<const char *>(x);
+    if (ldx != ldy || ldx <= k || diff % es != 0) return true;
+    const int64_t d = diff / es;
+    const int64_t r = ((d % ldx) + ldx) % ldx;
+    return r < k || r > ldx - k;
+}
+
 static size_t span_bytes(int64_t rows, int64_t ld, int32_t k, int dtype) {
     if (rows <= 0) return 0;
     return (size_t)((rows - 1) * ld + k) * elem_size(dtype);
@@ -124,8 +138,8 @@ gbsp_status gbsp_set_kernel(gbsp_handle h, const gbsp_kernel_opts *o) {
     if (o->rows_per_warp != 0 && o->rows_per_warp != 1 && o->rows_per_warp != 2 &&
         o->rows_per_warp != 4)
         return arg_error("gbsp_set_kernel: rows_per_warp must be 1, 2 or 4");
-    if (o->tile != 0 && o->tile != 512 && o->tile != 1024 && o->tile != 2048)
-        return arg_error("gbsp_set_kernel: tile must be 512, 1024 or 2048");
+    if (o->tile != 0 && o->tile != 1024 && o->tile != 2048)
+        return arg_error("gbsp_set_kernel: tile must be 1024 or 2048");
     if (o->rhs_tile != 0 && (o->rhs_tile < 1 || o->rhs_tile > 32))
         return arg_error("gbsp_set_kernel: rhs_tile must be in 1..32");
     if (o->accum != 0 && o->accum != GBSP_ACC_COMPENSATED)
@@ -145,14 +159,38 @@ gbsp_status gbsp_get_kernel(gbsp_handle h, gbsp_kernel_opts *out) {
     if (!h || !out) return arg_error("gbsp_get_kernel: NULL argument");
     *out = h->kopt;
     out->tile = h->tile;
+    out->format = h->kind == KIND_JDS ? h->format : GBSP_CRS;
+    out->block = h->kind == KIND_JDS ? h->block : 0;
+    out->unroll = h->kind == KIND_JDS ? h->unroll : 0;
     return GBSP_OK;
+}
+
+gbsp_status gbsp_set_values(gbsp_handle h, const void *d_val) {
+    if (!h) return arg_error("gbsp_set_values: NULL handle");
+    if (h->nnz > 0 && !d_val) return arg_error("gbsp_set_values: NULL values");
+    if (reinterpret_cast<uintptr_t>(d_val) & (elem_size(h->dtype) - 1))
+        return arg_error("gbsp_set_values: misaligned values");
+    if (h->kind == KIND_CRS && h->tile_rows && (reinterpret_cast<uintptr_t>(d_val) & 15))
+        return arg_error("gbsp_set_values: the prepared TILED kernel needs 16-byte aligned values");
+    h->val = d_val;
+    return GBSP_OK;
+}
+
+gbsp_status gbsp_jds_values(gbsp_handle h, const void *d_src_val, void *stream) {
+    if (!h || (h->nnz > 0 && !d_src_val)) return arg_error("gbsp_jds_values: NULL argument");
+    if (h->kind != KIND_JDS) return arg_error("gbsp_jds_values: not a JDS-family handle");
+    if (!h->vmap) {
+        set_error("gbsp_jds_values: handle was built without a value map");
+        return GBSP_ERR_UNSUPPORTED;
+    }
+    return gather_values_launch(h->nnz, h->vmap, d_src_val, const_cast<void *>(h->val), h->dtype,
+                                static_cast<cudaStream_t>(stream));
 }
 
 gbsp_status gbsp_crs_tile_bytes(gbsp_handle crs, int32_t tile, int64_t *bytes) {
     if (!crs || !bytes) return arg_error("gbsp_crs_tile_bytes: NULL argument");
-    if (tile != 512 && tile != 1024 && tile != 2048)
-        return arg_error("gbsp_crs_tile_bytes: tile must be 512, 1024 or 2048");
-    *bytes = 4 * (ceil_div(crs->n_rows + crs->nnz, tile) + 1);
+    if (tile != 1024 && tile != 2048) return arg_error("gbsp_crs_tile_bytes: tile must be 1024 or 2048");
+    *bytes = crs_tile_table_bytes(*crs, tile);
     return GBSP_OK;
 }
 
@@ -162,13 +200,25 @@ gbsp_status gbsp_crs_prepare(gbsp_handle crs, int32_t tile, void *d_table, int64
     gbsp_status st = gbsp_crs_tile_bytes(crs, tile, &need);
     if (st != GBSP_OK) return st;
     if (crs->kind != KIND_CRS) return arg_error("gbsp_crs_prepare: not a CRS handle");
-    if (!d_table) return arg_error("gbsp_crs_prepare: table is NULL");
+    if (!d_table || (reinterpret_cast<uintptr_t>(d_table) & 15))
+        return arg_error("gbsp_crs_prepare: table must be a 16-byte aligned device buffer");
+    // the bulk copies of the TILED kernel need 16-byte aligned arrays
+    if ((reinterpret_cast<uintptr_t>(crs->row_ptr) & 15) || (reinterpret_cast<uintptr_t>(crs->col) & 15) ||
+        (reinterpret_cast<uintptr_t>(crs->val) & 15))
+        return arg_error("gbsp_crs_prepare: TILED needs row_ptr, col and val 16-byte aligned");
     if (table_bytes < need) {
         set_error("gbsp_crs_prepare: table needs %lld bytes", (long long)need);
         return GBSP_ERR_NOMEM;
     }
     return crs_prepare_tiles(*crs, tile, static_cast<int32_t *>(d_table),
                              static_cast<cudaStream_t>(stream));
+}
+
+gbsp_status gbsp_set_status_word(gbsp_handle h, int32_t *d_status) {
+    if (!h) return arg_error("gbsp_set_status_word: NULL handle");
+    if (reinterpret_cast<uintptr_t>(d_status) & 3) return arg_error("gbsp_set_status_word: misaligned");
+    h->status = d_status;
+    return GBSP_OK;
 }
 
 gbsp_status gbsp_jds_plan(gbsp_handle crs, const gbsp_jds_opts *opts, int32_t *d_scratch,
@@ -285,7 +335,7 @@ gbsp_status gbsp_spmm(gbsp_handle A, int32_t op, int32_t basis, int32_t k, const
     }
     const size_t xb = span_bytes(A->n_cols, ldx, k, A->dtype), yb = span_bytes(A->n_rows, ldy, k, A->dtype);
     if ((xb > 0 && !d_X) || (yb > 0 && !d_Y)) return arg_error("gbsp_spmm: NULL vector");
-    if (overlap(d_X, xb, d_Y, yb)) return arg_error("gbsp_spmm: x and y overlap");
+    if (blocks_overlap(d_X, xb, ldx, d_Y, yb, ldy, k, A->dtype)) return arg_error("gbsp_spmm: x and y overlap");
     const uintptr_t am = elem_size(A->dtype) - 1;
     if ((reinterpret_cast<uintptr_t>(d_X) & am) || (reinterpret_cast<uintptr_t>(d_Y) & am))
         return arg_error("gbsp_spmm: misaligned vector");

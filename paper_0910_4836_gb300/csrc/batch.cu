@@ -1,25 +1,402 @@
-// Batched persistent launch and autotuner (not yet available in this build).
+// Batched products in one persistent launch.
+//
+// Many matrices of uneven sizes, each with its own k right-hand sides,
+// storage scheme and kernel options, are cut into work items of about
+// `chunk` stored entries (a contiguous range of rows of one matrix).  The
+// work table lives in caller memory; CTAs of one persistent grid take items
+// through a device counter (reset by a memset on the stream before every
+// launch, so the pair can be captured in a CUDA graph and replayed).  Each
+// item runs the same per-row arithmetic as the stand-alone kernel of its
+// format and options, so a matrix's batched result is bit-identical to the
+// result of gbsp_spmm on it alone.
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "accum.cuh"
 #include "internal.cuh"
+#include "sm100.cuh"
+
+namespace gbsp {
+
+struct BatchMat {
+    int32_t kind;      // KIND_CRS / KIND_JDS
+    int32_t format;    // gbsp_format
+    int32_t vm;        // ValMode
+    int32_t k;         // right-hand sides
+    int32_t lanes, rows, rhs_tile, unroll;
+    int32_t block;     // RBJDS / SOJDS block
+    int32_t pad;
+    int64_t n_rows, n_diag;
+    const int32_t *row_ptr, *col, *jd_ptr, *blk_ptr;
+    const void *val;
+    const void *x;
+    void *y;
+    int64_t ldx, ldy;
+};
+
+struct BatchWork {
+    int32_t mat;
+    int32_t pad;
+    int64_t rb, re;  // rows [rb, re) of matrix `mat`
+};
+
+constexpr int kBatchThreads = 256;
+constexpr uint64_t kReadyLimitNs = 1000000000ull;  // 1 s bound on the ready-flag wait
+
+// CRS rows [rb, re), k = 1, L lanes per row (same arithmetic as crs_vector_kernel).
+template <int VM, int L>
+__device__ void batch_crs_rows(const BatchMat &m, int64_t rb, int64_t re) {
+    typedef typename ValT<VM>::T T;
+    constexpr int G = 32 / L;
+    const int lane = threadIdx.x & 31, grp = lane / L, gl = lane % L, wid = threadIdx.x >> 5;
+    const T *val = static_cast<const T *>(m.val);
+    const T *x = static_cast<const T *>(m.x);
+    T *y = static_cast<T *>(m.y);
+    for (int64_t base = rb + (int64_t)wid * G; base < re; base += (int64_t)(kBatchThreads / 32) * G) {
+        const int64_t r = base + grp;
+        int k0 = 0, k1 = 0;
+        if (r < re) {
+            k0 = __ldg(m.row_ptr + r);
+            k1 = __ldg(m.row_ptr + r + 1);
+        }
+        Acc<VM> acc;
+        acc.init();
+        for (int j = k0 + gl; j < k1; j += L) acc.add(__ldg(val + j), ld_vec(x + (int64_t)__ldg(m.col + j) * m.ldx));
+        group_reduce<L, VM>(acc);
+        if (gl == 0 && r < re) y[r * m.ldy] = acc.result();
+    }
+}
+
+// CRS rows with k > 1: lanes over right-hand sides (same as crs_spmm_kernel).
+template <int VM, int KT>
+__device__ void batch_crs_spmm_rows(const BatchMat &m, int64_t rb, int64_t re, int c0) {
+    typedef typename ValT<VM>::T T;
+    constexpr int G = 32 / KT;
+    const int lane = threadIdx.x & 31, grp = lane / KT, c = lane % KT, wid = threadIdx.x >> 5;
+    const int cc = c0 + c;
+    const bool active = cc < m.k;
+    const T *val = static_cast<const T *>(m.val);
+    const T *X = static_cast<const T *>(m.x);
+    T *Y = static_cast<T *>(m.y);
+    for (int64_t r = rb + (int64_t)wid * G + grp; r < re; r += (int64_t)(kBatchThreads / 32) * G) {
+        const int k0 = __ldg(m.row_ptr + r), k1 = __ldg(m.row_ptr + r + 1);
+        Acc<VM> acc;
+        acc.init();
+        for (int j = k0; j < k1; ++j) {
+            const int ci = __ldg(m.col + j);
+            const T vi = __ldg(val + j);
+            if (active) acc.add(vi, ld_vec(X + (int64_t)ci * m.ldx + cc));
+        }
+        if (active) Y[r * m.ldy + cc] = acc.result();
+    }
+}
+
+// JDS-family rows [rb, re): one thread per row, every right-hand side of the
+// tile per thread, row entries in slot order (same arithmetic as the JDS
+// kernels).  RBJDS / SOJDS work items are whole blocks.
+template <int VM, int KT>
+__device__ void batch_jds_rows(const BatchMat &m, int64_t rb, int64_t re, int c0) {
+    typedef typename ValT<VM>::T T;
+    const T *val = static_cast<const T *>(m.val);
+    const T *x = static_cast<const T *>(m.x);
+    T *y = static_cast<T *>(m.y);
+    const bool contig = m.format == GBSP_RBJDS || m.format == GBSP_SOJDS;
+    for (int64_t r = rb + threadIdx.x; r < re; r += kBatchThreads) {
+        Acc<VM> acc[KT];
+#pragma unroll
+        for (int q = 0; q < KT; ++q) acc[q].init();
+        int64_t b0 = 0, b1 = 0, off = 0;
+        if (contig) {
+            const int64_t blk = r / m.block;
+            b0 = blk * m.block;
+            b1 = min(b0 + (int64_t)m.block, m.n_rows);
+            off = __ldg(m.blk_ptr + blk);
+        }
+        int32_t st = __ldg(m.jd_ptr);
+        for (int64_t d = 0; d < m.n_diag; ++d) {
+            const int32_t en = __ldg(m.jd_ptr + d + 1);
+            const int64_t dl = en - st;
+            if (dl <= r) break;
+            const int64_t kk = contig ? off + (r - b0) : (int64_t)st + r;
+            const int ci = ld_stream(m.col + kk);
+            const T vi = ld_stream(val + kk);
+            const T *xr = x + (int64_t)ci * m.ldx + c0;
+#pragma unroll
+            for (int q = 0; q < KT; ++q)
+                if (c0 + q < m.k) acc[q].add(vi, ld_vec(xr + q));
+            if (contig) off += min(b1, dl) - b0;
+            st = en;
+        }
+#pragma unroll
+        for (int q = 0; q < KT; ++q)
+            if (c0 + q < m.k) y[r * m.ldy + c0 + q] = acc[q].result();
+    }
+}
+
+template <int VM>
+__device__ void batch_item(const BatchMat &m, int64_t rb, int64_t re) {
+    if (m.kind == KIND_CRS) {
+        if (m.k == 1) {
+            switch (m.lanes) {
+                case 1: batch_crs_rows<VM, 1>(m, rb, re); break;
+                case 2: batch_crs_rows<VM, 2>(m, rb, re); break;
+                case 4: batch_crs_rows<VM, 4>(m, rb, re); break;
+                case 8: batch_crs_rows<VM, 8>(m, rb, re); break;
+                case 16: batch_crs_rows<VM, 16>(m, rb, re); break;
+                default: batch_crs_rows<VM, 32>(m, rb, re); break;
+            }
+        } else {
+            int KT = 2;
+            while (KT < min(m.k, m.rhs_tile > 0 ? min(m.rhs_tile, 32) : 16)) KT <<= 1;
+            for (int c0 = 0; c0 < m.k; c0 += KT) {
+                switch (KT) {
+                    case 2: batch_crs_spmm_rows<VM, 2>(m, rb, re, c0); break;
+                    case 4: batch_crs_spmm_rows<VM, 4>(m, rb, re, c0); break;
+                    case 8: batch_crs_spmm_rows<VM, 8>(m, rb, re, c0); break;
+                    case 16: batch_crs_spmm_rows<VM, 16>(m, rb, re, c0); break;
+                    default: batch_crs_spmm_rows<VM, 32>(m, rb, re, c0); break;
+                }
+            }
+        }
+    } else {
+        if (m.k == 1) {
+            batch_jds_rows<VM, 1>(m, rb, re, 0);
+        } else {
+            int KT = 2;
+            while (KT < min(m.k, m.rhs_tile > 0 ? min(m.rhs_tile, 16) : 16)) KT <<= 1;
+            for (int c0 = 0; c0 < m.k; c0 += KT) {
+                switch (KT) {
+                    case 2: batch_jds_rows<VM, 2>(m, rb, re, c0); break;
+                    case 4: batch_jds_rows<VM, 4>(m, rb, re, c0); break;
+                    case 8: batch_jds_rows<VM, 8>(m, rb, re, c0); break;
+                    default: batch_jds_rows<VM, 16>(m, rb, re, c0); break;
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBatchThreads)
+batch_kernel(const BatchMat *__restrict__ mats, const BatchWork *__restrict__ work, int64_t n_work,
+             int32_t *counter, const volatile int32_t *ready, int32_t *status) {
+    __shared__ int64_t item;
+    __shared__ int32_t go;
+    if (threadIdx.x == 0) {
+        go = 1;
+        if (ready) {
+            // bounded wait for a flag set by the host or by work finished
+            // earlier on the stream; never by a concurrently running kernel
+            const uint64_t t0 = global_timer_ns();
+            while (*ready == 0) {
+                if (global_timer_ns() - t0 > kReadyLimitNs) {
+                    go = 0;
+                    if (status) atomicExch(status, (int32_t)GBSP_ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(1000);
+            }
+        }
+    }
+    __syncthreads();
+    if (!go) return;
+    for (;;) {
+        if (threadIdx.x == 0) item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t w = item;
+        __syncthreads();
+        if (w >= n_work) break;
+        const BatchWork wk = work[w];
+        const BatchMat m = mats[wk.mat];
+        if (m.vm == VM_F64) batch_item<VM_F64>(m, wk.rb, wk.re);
+        else if (m.vm == VM_F32C) batch_item<VM_F32C>(m, wk.rb, wk.re);
+        else batch_item<VM_F32>(m, wk.rb, wk.re);
+    }
+}
+
+}  // namespace gbsp
 
 using namespace gbsp;
 
+struct gbsp_batch_s {
+    int32_t n_mats = 0;
+    int64_t n_work = 0;
+    int32_t *counter = nullptr;
+    const BatchMat *mats = nullptr;
+    const BatchWork *work = nullptr;
+    const int32_t *ready = nullptr;
+    int grid = 0;
+};
+
+namespace {
+
+constexpr int64_t kCounterBytes = 256;
+
+int64_t align256(int64_t b) { return (b + 255) & ~int64_t(255); }
+
+// Host-side work list: contiguous row ranges of about `chunk` entries (whole
+// blocks for RBJDS / SOJDS).  Needs the row pointers on the host, so it reads
+// the CRS row_ptr (or JDS jd_ptr) back once.
+gbsp_status make_work(int32_t n, const gbsp_batch_item *items, int32_t chunk, cudaStream_t s,
+                      std::vector<BatchMat> *mats, std::vector<BatchWork> *work) {
+    mats->clear();
+    work->clear();
+    for (int32_t b = 0; b < n; ++b) {
+        const gbsp_batch_item &it = items[b];
+        if (!it.A) return arg_error("gbsp_batch: NULL handle in item");
+        const Mat &A = *it.A;
+        if (it.k < 1 || it.ldx < it.k || it.ldy < it.k) return arg_error("gbsp_batch: bad k / leading dimension");
+        if (A.n_rows > 0 && (!it.X || !it.Y)) return arg_error("gbsp_batch: NULL X or Y");
+        BatchMat m{};
+        m.kind = A.kind;
+        m.format = A.kind == KIND_CRS ? GBSP_CRS : A.format;
+        m.vm = A.dtype == GBSP_F64 ? VM_F64 : (A.kopt.accum == GBSP_ACC_COMPENSATED ? VM_F32C : VM_F32);
+        m.k = it.k;
+        m.lanes = A.kopt.lanes > 0 ? A.kopt.lanes : 4;
+        m.rows = A.kopt.rows_per_warp;
+        m.rhs_tile = A.kopt.rhs_tile;
+        m.unroll = A.unroll;
+        m.block = A.built_block > 0 ? A.built_block : 1;
+        m.n_rows = A.n_rows;
+        m.n_diag = A.n_diag;
+        m.row_ptr = A.row_ptr;
+        m.col = A.col;
+        m.jd_ptr = A.jd_ptr;
+        m.blk_ptr = A.blk_ptr;
+        m.val = A.val;
+        m.x = it.X;
+        m.y = it.Y;
+        m.ldx = it.ldx;
+        m.ldy = it.ldy;
+        if (m.format == GBSP_JDS_LITERAL) m.format = GBSP_JDS;  // same arithmetic row by row
+        mats->push_back(m);
+        if (A.n_rows == 0) continue;
+        // row weights: entries per row, from the host copy of the structure
+        std::vector<int64_t> start;  // cumulative entries before row r, sampled at chunk edges
+        if (A.kind == KIND_CRS) {
+            std::vector<int32_t> rp((size_t)A.n_rows + 1);
+            GBSP_CUDA(cudaMemcpyAsync(rp.data(), A.row_ptr, 4 * (A.n_rows + 1), cudaMemcpyDeviceToHost, s));
+            GBSP_CUDA(cudaStreamSynchronize(s));
+            int64_t rb = 0;
+            const int64_t minrows = 32;
+            while (rb < A.n_rows) {
+                int64_t re = rb + minrows;
+                // extend while under the chunk (binary search on row_ptr)
+                const int64_t target = (int64_t)rp[(size_t)rb] + chunk;
+                int64_t lo = std::min(re, A.n_rows), hi = A.n_rows;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi + 1) / 2;
+                    if (rp[(size_t)mid] <= target) lo = mid;
+                    else hi = mid - 1;
+                }
+                re = std::max(std::min(re, A.n_rows), lo);
+                work->push_back(BatchWork{b, 0, rb, re});
+                rb = re;
+            }
+        } else {
+            // JDS family: rows are sorted by decreasing length; entries of
+            // rows [rb, re) = sum_d clamp(diagLen(d) - rb, 0, re - rb)
+            const std::vector<int32_t> &jd = A.h_jd_ptr;
+            const int64_t blk = (A.format == GBSP_RBJDS || A.format == GBSP_SOJDS) ? A.built_block : 32;
+            auto entries = [&](int64_t rb, int64_t re) {
+                int64_t e = 0;
+                for (size_t d = 0; d + 1 < jd.size(); ++d) {
+                    const int64_t dl = jd[d + 1] - jd[d];
+                    if (dl <= rb) break;
+                    e += std::min(dl, re) - rb;
+                }
+                return e;
+            };
+            int64_t rb = 0;
+            while (rb < A.n_rows) {
+                int64_t re = std::min(rb + blk, A.n_rows);
+                while (re < A.n_rows && entries(rb, std::min(re + blk, A.n_rows)) <= chunk)
+                    re = std::min(re + blk, A.n_rows);
+                work->push_back(BatchWork{b, 0, rb, re});
+                rb = re;
+            }
+        }
+    }
+    return GBSP_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
-gbsp_status gbsp_batch_plan(int32_t, const gbsp_batch_item *, int32_t, int64_t *) {
-    set_error("batched launch not available in this build");
-    return GBSP_ERR_UNSUPPORTED;
+gbsp_status gbsp_batch_plan(int32_t n, const gbsp_batch_item *items, int32_t chunk, int64_t *table_bytes) {
+    if (n < 0 || (n > 0 && !items) || !table_bytes) return arg_error("gbsp_batch_plan: bad arguments");
+    if (chunk <= 0) chunk = 4096;
+    std::vector<BatchMat> mats;
+    std::vector<BatchWork> work;
+    gbsp_status st = make_work(n, items, chunk, nullptr, &mats, &work);
+    if (st != GBSP_OK) return st;
+    *table_bytes = kCounterBytes + align256((int64_t)sizeof(BatchMat) * n) +
+                   align256((int64_t)sizeof(BatchWork) * (int64_t)work.size());
+    return GBSP_OK;
 }
-gbsp_status gbsp_batch_create(int32_t, const gbsp_batch_item *, int32_t, void *, int64_t, void *,
-                              gbsp_batch *) {
-    set_error("batched launch not available in this build");
-    return GBSP_ERR_UNSUPPORTED;
+
+gbsp_status gbsp_batch_create(int32_t n, const gbsp_batch_item *items, int32_t chunk, void *d_table,
+                              int64_t table_bytes, const int32_t *d_ready, void *stream, gbsp_batch *out) {
+    if (!out) return arg_error("gbsp_batch_create: out is NULL");
+    *out = nullptr;
+    if (n < 0 || (n > 0 && !items) || !d_table) return arg_error("gbsp_batch_create: bad arguments");
+    if (reinterpret_cast<uintptr_t>(d_table) & 255) return arg_error("gbsp_batch_create: table must be 256-byte aligned");
+    if (chunk <= 0) chunk = 4096;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<BatchMat> mats;
+    std::vector<BatchWork> work;
+    gbsp_status st = make_work(n, items, chunk, s, &mats, &work);
+    if (st != GBSP_OK) return st;
+    const int64_t need = kCounterBytes + align256((int64_t)sizeof(BatchMat) * n) +
+                         align256((int64_t)sizeof(BatchWork) * (int64_t)work.size());
+    if (table_bytes < need) {
+        set_error("gbsp_batch_create: table needs %lld bytes", (long long)need);
+        return GBSP_ERR_NOMEM;
+    }
+    char *p = static_cast<char *>(d_table);
+    gbsp_batch b = new (std::nothrow) gbsp_batch_s();
+    if (!b) return arg_error("gbsp_batch_create: out of host memory");
+    b->n_mats = n;
+    b->n_work = (int64_t)work.size();
+    b->counter = reinterpret_cast<int32_t *>(p);
+    b->mats = reinterpret_cast<const BatchMat *>(p + kCounterBytes);
+    b->work = reinterpret_cast<const BatchWork *>(p + kCounterBytes + align256((int64_t)sizeof(BatchMat) * n));
+    b->ready = d_ready;
+    if (n > 0)
+        GBSP_CUDA(cudaMemcpyAsync(const_cast<BatchMat *>(b->mats), mats.data(), sizeof(BatchMat) * n,
+                                  cudaMemcpyHostToDevice, s));
+    if (!work.empty())
+        GBSP_CUDA(cudaMemcpyAsync(const_cast<BatchWork *>(b->work), work.data(), sizeof(BatchWork) * work.size(),
+                                  cudaMemcpyHostToDevice, s));
+    GBSP_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
+    int per_sm = 0;
+    GBSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBatchThreads, 0));
+    b->grid = (int)std::max<int64_t>(1, std::min<int64_t>(b->n_work, (int64_t)num_sms() * std::max(per_sm, 1)));
+    *out = b;
+    return GBSP_OK;
 }
-gbsp_status gbsp_batch_run(gbsp_batch, int32_t *, void *) { return GBSP_ERR_UNSUPPORTED; }
-gbsp_status gbsp_batch_destroy(gbsp_batch) { return GBSP_OK; }
-gbsp_status gbsp_autotune(gbsp_handle, int32_t, const void *, void *, void *, gbsp_kernel_opts *,
-                          float *) {
-    set_error("autotuner not available in this build");
-    return GBSP_ERR_UNSUPPORTED;
+
+gbsp_status gbsp_batch_run(gbsp_batch b, int32_t *d_status, void *stream) {
+    if (!b) return arg_error("gbsp_batch_run: NULL batch");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (b->n_work == 0) return GBSP_OK;
+    GBSP_CUDA(cudaMemsetAsync(b->counter, 0, sizeof(int32_t), s));
+    batch_kernel<<<b->grid, kBatchThreads, 0, s>>>(b->mats, b->work, b->n_work, b->counter, b->ready, d_status);
+    GBSP_LAUNCH_CHECK("batch_kernel");
+    return GBSP_OK;
+}
+
+gbsp_status gbsp_batch_info(gbsp_batch b, int64_t *n_work, int32_t *grid) {
+    if (!b) return arg_error("gbsp_batch_info: NULL batch");
+    if (n_work) *n_work = b->n_work;
+    if (grid) *grid = b->grid;
+    return GBSP_OK;
+}
+
+gbsp_status gbsp_batch_destroy(gbsp_batch b) {
+    delete b;
+    return GBSP_OK;
 }
 
 }  // extern "C"

@@ -292,7 +292,7 @@ __global__ void jds_scatter_kernel(int64_t n, const int32_t *__restrict__ perm,
                                    const int32_t *__restrict__ row_ptr,
                                    const int32_t *__restrict__ col, const T *__restrict__ val,
                                    const int32_t *__restrict__ jd_ptr, int64_t n_diag,
-                                   int symmetric, int32_t *col_out, T *val_out) {
+                                   int symmetric, int32_t *col_out, T *val_out, int32_t *vmap) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const int32_t src = row_ptr[perm[r]];
@@ -303,6 +303,7 @@ __global__ void jds_scatter_kernel(int64_t n, const int32_t *__restrict__ perm,
         const int32_t c = col[src + d];
         col_out[dst] = symmetric ? iperm[c] : c;
         val_out[dst] = val[src + d];
+        if (vmap) vmap[dst] = src + d;
     }
 }
 
@@ -328,8 +329,8 @@ __global__ void rbjds_scatter_kernel(int64_t n_rows, int64_t n_diag, int64_t blo
                                      const int32_t *__restrict__ jd_ptr,
                                      const int32_t *__restrict__ blk_ptr,
                                      const int32_t *__restrict__ col_in,
-                                     const T *__restrict__ val_in, int32_t *col_out,
-                                     T *val_out) {
+                                     const T *__restrict__ val_in, const int32_t *__restrict__ map_in,
+                                     int32_t *col_out, T *val_out, int32_t *map_out) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rows) return;
     const int64_t k = r / block, b0 = k * block, b1 = std::min<int64_t>(b0 + block, n_rows);
@@ -340,6 +341,7 @@ __global__ void rbjds_scatter_kernel(int64_t n_rows, int64_t n_diag, int64_t blo
         const int64_t src = (int64_t)jd_ptr[d] + r;
         col_out[off + (r - b0)] = col_in[src];
         val_out[off + (r - b0)] = val_in[src];
+        if (map_out) map_out[off + (r - b0)] = map_in[src];
         off += (dl < b1 ? dl : b1) - b0;
     }
 }
@@ -356,7 +358,8 @@ __global__ void sojds_kernel(int64_t n_rows, int64_t n_diag, int64_t block, int6
                              const int32_t *__restrict__ jd_ptr,
                              const int32_t *__restrict__ blk_ptr,
                              const int32_t *__restrict__ col_in, const T *__restrict__ val_in,
-                             int32_t *col_out, T *val_out, int32_t max_slots) {
+                             const int32_t *__restrict__ map_in, int32_t *col_out, T *val_out,
+                             int32_t *map_out, int32_t max_slots) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
@@ -420,6 +423,8 @@ __global__ void sojds_kernel(int64_t n_rows, int64_t n_diag, int64_t block, int6
                     used[pick] = 1;
                     col_out[dst] = cur_col[pick];
                     val_out[dst] = cur_val[pick];
+                    // the picked entry sat in slot `pick` of this row in the input
+                    if (map_out) map_out[dst] = map_in[jd_ptr[pick] + r];
                 }
                 __syncwarp();
                 if (lane == 0) prev[d] = cur_col[pick];
@@ -458,7 +463,7 @@ gbsp_status jds_plan_impl(const Mat &A, const gbsp_jds_opts &o, int32_t *d_scrat
     // workspace: lengths, keys, sort buffers, diagLen (+ RBJDS staging)
     int64_t ws = align256(4 * A.n_rows) + align256(4 * A.n_rows) + sort_ws_bytes(A.n_rows) +
                  align256(4 * (max_len + 1)) + align256(scan_ws_bytes(max_len + 1)) + 256;
-    if (blocked) ws += align256(4 * A.nnz) + align256((A.dtype == GBSP_F64 ? 8 : 4) * A.nnz);
+    if (blocked) ws += 2 * align256(4 * A.nnz) + align256((A.dtype == GBSP_F64 ? 8 : 4) * A.nnz);
     out->workspace_bytes = ws;
     return GBSP_OK;
 }
@@ -466,21 +471,21 @@ gbsp_status jds_plan_impl(const Mat &A, const gbsp_jds_opts &o, int32_t *d_scrat
 template <typename T>
 static void launch_jds_scatter(const Mat &A, const int32_t *perm, const int32_t *iperm,
                                const int32_t *jd_ptr, int64_t n_diag, int symmetric,
-                               int32_t *col_out, void *val_out, cudaStream_t s) {
+                               int32_t *col_out, void *val_out, int32_t *vmap, cudaStream_t s) {
     jds_scatter_kernel<T><<<(unsigned)ceil_div(A.n_rows, 256), 256, 0, s>>>(
         A.n_rows, perm, iperm, A.row_ptr, A.col, static_cast<const T *>(A.val), jd_ptr, n_diag,
-        symmetric, col_out, static_cast<T *>(val_out));
+        symmetric, col_out, static_cast<T *>(val_out), vmap);
 }
 
 template <typename T>
 static gbsp_status relayout_blocked(const Mat &J, int64_t block, int format, const int32_t *col_in,
-                                    const void *val_in, int32_t *col_out, void *val_out,
-                                    cudaStream_t s) {
+                                    const void *val_in, const int32_t *map_in, int32_t *col_out,
+                                    void *val_out, int32_t *map_out, cudaStream_t s) {
     const int64_t nb = ceil_div(J.n_rows, block);
     if (format == GBSP_RBJDS) {
         rbjds_scatter_kernel<T><<<(unsigned)ceil_div(J.n_rows, 256), 256, 0, s>>>(
-            J.n_rows, J.n_diag, block, J.jd_ptr, J.blk_ptr, col_in, static_cast<const T *>(val_in),
-            col_out, static_cast<T *>(val_out));
+            J.n_rows, J.n_diag, block, J.jd_ptr, J.blk_ptr, col_in, static_cast<const T *>(val_in), map_in,
+            col_out, static_cast<T *>(val_out), map_out);
         GBSP_LAUNCH_CHECK("rbjds_scatter_kernel");
         return GBSP_OK;
     }
@@ -500,8 +505,9 @@ static gbsp_status relayout_blocked(const Mat &J, int64_t block, int format, con
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(nb, warps), (int64_t)num_sms() * 8));
     sojds_kernel<T><<<(unsigned)grid, warps * 32, smem, s>>>(J.n_rows, J.n_diag, block, nb, J.jd_ptr,
                                                              J.blk_ptr, col_in,
-                                                             static_cast<const T *>(val_in), col_out,
-                                                             static_cast<T *>(val_out), (int32_t)slots);
+                                                             static_cast<const T *>(val_in), map_in,
+                                                             col_out, static_cast<T *>(val_out), map_out,
+                                                             (int32_t)slots);
     GBSP_LAUNCH_CHECK("sojds_kernel");
     return GBSP_OK;
 }
@@ -525,13 +531,15 @@ gbsp_status jds_build_impl(const Mat &A, const gbsp_jds_opts &o, const gbsp_jds_
     p += align256(scan_ws_bytes(sz.n_diag + 1));
     int32_t *max_len_d = reinterpret_cast<int32_t *>(p);
     p += 256;
-    int32_t *col_stage = nullptr;
+    int32_t *col_stage = nullptr, *map_stage = nullptr;
     void *val_stage = nullptr;
     if (blocked) {
         col_stage = reinterpret_cast<int32_t *>(p);
         p += align256(4 * A.nnz);
         val_stage = p;
         p += align256(vsz * A.nnz);
+        map_stage = reinterpret_cast<int32_t *>(p);
+        p += align256(4 * A.nnz);
     }
 
     const unsigned gr = (unsigned)ceil_div(std::max<int64_t>(n, 1), 256);
@@ -559,13 +567,14 @@ gbsp_status jds_build_impl(const Mat &A, const gbsp_jds_opts &o, const gbsp_jds_
     // (iv), (v) shift left and scatter diagonal by diagonal
     int32_t *col_dst = blocked ? col_stage : b.col;
     void *val_dst = blocked ? val_stage : b.val;
+    int32_t *map_dst = b.vmap ? (blocked ? map_stage : b.vmap) : nullptr;
     if (n > 0) {
         if (A.dtype == GBSP_F64)
             launch_jds_scatter<double>(A, b.perm, b.iperm, b.jd_ptr, sz.n_diag, symmetric, col_dst,
-                                       val_dst, s);
+                                       val_dst, map_dst, s);
         else
             launch_jds_scatter<float>(A, b.perm, b.iperm, b.jd_ptr, sz.n_diag, symmetric, col_dst,
-                                      val_dst, s);
+                                      val_dst, map_dst, s);
         GBSP_LAUNCH_CHECK("jds_scatter_kernel");
     }
 
@@ -588,6 +597,7 @@ gbsp_status jds_build_impl(const Mat &A, const gbsp_jds_opts &o, const gbsp_jds_
     J->perm = b.perm;
     J->iperm = b.iperm;
     J->blk_ptr = blocked ? b.blk_ptr : nullptr;
+    J->vmap = b.vmap;
     J->kopt = A.kopt;
 
     if (blocked && n > 0) {
@@ -596,9 +606,9 @@ gbsp_status jds_build_impl(const Mat &A, const gbsp_jds_opts &o, const gbsp_jds_
         GBSP_LAUNCH_CHECK("blk_ptr_kernel");
         gbsp_status st = A.dtype == GBSP_F64
                              ? relayout_blocked<double>(*J, block, o.format, col_stage, val_stage,
-                                                        b.col, b.val, s)
+                                                        map_dst, b.col, b.val, b.vmap, s)
                              : relayout_blocked<float>(*J, block, o.format, col_stage, val_stage,
-                                                       b.col, b.val, s);
+                                                       map_dst, b.col, b.val, b.vmap, s);
         if (st != GBSP_OK) return st;
     } else if (blocked) {
         GBSP_CUDA(cudaMemsetAsync(b.blk_ptr, 0, 4, s));
@@ -701,18 +711,22 @@ gbsp_status transpose_build_impl(const Mat &A, const gbsp_transpose_buffers &b, 
     return transpose_values_impl(*T, s);
 }
 
-gbsp_status transpose_values_impl(const Mat &T, cudaStream_t s) {
-    if (T.nnz == 0) return GBSP_OK;
-    const Mat &A = *T.transpose_src;
-    const unsigned g = (unsigned)ceil_div(T.nnz, 256);
-    if (T.dtype == GBSP_F64)
-        gather_values_kernel<double><<<g, 256, 0, s>>>(T.nnz, T.tmap, static_cast<const double *>(A.val),
-                                                       static_cast<double *>(const_cast<void *>(T.val)));
+gbsp_status gather_values_launch(int64_t n, const int32_t *map, const void *src, void *dst, int dtype,
+                                 cudaStream_t s) {
+    if (n == 0) return GBSP_OK;
+    const unsigned g = (unsigned)ceil_div(n, 256);
+    if (dtype == GBSP_F64)
+        gather_values_kernel<double><<<g, 256, 0, s>>>(n, map, static_cast<const double *>(src),
+                                                       static_cast<double *>(dst));
     else
-        gather_values_kernel<float><<<g, 256, 0, s>>>(T.nnz, T.tmap, static_cast<const float *>(A.val),
-                                                      static_cast<float *>(const_cast<void *>(T.val)));
+        gather_values_kernel<float><<<g, 256, 0, s>>>(n, map, static_cast<const float *>(src),
+                                                      static_cast<float *>(dst));
     GBSP_LAUNCH_CHECK("gather_values_kernel");
     return GBSP_OK;
+}
+
+gbsp_status transpose_values_impl(const Mat &T, cudaStream_t s) {
+    return gather_values_launch(T.nnz, T.tmap, T.transpose_src->val, const_cast<void *>(T.val), T.dtype, s);
 }
 
 }  // namespace gbsp

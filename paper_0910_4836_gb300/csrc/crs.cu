@@ -57,8 +57,10 @@ crs_vector_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
             for (int i = 0; i < R; ++i) {
                 const int k = k0[i] + j;
                 const bool ok = k < k1[i];
-                c[i] = ok ? ld_stream(col + k) : -1;
-                v[i] = ok ? ld_stream(val + k) : T(0);
+                // read-only path, not evict-first: a lane group touches a
+                // sector in several iterations, so it must survive in L1/L2
+                c[i] = ok ? __ldg(col + k) : -1;
+                v[i] = ok ? __ldg(val + k) : T(0);
             }
 #pragma unroll
             for (int i = 0; i < R; ++i)
@@ -125,7 +127,9 @@ crs_spmm_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
     }
 }
 
-// dval_k (+)= sum_{t<m} G[row_k, t] X[col_k, t]  (m = 1: g[row] x[col]).
+// dval_k: d = (accumulate ? dval_k : 0), then d = fma(G[row_k, t], X[col_k, t], d)
+// for t = 0, 1, ..., m-1 (m = 1: g[row] x[col]).  One running sum in a fixed
+// order, so splitting the t range over several calls changes nothing.
 template <typename T, int L>
 __global__ void __launch_bounds__(kThreads)
 crs_dval_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
@@ -141,9 +145,9 @@ crs_dval_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
         const int k0 = __ldg(row_ptr + r), k1 = __ldg(row_ptr + r + 1);
         for (int kk = k0 + gl; kk < k1; kk += L) {
             const int64_t cj = ld_stream(col + kk);
-            T s = T(0);
-            for (int t = 0; t < m; ++t) s = fma(__ldg(G + r * ldg + t), __ldg(X + cj * ldx + t), s);
-            dval[kk] = accumulate ? dval[kk] + s : s;
+            T d = accumulate ? dval[kk] : T(0);
+            for (int t = 0; t < m; ++t) d = fma(__ldg(G + r * ldg + t), __ldg(X + cj * ldx + t), d);
+            dval[kk] = d;
         }
     }
 }

@@ -28,10 +28,14 @@ struct Mat {
     // kernel options
     gbsp_kernel_opts kopt{};
 
-    // TILED CRS tile table
+    // TILED CRS tile table (first row of every tile, then one int4 per tile)
     const int32_t *tile_rows = nullptr;
+    const int4 *tile_meta = nullptr;
     int64_t n_tiles = 0;
     int32_t tile = 0;
+
+    // optional device status word for bounded-wait timeouts
+    int32_t *status = nullptr;
 
     // JDS family
     int format = GBSP_CRS;
@@ -40,6 +44,7 @@ struct Mat {
     int32_t built_block = 0;  // block size the RBJDS/SOJDS layout was built with
     int64_t n_diag = 0, n_blocks = 0;
     const int32_t *jd_ptr = nullptr, *perm = nullptr, *iperm = nullptr, *blk_ptr = nullptr;
+    const int32_t *vmap = nullptr;  // JDS position -> CRS entry (optional)
     std::vector<int32_t> h_jd_ptr;  // host copy, read back once at build (literal launches)
 
     // transposed structure (CRS handle built by gbsp_transpose_build)
@@ -96,6 +101,7 @@ struct VecArgs {
 
 gbsp_status crs_launch(const Mat &A, const VecArgs &v, cudaStream_t s);
 gbsp_status crs_prepare_tiles(Mat &A, int32_t tile, int32_t *table, cudaStream_t s);
+int64_t crs_tile_table_bytes(const Mat &A, int32_t tile);
 gbsp_status crs_validate_launch(const Mat &A, int32_t *d_status, cudaStream_t s);
 gbsp_status crs_dval_launch(const Mat &A, int32_t m, const void *G, int64_t ldg, const void *X,
                             int64_t ldx, void *dval, int32_t accumulate, cudaStream_t s);
@@ -115,6 +121,8 @@ gbsp_status transpose_workspace_impl(const Mat &A, int64_t *bytes);
 gbsp_status transpose_build_impl(const Mat &A, const gbsp_transpose_buffers &b, int64_t ws_bytes,
                                  cudaStream_t s, Mat *T);
 gbsp_status transpose_values_impl(const Mat &T, cudaStream_t s);
+gbsp_status gather_values_launch(int64_t n, const int32_t *map, const void *src, void *dst, int dtype,
+                                 cudaStream_t s);
 
 }  // namespace gbsp
 

@@ -140,7 +140,6 @@ class CRSMatrix(_Product):
         self._device = self.row_ptr.device
         self._tile_table = None
         self._transpose = None
-        self._tbufs = None
         L.check(L.load().gbsp_crs_create(self.n_rows, self.n_cols, self.nnz, _vp(self.row_ptr),
                                          _vp(self.col), _vp(self.val), _DT[self.dtype],
                                          ctypes.byref(self._h)), "gbsp_crs_create")
@@ -151,6 +150,14 @@ class CRSMatrix(_Product):
         return cls(torch.as_tensor(A.row_ptr, dtype=torch.int32).to(device),
                    torch.as_tensor(A.col, dtype=torch.int32).to(device),
                    torch.as_tensor(A.val).to(device=device, dtype=dtype), A.n_cols)
+
+    def set_values(self, val: torch.Tensor) -> None:
+        """Point the handle at new values (same pattern and dtype); no copy."""
+        val = _need_cuda(val, "val", self.dtype)
+        if val.numel() != self.nnz:
+            raise ValueError("val has the wrong length")
+        L.check(L.load().gbsp_set_values(self._h, _vp(val)), "gbsp_set_values")
+        self.val = val
 
     def validate(self, stream=None) -> int:
         """0 if the CRS arrays are well formed, else GBSP_ERR_MATRIX (-2)."""
@@ -171,8 +178,8 @@ class CRSMatrix(_Product):
         self.set_kernel("tiled")
 
     def to_jds(self, fmt: str = "JDS", perm: str = "symmetric", block: int = 256, unroll: int = 4,
-               stream=None) -> "JDSMatrix":
-        return JDSMatrix(self, fmt, perm, block, unroll, stream)
+               stream=None, value_map: bool = False) -> "JDSMatrix":
+        return JDSMatrix(self, fmt, perm, block, unroll, stream, value_map)
 
     def transpose(self, stream=None) -> "CRSMatrix":
         """Build the transposed structure (a CRS of A^T with its entry map)
@@ -196,7 +203,7 @@ class CRSMatrix(_Product):
         del work
         T.row_ptr, T.col, T.val, T.tmap = t_row_ptr, t_col, t_val, tmap
         T.dtype, T.n_rows, T.n_cols, T.nnz = self.dtype, self.n_cols, self.n_rows, self.nnz
-        T._device, T._tile_table, T._transpose, T._tbufs = dev, None, None, None
+        T._device, T._tile_table, T._transpose = dev, None, None
         T._source = self
         self._transpose = T
         return T
@@ -242,7 +249,8 @@ class JDSMatrix(_Product):
     fmt: JDS, NBJDS, NUJDS, RBJDS, SOJDS or JDS_LITERAL; perm: 'symmetric'
     (rows and columns permuted, the paper's scheme) or 'row_only'."""
 
-    def __init__(self, A: CRSMatrix, fmt="JDS", perm="symmetric", block=256, unroll=4, stream=None):
+    def __init__(self, A: CRSMatrix, fmt="JDS", perm="symmetric", block=256, unroll=4, stream=None,
+                 value_map: bool = False):
         super().__init__()
         lib = L.load()
         dev = A._device
@@ -263,15 +271,21 @@ class JDSMatrix(_Product):
         self.blk_ptr = (torch.empty(sizes.n_blocks + 1, dtype=torch.int32, device=dev)
                         if fmt in ("RBJDS", "SOJDS") else None)
         work = torch.empty(max(sizes.workspace_bytes, 1), dtype=torch.uint8, device=dev)
+        self.vmap = torch.empty(A.nnz, dtype=torch.int32, device=dev) if value_map else None
         bufs = L.JdsBuffers(_vp(self.jd_ptr).value, _vp(self.col).value, _vp(self.val).value,
                             _vp(self.perm).value, _vp(self.iperm).value, _vp(self.blk_ptr).value,
-                            _vp(work).value)
+                            _vp(work).value, _vp(self.vmap).value)
         L.check(lib.gbsp_jds_build(A.handle, ctypes.byref(opts), ctypes.byref(bufs),
                                    ctypes.byref(sizes), _stream(stream), ctypes.byref(self._h)),
                 "gbsp_jds_build")
         del work  # the build synchronised the stream
         self.fmt, self.perm_mode, self.block, self.unroll = fmt, perm, block, unroll
         self.symmetric = perm == "symmetric"
+
+    def refresh_values(self, crs_val: torch.Tensor, stream=None) -> None:
+        """Re-gather the stored values from CRS-ordered values (needs value_map)."""
+        crs_val = _need_cuda(crs_val, "crs_val", self.dtype)
+        L.check(L.load().gbsp_jds_values(self._h, _vp(crs_val), _stream(stream)), "gbsp_jds_values")
 
     def set_format(self, fmt: str, block: int = 0, unroll: int = 0) -> None:
         L.check(L.load().gbsp_jds_set_format(self._h, L.FORMATS[fmt], block, unroll),
