@@ -362,6 +362,32 @@ gbsp_status gbsp_batch_run(gbsp_batch b, int32_t *d_status, void *stream);
 gbsp_status gbsp_batch_info(gbsp_batch b, int64_t *n_work, int32_t *grid);
 gbsp_status gbsp_batch_destroy(gbsp_batch b);
 
+/* ------------------------------------------------------ allocation-free -- */
+
+/* y = A x (or y += A x) for a CRS matrix in ONE call that allocates
+ * nothing: no handle, no plan buffer, no cudaMalloc / cudaFree and no
+ * allocating library routine.  It is for callers that cannot allocate
+ * device memory themselves -- for example a solver whose device memory all
+ * belongs to a host application's pool, or code on a path where an
+ * allocation is not allowed because it would synchronise the device.  (The
+ * paper has no counterpart; this is a library convenience.)
+ *
+ * Arguments are those of gbsp_crs_create plus x (n_cols), y (n_rows) and
+ * `accumulate`; row_ptr, col and val must be 16-byte aligned.  It runs the
+ * TILED kernel with 1024-item tiles, whose tile table is built on every call
+ * in a fixed 8 MiB array of device memory inside the library (held by every
+ * GPU that loads the library until the process exits), so n_rows + nnz may
+ * be at most about 4.1e8; larger sizes return GBSP_ERR_ARG with a message.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress), so make the first call on each device before any
+ * stream capture.  All calls share the one array and rewrite it fully:
+ * calls that can overlap on the GPU (different streams without ordering)
+ * race and give wrong results; calls ordered on one stream are safe. */
+gbsp_status gbsp_crs_spmv_noalloc(int64_t n_rows, int64_t n_cols, int64_t nnz,
+                                  const int32_t *d_row_ptr, const int32_t *d_col,
+                                  const void *d_val, gbsp_dtype dtype, int32_t accumulate,
+                                  const void *d_x, void *d_y, void *stream);
+
 /* ------------------------------------------------------------ autotuner -- */
 
 /* Time the candidate kernels for `A` with k right-hand sides on the device

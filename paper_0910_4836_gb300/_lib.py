@@ -96,6 +96,8 @@ SIGNATURES = {
     "gbsp_batch_info": (c_i32, [c_vp, P(c_i64), P(c_i32)]),
     "gbsp_batch_destroy": (c_i32, [c_vp]),
     "gbsp_autotune": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp, P(KernelOpts), P(c_f32)]),
+    "gbsp_crs_spmv_noalloc": (c_i32, [c_i64, c_i64, c_i64, c_vp, c_vp, c_vp, c_i32, c_i32, c_vp, c_vp,
+                                      c_vp]),
 }
 
 _lib = None

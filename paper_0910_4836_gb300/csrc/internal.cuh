@@ -102,6 +102,7 @@ struct VecArgs {
 gbsp_status crs_launch(const Mat &A, const VecArgs &v, cudaStream_t s);
 gbsp_status crs_prepare_tiles(Mat &A, int32_t tile, int32_t *table, cudaStream_t s);
 int64_t crs_tile_table_bytes(const Mat &A, int32_t tile);
+gbsp_status crs_tiled_launch(const Mat &A, const VecArgs &v, cudaStream_t s);
 gbsp_status crs_validate_launch(const Mat &A, int32_t *d_status, cudaStream_t s);
 gbsp_status crs_dval_launch(const Mat &A, int32_t m, const void *G, int64_t ldg, const void *X,
                             int64_t ldx, void *dval, int32_t accumulate, cudaStream_t s);
