@@ -28,19 +28,21 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "SpMVM GFlop/s & HBM GB/s vs roofline; batched & fwd+bwd speedup vs plain"
-WORKLOAD = "hh_like N=6,000,000 FP64 CRS SpMVM (symmetric banded + 20% scattered, ~13 nnz/row)"
+WORKLOAD = ("hh_like N=6,000,000 FP64 SpMVM, fastest of CRS and the JDS family "
+            "(symmetric banded + 20% scattered, ~13 nnz/row)")
 FALLBACK_HBM_GBS = 6800.0
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--steps", type=int, default=3000)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", type=int, default=1, choices=[1, 2, 4])
-    p.add_argument("--kernel", default="auto", help="auto | tiled | vector")
-    p.add_argument("--no-formats", action="store_true", help="skip the per-format table")
+    p.add_argument("--kernel", default="auto", help="auto, or a name prefix (CRS, JDS, NUJDS, ...)")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the FP32, batched and forward+backward measurements")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     return p.parse_args()
 
@@ -138,7 +140,7 @@ def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0910_4836_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.startswith("crs") or f.endswith(".cuh"):
+        if f.endswith((".cu", ".cuh")):
             with open(os.path.join(csrc, f), "rb") as fh:
                 h.update(fh.read())
     return h.hexdigest()[:12]
@@ -152,24 +154,8 @@ NCU_TRAFFIC = {}
 
 # --------------------------------------------------------------- ours ------
 
-def run_ours(args):
+def _timer(dev):
     import torch
-    world, rank, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    dev = torch.device("cuda", local if world > 1 else 0)
-    torch.cuda.set_device(dev)
-
-    import paper_0910_4836_gb300 as g
-    from paper_0910_4836_gb300 import CRSMatrix, JDSMatrix  # noqa: F401
-    g.build()
-
-    A, x_host = make_workload(args.config)
-    M = CRSMatrix.from_host(A, device=dev, dtype=torch.float64)
-    x = torch.as_tensor(x_host).to(dev)
-    y = torch.empty(A.n_rows, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def time_launches(fn, reps):
@@ -182,30 +168,82 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         return [ev[i].elapsed_time(ev[i + 1]) for i in range(reps)]
 
-    # kernel choice: the tuned candidates, fastest over a few timed launches
-    candidates = []
-    if args.kernel in ("auto", "tiled"):
-        candidates += [("tiled", t) for t in (2048, 1024)]
-    if args.kernel in ("auto", "vector"):
-        candidates += [("vector", (l, r)) for l, r in ((8, 2), (8, 4), (16, 2), (4, 4))]
-    best = None
-    for kind, p in candidates:
-        if kind == "tiled":
-            M.prepare_tiled(p)
-        else:
-            M.set_kernel("vector", lanes=p[0], rows_per_warp=p[1])
-        t = statistics.median(time_launches(lambda: M.spmv(x, out=y), 5))
+    return time_launches
+
+
+def candidates(M, A, x):
+    """(name, handle, input vector, algorithmic bytes, setting) of every
+    storage scheme and kernel option on this matrix (the paper's serial
+    comparison of Sect. 3.2, on GB300).  JDS-family inputs are in their
+    permuted basis."""
+    crs_b = algorithmic_bytes(A.n_rows, A.n_cols, A.nnz)
+    out = []
+    for l, r in ((4, 4), (8, 2), (16, 2)):
+        out.append((f"CRS vector l{l} r{r}", M, x, crs_b, ("vector", l, r)))
+    for t in (1024, 2048):
+        out.append((f"CRS tiled {t}", M, x, crs_b, ("tiled", t)))
+    for perm in ("symmetric", "row_only"):
+        J = M.to_jds("JDS", perm)
+        xp = J.permute(x) if perm == "symmetric" else x
+        jb = 12 * A.nnz + 4 * (J.n_diag + 1) + 8 * A.n_cols + 8 * A.n_rows
+        for fmt, b, u in (("JDS", 0, 0), ("NUJDS", 0, 2), ("NUJDS", 0, 4), ("NUJDS", 0, 8),
+                          ("NBJDS", 1024, 0), ("NBJDS", 2048, 0), ("JDS_LITERAL", 0, 0)):
+            name = f"{fmt} {perm}" + (f" b={b}" if b else "") + (f" u={u}" if u else "")
+            out.append((name, J, xp, jb, ("jds", fmt, b, u)))
+        for fmt in ("RBJDS", "SOJDS"):
+            R = M.to_jds(fmt, perm, block=1024)
+            rb = jb + 4 * (R.n_blocks + 1)
+            out.append((f"{fmt} {perm} b=1024", R, xp, rb, ("fixed",)))
+    return out
+
+
+def configure(H, how):
+    if how[0] == "vector":
+        H.set_kernel("vector", lanes=how[1], rows_per_warp=how[2])
+    elif how[0] == "tiled":
+        H.prepare_tiled(how[1])
+    elif how[0] == "jds":
+        H.set_format(how[1], block=how[2], unroll=how[3])
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    import paper_0910_4836_gb300 as g
+    from paper_0910_4836_gb300 import CRSMatrix
+    g.build()
+    time_launches = _timer(dev)
+
+    A, x_host = make_workload(args.config)
+    M = CRSMatrix.from_host(A, device=dev, dtype=torch.float64)
+    x = torch.as_tensor(x_host).to(dev)
+    y = torch.empty(A.n_rows, dtype=torch.float64, device=dev)
+    peak, peak_kind = peaks()
+
+    # every scheme timed (median of 10 launches); the fastest is the step
+    table, best = {}, None
+    for name, H, xin, nbytes, how in candidates(M, A, x):
+        if args.kernel != "auto" and not name.startswith(args.kernel):
+            continue
+        configure(H, how)
+        t = statistics.median(time_launches(lambda: H.spmv(xin, out=y), 10))
+        table[name] = {"gflops": round(2.0 * A.nnz / (t * 1e-3) / 1e9, 1),
+                       "gbs": round(nbytes / (t * 1e-3) / 1e9, 1), "ms": round(t, 4),
+                       "frac": round(nbytes / (t * 1e-3) / 1e9 / peak, 3)}
         if best is None or t < best[0]:
-            best = (t, kind, p)
-    _, kind, p = best
-    if kind == "tiled":
-        M.prepare_tiled(p)
-    else:
-        M.set_kernel("vector", lanes=p[0], rows_per_warp=p[1])
-    kernel_desc = f"{kind} {p}"
+            best = (t, name, H, xin, nbytes, how)
+    _, kname, H, xin, alg, how = best
+    configure(H, how)
 
     def step():
-        M.spmv(x, out=y)
+        H.spmv(xin, out=y)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -225,28 +263,28 @@ def run_ours(args):
     ms = total_ms / args.steps
     flops = 2.0 * A.nnz
     gflops = world * flops / (ms * 1e-3) / 1e9
-    alg = algorithmic_bytes(A.n_rows, A.n_cols, A.nnz)
     gbs = alg / (ms * 1e-3) / 1e9
-    peak, peak_kind = peaks()
     h = kernel_source_hash()
-    traffic = NCU_TRAFFIC.get((args.config, kind, str(p), h))
+    traffic = NCU_TRAFFIC.get((args.config, kname, h))
 
-    # end to end through the public API: pinned host x in, host y out
-    xh = torch.as_tensor(x_host).pin_memory()
+    # end to end through the public API: pinned host input in, host result out
+    xh = xin.detach().cpu().pin_memory()
     yh = torch.empty(A.n_rows, dtype=torch.float64).pin_memory()
+    xd = torch.empty_like(xin)
 
     def e2e_step():
-        x.copy_(xh, non_blocking=True)
-        M.spmv(x, out=y)
+        xd.copy_(xh, non_blocking=True)
+        H.spmv(xd, out=y)
         yh.copy_(y, non_blocking=True)
 
     for _ in range(3):
         e2e_step()
-    et = time_launches(e2e_step, max(5, min(args.steps, 20)))
+    et = time_launches(e2e_step, 50)
     e2e_ms = sum(et) / len(et)
 
     result = None
     if rank == 0:
+        basis = "original basis" if kname.startswith("CRS") else "permuted basis (Sect. 2)"
         result = {
             "metric": METRIC, "value": round(gflops, 2), "unit": "GFlop/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 5),
@@ -254,7 +292,7 @@ def run_ours(args):
             "data": "synthetic (seeded SplitMix64; stand-in for the paper's Holstein-Hubbard matrix)",
             "hbm_gbs": round(gbs, 1),
             "config": {"workload": WORKLOAD, "config_index": args.config, "n_rows": A.n_rows,
-                       "nnz": A.nnz, "kernel": kernel_desc,
+                       "nnz": A.nnz, "kernel": kname, "vectors": basis,
                        "l2": "inputs larger than L2 (matrix ~1 GB), no flush",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
@@ -264,11 +302,17 @@ def run_ours(args):
             "e2e": {"value": round(world * flops / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GFlop/s",
                     "h2d_bytes_per_step": 8 * A.n_cols, "d2h_bytes_per_step": 8 * A.n_rows,
                     "ms_per_step": round(e2e_ms, 4)},
-            "gpu_launches": args.steps * launches_per_step(kind),
+            "gpu_launches": args.steps * launches_per_step(kname, H),
             "clocks": clk.summary(),
+            "formats": table,
         }
-        if not args.no_formats:
-            result["formats"] = format_table(M, A, x, time_launches, dev, peak)
+        if not args.no_extras:
+            result["fp32"] = fp32_numbers(M, A, x, y, dev, time_launches, table[kname]["ms"])
+            del table
+            torch.cuda.empty_cache()
+            result["batched"] = batched_speedups(dev, time_launches)
+            torch.cuda.empty_cache()
+            result["fwd_bwd"] = fwd_bwd_speedup(dev, time_launches)
         result["cpu_baseline"] = cpu_baseline(A, x_host, args.cpu_seconds)
     if world > 1:
         torch.distributed.barrier()
@@ -276,45 +320,143 @@ def run_ours(args):
     return result
 
 
-def launches_per_step(kind):
+def launches_per_step(kname, H):
+    if kname.startswith("JDS_LITERAL"):
+        return int(H.n_diag) + 1  # one zeroing launch and one launch per diagonal
     return 1
 
 
-def format_table(M, A, x, time_launches, dev, peak):
-    """GFlop/s of every storage scheme on the same matrix (the paper's
-    serial comparison, on GB300): median of 10 launches each."""
+
+# ------------------------------------------------------------- extras ------
+
+def fp32_numbers(M, A, x, y64, dev, time_launches, ms64):
+    """FP32 values with compensated (Dot2) row sums on the same matrix: speed
+    and the error against the FP64 GPU result, relative to sum |a||x|."""
     import torch
-    out = {}
-    flops = 2.0 * A.nnz
-    y = torch.empty(A.n_rows, dtype=torch.float64, device=dev)
+    from paper_0910_4836_gb300 import CRSMatrix
+    M32 = CRSMatrix(M.row_ptr, M.col, M.val.float(), A.n_cols)
+    M32.set_kernel("vector", compensated=True)
+    x32 = x.float()
+    y32 = torch.empty(A.n_rows, dtype=torch.float32, device=dev)
+    J32 = M32.to_jds("NUJDS", "symmetric", unroll=4)
+    xp32 = J32.permute(x32)
+    res = {}
+    opts = [("CRS vector l4 r4", M32, x32, lambda: M32.set_kernel("vector", lanes=4, rows_per_warp=4)),
+            ("CRS tiled 1024", M32, x32, lambda: M32.prepare_tiled(1024)),
+            ("NUJDS symmetric u=4", J32, xp32, lambda: None)]
+    best = None
+    for name, H, xin, conf in opts:
+        conf()
+        t = statistics.median(time_launches(lambda: H.spmv(xin, out=y32), 10))
+        res[name] = {"gflops": round(2.0 * A.nnz / (t * 1e-3) / 1e9, 1), "ms": round(t, 4),
+                     "gbs": round((8 * A.nnz + 4 * (A.n_rows + 1) + 4 * (A.n_rows + A.n_cols))
+                                  / (t * 1e-3) / 1e9, 1)}
+        if best is None or t < best[0]:
+            best = (t, name)
+    # accuracy against the FP64 product on the GPU (itself within 1e-14 of the oracle)
+    M.set_kernel("vector", lanes=4, rows_per_warp=4)
+    ref = M.spmv(x)
+    Mabs = CRSMatrix(M.row_ptr, M.col, M.val.abs(), A.n_cols)
+    sabs = Mabs.spmv(x.abs())
+    M32.set_kernel("vector", lanes=4, rows_per_warp=4, compensated=True)
+    yc = M32.spmv(x32).double()
+    M32.set_kernel("vector", lanes=4, rows_per_warp=4, compensated=False)
+    yp = M32.spmv(x32).double()
+    den = sabs.clamp_min(1e-300)
+    return {"best": best[1], "speedup_vs_fp64": round(ms64 / best[0], 3), "kernels": res,
+            "max_err_over_sum_abs_compensated": float(((yc - ref).abs() / den).max()),
+            "max_err_over_sum_abs_plain": float(((yp - ref).abs() / den).max()),
+            "note": "error of FP32 data and FP32 vector against the FP64 product of the FP64 data"}
 
-    def rec(name, fn, nbytes):
-        t = statistics.median(time_launches(fn, 10))
-        out[name] = {"gflops": round(flops / (t * 1e-3) / 1e9, 1),
-                     "gbs": round(nbytes / (t * 1e-3) / 1e9, 1), "ms": round(t, 4)}
 
-    alg = algorithmic_bytes(A.n_rows, A.n_cols, A.nnz)
-    for l, r in ((4, 4), (8, 2), (16, 2), (32, 1)):
-        M.set_kernel("vector", lanes=l, rows_per_warp=r)
-        rec(f"CRS vector l{l} r{r}", lambda: M.spmv(x, out=y), alg)
-    for t in (1024, 2048):
-        M.prepare_tiled(t)
-        rec(f"CRS tiled {t}", lambda: M.spmv(x, out=y), alg)
-    jalg = 12 * A.nnz + 16 * A.n_rows  # permuted basis; jd_ptr is negligible
-    for perm in ("symmetric", "row_only"):
-        J = M.to_jds("JDS", perm)
-        xp = J.permute(x) if perm == "symmetric" else x
-        for fmt, b, u in (("JDS", 0, 0), ("NUJDS", 0, 4), ("NBJDS", 1024, 0), ("JDS_LITERAL", 0, 0)):
-            J.set_format(fmt, block=b, unroll=u)
-            rec(f"{fmt} {perm}" + (f" b={b}" if b else "") + (f" u={u}" if u else ""),
-                lambda: J.spmv(xp, out=y), jalg)
-        del J
-        for fmt in ("RBJDS", "SOJDS"):
-            R = M.to_jds(fmt, perm, block=1024)
-            rec(f"{fmt} {perm} b=1024", lambda: R.spmv(xp, out=y), jalg)
-            del R
+def batched_speedups(dev, time_launches):
+    """256 uneven matrices (half 7-point stencils, half random rows) in one
+    persistent launch replayed from a CUDA graph, against the plain path:
+    one CRS launch per matrix and right-hand side, no graph."""
+    import torch
+    from paper_0910_4836_gb300 import Batch, CRSMatrix, synth as S
+    mats = S.batch_set(256, 3)
+    out = {"matrices": len(mats), "rows": int(sum(m.n_rows for m in mats)),
+           "nnz": int(sum(m.nnz for m in mats))}
+    for dtype, kmode in ((torch.float64, "1"), (torch.float64, "16"), (torch.float64, "mixed"),
+                         (torch.float32, "mixed")):
+        ks = S.batch_k(len(mats), kmode)
+        bt, handles, Xs, Ys = Batch.autotuned(mats, ks, dtype, device=dev)
+        for X in Xs:
+            X.uniform_(-1, 1)
+        g = bt.graph()
+        t_batch = statistics.median(time_launches(g.replay, 20))
+        plain = [CRSMatrix(h.row_ptr, h.col, h.val, h.n_cols) if isinstance(h, CRSMatrix)
+                 else CRSMatrix.from_host(m, device=dev, dtype=dtype) for h, m in zip(handles, mats)]
+        for P in plain:
+            if dtype == torch.float32:
+                P.set_kernel("vector", compensated=True)
+        cols = [[torch.empty(m.n_cols, dtype=dtype, device=dev).uniform_(-1, 1) for _ in range(k)]
+                for m, k in zip(mats, ks)]
+        outs = [torch.empty(m.n_rows, dtype=dtype, device=dev) for m in mats]
+
+        def plain_run():
+            for P, cs, o in zip(plain, cols, outs):
+                for c in cs:
+                    P.spmv(c, out=o)
+
+        t_plain = statistics.median(time_launches(plain_run, 5))
+        flops = sum(2.0 * m.nnz * k for m, k in zip(mats, ks))
+        nw, grid = bt.info()
+        out[f"{'f64' if dtype == torch.float64 else 'f32'}_k{kmode}"] = {
+            "batched_ms": round(t_batch, 4), "plain_ms": round(t_plain, 4),
+            "speedup": round(t_plain / t_batch, 2), "batched_gflops": round(flops / (t_batch * 1e-3) / 1e9, 1),
+            "launches_plain": int(sum(ks)), "work_items": nw, "ctas": grid,
+            "jds_items": sum(1 for h in handles if not isinstance(h, CRSMatrix))}
+        del bt, handles, Xs, Ys, plain, cols, outs, g
         torch.cuda.empty_cache()
     return out
+
+
+def fwd_bwd_speedup(dev, time_launches):
+    """loss = ||A^20 x||^2 on the 27-point stencil, 100^3: forward and
+    backward, plain (all 20 activations stored, one dval launch per step)
+    against tuned (checkpoint every 5 steps, fused multi-step dval)."""
+    import torch
+    from paper_0910_4836_gb300 import synth as S
+    from paper_0910_4836_gb300.autograd import Pattern, power_apply
+    A = S.stencil27(100, 4)
+    m = 20
+    res = {"n_rows": A.n_rows, "nnz": A.nnz, "m": m}
+    for dtype in (torch.float64, torch.float32):
+        p = Pattern.from_host(A, device=dev, dtype=dtype)
+        val = torch.as_tensor(A.val).to(device=dev, dtype=dtype)
+        x0 = torch.as_tensor(S.vector(A.n_cols, 4)).to(device=dev, dtype=dtype)
+        M = p.bind(val)
+        p.adjoint_op(val)  # build the transposed structure once
+        AT = p.AT
+
+        def plain():
+            xs = [x0]
+            for _ in range(m):
+                xs.append(M.spmv(xs[-1]))
+            g = 2 * xs[-1]
+            dval = torch.zeros(A.nnz, dtype=dtype, device=dev)
+            for t in range(m, 0, -1):
+                M.dval(g, xs[t - 1], out=dval, accumulate=True)
+                g = AT.spmv(g)
+            return dval, g
+
+        def tuned(c=5):
+            v = val.clone().requires_grad_(True)
+            xx = x0.clone().requires_grad_(True)
+            y = power_apply(p, v, xx, m, checkpoint=c)
+            (y * y).sum().backward()
+            return v.grad, xx.grad
+
+        for _ in range(2):
+            plain(), tuned()
+        tp = statistics.median(time_launches(plain, 5))
+        tt = statistics.median(time_launches(tuned, 5))
+        key = "f64" if dtype == torch.float64 else "f32"
+        res[key] = {"plain_ms": round(tp, 3), "tuned_ms": round(tt, 3), "speedup": round(tp / tt, 3),
+                    "vectors_stored_plain": m + 1, "vectors_stored_tuned": m // 5 + 5}
+    return res
 
 
 # ------------------------------------------------------------ CPU side -----
