@@ -44,6 +44,9 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the FP32, batched and forward+backward measurements")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--ncu-case", action="store_true",
+                   help="no timing: run 3 launches of the --kernel candidate on a 2,000,000-row "
+                        "HH-like matrix (larger than L2, small enough for an ncu capture)")
     return p.parse_args()
 
 
@@ -171,26 +174,34 @@ def _timer(dev):
     return time_launches
 
 
-def candidates(M, A, x):
+def candidates(M, A, x, only=None):
     """(name, handle, input vector, algorithmic bytes, setting) of every
     storage scheme and kernel option on this matrix (the paper's serial
     comparison of Sect. 3.2, on GB300).  JDS-family inputs are in their
-    permuted basis."""
+    permuted basis.  `only`: a name prefix; other schemes are not built."""
     crs_b = algorithmic_bytes(A.n_rows, A.n_cols, A.nnz)
     out = []
+    want = lambda name: only is None or name.startswith(only)
     for l, r in ((4, 4), (8, 2), (16, 2)):
         out.append((f"CRS vector l{l} r{r}", M, x, crs_b, ("vector", l, r)))
     for t in (1024, 2048):
         out.append((f"CRS tiled {t}", M, x, crs_b, ("tiled", t)))
     for perm in ("symmetric", "row_only"):
+        if only is not None and not any(f"{f} {perm}".startswith(only) or only.startswith(f"{f} {perm}")
+                                        for f in ("JDS", "NUJDS", "NBJDS", "JDS_LITERAL", "RBJDS", "SOJDS")):
+            continue
         J = M.to_jds("JDS", perm)
         xp = J.permute(x) if perm == "symmetric" else x
         jb = 12 * A.nnz + 4 * (J.n_diag + 1) + 8 * A.n_cols + 8 * A.n_rows
-        for fmt, b, u in (("JDS", 0, 0), ("NUJDS", 0, 2), ("NUJDS", 0, 4), ("NUJDS", 0, 8),
-                          ("NBJDS", 1024, 0), ("NBJDS", 2048, 0), ("JDS_LITERAL", 0, 0)):
-            name = f"{fmt} {perm}" + (f" b={b}" if b else "") + (f" u={u}" if u else "")
-            out.append((name, J, xp, jb, ("jds", fmt, b, u)))
+        for fmt, b, u, r in (("JDS", 0, 0, 1), ("NUJDS", 0, 2, 1), ("NUJDS", 0, 4, 1), ("NUJDS", 0, 8, 1),
+                             ("NUJDS", 0, 2, 2), ("NUJDS", 0, 4, 2), ("NUJDS", 0, 2, 4), ("NUJDS", 0, 4, 4),
+                             ("NBJDS", 1024, 0, 1), ("NBJDS", 2048, 0, 1), ("JDS_LITERAL", 0, 0, 1)):
+            name = (f"{fmt} {perm}" + (f" b={b}" if b else "") + (f" u={u}" if u else "")
+                    + (f" r={r}" if r > 1 else ""))
+            out.append((name, J, xp, jb, ("jds", fmt, b, u, r)))
         for fmt in ("RBJDS", "SOJDS"):
+            if not want(f"{fmt} {perm} b=1024"):
+                continue
             R = M.to_jds(fmt, perm, block=1024)
             rb = jb + 4 * (R.n_blocks + 1)
             out.append((f"{fmt} {perm} b=1024", R, xp, rb, ("fixed",)))
@@ -204,6 +215,7 @@ def configure(H, how):
         H.prepare_tiled(how[1])
     elif how[0] == "jds":
         H.set_format(how[1], block=how[2], unroll=how[3])
+        H.set_kernel("vector", rows_per_warp=how[4])
 
 
 def run_ours(args):
@@ -229,7 +241,7 @@ def run_ours(args):
 
     # every scheme timed (median of 10 launches); the fastest is the step
     table, best = {}, None
-    for name, H, xin, nbytes, how in candidates(M, A, x):
+    for name, H, xin, nbytes, how in candidates(M, A, x, None if args.kernel == "auto" else args.kernel):
         if args.kernel != "auto" and not name.startswith(args.kernel):
             continue
         configure(H, how)
@@ -424,12 +436,17 @@ def fwd_bwd_speedup(dev, time_launches):
     m = 20
     res = {"n_rows": A.n_rows, "nnz": A.nnz, "m": m}
     for dtype in (torch.float64, torch.float32):
+        # plain: default CRS kernels, explicit transposed CRS
         p = Pattern.from_host(A, device=dev, dtype=dtype)
+        # tuned: autotuned forward and adjoint kernels (CRS or JDS, either side)
+        pt = Pattern.from_host(A, device=dev, dtype=dtype, forward="auto", adjoint="auto")
         val = torch.as_tensor(A.val).to(device=dev, dtype=dtype)
         x0 = torch.as_tensor(S.vector(A.n_cols, 4)).to(device=dev, dtype=dtype)
         M = p.bind(val)
         p.adjoint_op(val)  # build the transposed structure once
         AT = p.AT
+        pt.forward_op(val)
+        pt.adjoint_op(val)
 
         def plain():
             xs = [x0]
@@ -445,7 +462,7 @@ def fwd_bwd_speedup(dev, time_launches):
         def tuned(c=5):
             v = val.clone().requires_grad_(True)
             xx = x0.clone().requires_grad_(True)
-            y = power_apply(p, v, xx, m, checkpoint=c)
+            y = power_apply(pt, v, xx, m, checkpoint=c)
             (y * y).sum().backward()
             return v.grad, xx.grad
 
@@ -455,7 +472,8 @@ def fwd_bwd_speedup(dev, time_launches):
         tt = statistics.median(time_launches(tuned, 5))
         key = "f64" if dtype == torch.float64 else "f32"
         res[key] = {"plain_ms": round(tp, 3), "tuned_ms": round(tt, 3), "speedup": round(tp / tt, 3),
-                    "vectors_stored_plain": m + 1, "vectors_stored_tuned": m // 5 + 5}
+                    "vectors_stored_plain": m + 1, "vectors_stored_tuned": m // 5 + 5,
+                    "tuned_forward": type(pt.F).__name__, "tuned_adjoint": type(pt._adj).__name__}
     return res
 
 
@@ -508,8 +526,34 @@ def run_reference(args):
             "e2e": {"value": val, "unit": "GFlop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_ncu_case(args):
+    """A few launches of one kernel on a 2e6-row HH-like matrix (~350 MB,
+    above the 129 MB L2) for an ncu capture; prints nothing to time."""
+    import torch
+    from paper_0910_4836_gb300 import CRSMatrix, build, synth as S
+    build()
+    A = S.hh_like(2_000_000, 1)
+    M = CRSMatrix.from_host(A)
+    x = torch.as_tensor(S.vector(A.n_cols, 1)).cuda()
+    y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+    only = None if args.kernel == "auto" else args.kernel
+    for name, H, xin, _, how in candidates(M, A, x, only):
+        if only is not None and name != only:
+            continue
+        configure(H, how)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        for _ in range(3):
+            H.spmv(xin, out=y)
+        torch.cuda.synchronize()
+        print("ran", name)
+
+
 def main():
     args = parse()
+    if args.ncu_case:
+        run_ncu_case(args)
+        return
     res = run_reference(args) if args.impl == "reference" else run_ours(args)
     if res is not None:
         print(json.dumps(res), flush=True)

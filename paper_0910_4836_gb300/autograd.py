@@ -22,14 +22,19 @@ from .sparse import CRSMatrix
 
 
 class Pattern:
-    """Sparsity pattern (row_ptr, col on the GPU) plus the kernels' set-up:
-    the product handle and, built once, the transposed structure.
+    """Sparsity pattern (row_ptr, col on the GPU) plus the kernels' set-up.
 
-    adjoint: "crs" runs A^T g with the CRS kernels of the transposed
-    structure, "jds" with a JDS (row-only permutation) of it."""
+    The value gradient always runs on the CRS handle (dval is in CRS entry
+    order).  The products can run elsewhere:
+      forward: "crs" -- the CRS handle; "jds" -- a JDS of A (row-only
+               permutation, NUJDS walk) whose values are re-gathered when they
+               change; "auto" -- whichever the autotuner times faster.
+      adjoint: "crs" -- the CRS of A^T (transposed structure); "jds" -- a JDS
+               of A^T (the transposed-JDS form); "auto" -- the faster one.
+    """
 
     def __init__(self, row_ptr: torch.Tensor, col: torch.Tensor, n_cols: int, dtype=torch.float64,
-                 adjoint: str = "crs", tiled: bool = False):
+                 adjoint: str = "crs", forward: str = "crs", tiled: bool = False):
         self.row_ptr = row_ptr.contiguous()
         self.col = col.contiguous()
         self.n_rows = self.row_ptr.numel() - 1
@@ -37,13 +42,17 @@ class Pattern:
         self.nnz = self.col.numel()
         self.dtype = dtype
         self.adjoint = adjoint
+        self.forward = forward
         dummy = torch.zeros(max(self.nnz, 1), dtype=dtype, device=self.row_ptr.device)[: self.nnz]
         self.A = CRSMatrix(self.row_ptr, self.col, dummy, self.n_cols)
         if tiled:
             self.A.prepare_tiled(1024)
+        self.F = None
+        self._fkey = None
         self.AT = None
         self.JT = None
-        self._vals_version = None
+        self._adj = None
+        self._akey = None
 
     @classmethod
     def from_host(cls, A, device="cuda", dtype=torch.float64, **kw) -> "Pattern":
@@ -51,11 +60,36 @@ class Pattern:
                    torch.as_tensor(A.col, dtype=torch.int32).to(device), A.n_cols, dtype, **kw)
 
     def bind(self, val: torch.Tensor) -> CRSMatrix:
-        """Point the product handle at `val`."""
+        """Point the CRS handle at `val`."""
         if val.dtype != self.dtype or val.numel() != self.nnz:
             raise ValueError("values do not match the pattern")
         self.A.set_values(val.detach())
         return self.A
+
+    def forward_op(self, val: torch.Tensor):
+        A = self.bind(val)
+        if self.forward == "crs":
+            return A
+        if self.F is None:
+            J = A.to_jds("NUJDS", "row_only", unroll=4, value_map=True)
+            J.refresh_values(val.detach())
+            if self.forward == "auto":
+                _, ms_a = A.autotune(1)
+                _, ms_j = J.autotune(1)
+                self.F = J if ms_j < ms_a else A
+            else:
+                self.F = J
+            self._fkey = None
+        if self.F is not A:
+            key = (val.data_ptr(), val._version)
+            if self._fkey != key:
+                self.F.refresh_values(val.detach())
+                self._fkey = key
+        return self.F
+
+    def apply(self, val: torch.Tensor, x: torch.Tensor, out=None) -> torch.Tensor:
+        """A x for 1-D x or an (n, 1) column view (with `out` likewise)."""
+        return self.forward_op(val).spmm(x, out=out, basis=1)
 
     def adjoint_op(self, val: torch.Tensor):
         """Handle computing A^T g for the bound values (built on first use,
@@ -63,15 +97,22 @@ class Pattern:
         self.bind(val)
         if self.AT is None:
             self.AT = self.A.transpose()
-            if self.adjoint == "jds":
+            if self.adjoint in ("jds", "auto"):
                 self.JT = self.AT.to_jds("NUJDS", "row_only", unroll=4, value_map=True)
-        key = (val.data_ptr(), val._version)
-        if self._vals_version != key:
-            self.A.refresh_transpose_values()
-            if self.JT is not None:
                 self.JT.refresh_values(self.AT.val)
-            self._vals_version = key
-        return self.JT if self.JT is not None else self.AT
+            self._adj = self.JT if self.adjoint == "jds" else self.AT
+            if self.adjoint == "auto":
+                _, ms_c = self.AT.autotune(1)
+                _, ms_j = self.JT.autotune(1)
+                self._adj = self.JT if ms_j < ms_c else self.AT
+            self._akey = None
+        key = (val.data_ptr(), val._version)
+        if self._akey != key:
+            self.A.refresh_transpose_values()
+            if self._adj is self.JT:
+                self.JT.refresh_values(self.AT.val)
+            self._akey = key
+        return self._adj
 
     def apply_t(self, val: torch.Tensor, g: torch.Tensor, out=None) -> torch.Tensor:
         """A^T g for 1-D g or an (n, 1) column view (with `out` likewise)."""
@@ -85,7 +126,7 @@ class SpMVFunction(torch.autograd.Function):
     def forward(ctx, val, x, pattern: Pattern):
         ctx.pattern = pattern
         ctx.save_for_backward(val, x)
-        return pattern.bind(val).spmv(x.detach().contiguous())
+        return pattern.apply(val, x.detach().contiguous())
 
     @staticmethod
     def backward(ctx, gy):
@@ -109,11 +150,10 @@ class PowerFunction(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, val, x, pattern: Pattern, m: int, c: int):
-        A = pattern.bind(val)
         cur = x.detach().contiguous()
         ckpts = [cur]
         for t in range(1, m + 1):
-            cur = A.spmv(cur)
+            cur = pattern.apply(val, cur)
             if t % c == 0 and t < m:
                 ckpts.append(cur)
         ctx.pattern, ctx.m, ctx.c = pattern, m, c
@@ -124,7 +164,6 @@ class PowerFunction(torch.autograd.Function):
     def backward(ctx, gm):
         val, *ckpts = ctx.saved_tensors
         p, m, c = ctx.pattern, ctx.m, ctx.c
-        A = p.bind(val)
         n = p.n_rows
         dev, dt = gm.device, gm.dtype
         dval = torch.zeros(p.nnz, dtype=dt, device=dev) if ctx.needs_input_grad[0] else None
@@ -136,7 +175,7 @@ class PowerFunction(torch.autograd.Function):
             X = torch.empty((n, w), dtype=dt, device=dev)
             X[:, w - 1] = ckpts[seg]
             for j in range(1, w):
-                A.spmm(X[:, w - j:w - j + 1], out=X[:, w - 1 - j:w - j])
+                p.apply(val, X[:, w - j:w - j + 1], out=X[:, w - 1 - j:w - j])
             # G[:, i] = g_{t1-i}, i.e. g_{t-1} = A^T g_t down the segment
             G = torch.empty((n, w), dtype=dt, device=dev)
             G[:, 0] = g
@@ -144,9 +183,8 @@ class PowerFunction(torch.autograd.Function):
                 p.apply_t(val, G[:, i - 1:i], out=G[:, i:i + 1])
             if dval is not None:
                 # terms g_t[row] x_{t-1}[col] for t = t1, t1-1, ..., t0+1
-                A.dval_multi(G, X, out=dval, accumulate=True)
+                p.bind(val).dval_multi(G, X, out=dval, accumulate=True)
             g = p.apply_t(val, G[:, w - 1:w]).reshape(n)
-            A = p.bind(val)
         return dval, (g if ctx.needs_input_grad[1] else None), None, None, None
 
 

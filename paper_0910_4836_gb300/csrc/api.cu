@@ -138,6 +138,8 @@ gbsp_status gbsp_set_kernel(gbsp_handle h, const gbsp_kernel_opts *o) {
     if (o->rows_per_warp != 0 && o->rows_per_warp != 1 && o->rows_per_warp != 2 &&
         o->rows_per_warp != 4)
         return arg_error("gbsp_set_kernel: rows_per_warp must be 1, 2 or 4");
+    if (h->kind == KIND_JDS && o->kernel == GBSP_KERNEL_TILED)
+        return arg_error("gbsp_set_kernel: TILED is a CRS kernel");
     if (o->tile != 0 && o->tile != 1024 && o->tile != 2048)
         return arg_error("gbsp_set_kernel: tile must be 1024 or 2048");
     if (o->rhs_tile != 0 && (o->rhs_tile < 1 || o->rhs_tile > 32))

@@ -599,6 +599,7 @@ gbsp_status jds_build_impl(const Mat &A, const gbsp_jds_opts &o, const gbsp_jds_
     J->blk_ptr = blocked ? b.blk_ptr : nullptr;
     J->vmap = b.vmap;
     J->kopt = A.kopt;
+    J->kopt.rows_per_warp = 1;  // JDS walks: rows per thread
 
     if (blocked && n > 0) {
         blk_ptr_kernel<<<(unsigned)ceil_div(J->n_blocks + 1, 256), 256, 0, s>>>(

@@ -41,8 +41,8 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s bound on every wait
 template <int VM, int T, int S>
 struct StreamSmem {
     typedef typename ValT<VM>::T V;
-    V val[S][T + 4];
-    int32_t col[S][T + 4];
+    V val[S][T + 8];
+    int32_t col[S][T + 8];
     int32_t rp[S][T + 8];
     int4 meta[S];
     V xs[T + 4];
@@ -87,7 +87,7 @@ __global__ void tile_meta_kernel(int64_t n_tiles, int32_t T, const int32_t *__re
 
 template <int VM, int T, int S>
 __global__ void __launch_bounds__(kStreamThreads)
-crs_stream_kernel(int64_t n_tiles, const int4 *__restrict__ tile_meta,
+crs_stream_kernel(int64_t n_tiles, const int4 *__restrict__ tile_meta, int64_t n_rows, int64_t nnz,
                   const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                   const typename ValT<VM>::T *__restrict__ val,
                   const typename ValT<VM>::T *__restrict__ x, int64_t ldx,
@@ -119,8 +119,10 @@ crs_stream_kernel(int64_t n_tiles, const int4 *__restrict__ tile_meta,
         if (lane != 0) return;
         int64_t fill = 0;
         bool ok = true;
+        int4 m_next = t_begin < t_end ? __ldg(tile_meta + t_begin) : make_int4(0, 0, 0, 0);
         for (int64_t t = t_begin; t < t_end && ok; ++t) {
-            const int4 m = __ldg(tile_meta + t);
+            const int4 m = m_next;
+            if (t + 1 < t_end) m_next = __ldg(tile_meta + t + 1);  // prefetch the next tile's offsets
             const int32_t r1 = m.y < 0 ? -m.y - 1 : m.y;
             if (m.x == r1) continue;  // no row starts in this tile
             const int s = (int)(fill % S);
@@ -131,10 +133,17 @@ crs_stream_kernel(int64_t n_tiles, const int4 *__restrict__ tile_meta,
             }
             const int32_t r0 = m.x, k0 = m.z, kst = m.w;
             const int32_t rs_end = (m.y < 0 ? r1 - 1 : r1) + 1;  // rp entries [r0, rs_end)
-            // aligned interiors go by bulk copy, ragged ends by plain loads
-            const int32_t vlo = k0 & ~VMASK, vhi = kst & ~VMASK;
-            const int32_t clo = k0 & ~3, chi = kst & ~3;
-            const int32_t rlo = r0 & ~3, rhi = rs_end & ~3;
+            // The bulk copies start at the 16-byte boundary below each range
+            // and end at the one above it when that stays inside the array
+            // (the extra elements are never used); only a range that ends in
+            // the array's last 16 bytes leaves a ragged end for plain loads.
+            const int32_t vlo = k0 & ~VMASK, clo = k0 & ~3, rlo = r0 & ~3;
+            const int64_t vup = ((int64_t)kst + VMASK) & ~(int64_t)VMASK;
+            const int64_t cup = ((int64_t)kst + 3) & ~(int64_t)3;
+            const int64_t rup = ((int64_t)rs_end + 3) & ~(int64_t)3;
+            const int32_t vhi = vup <= nnz ? (int32_t)vup : (kst & ~VMASK);
+            const int32_t chi = cup <= nnz ? (int32_t)cup : (kst & ~3);
+            const int32_t rhi = rup <= n_rows + 1 ? (int32_t)rup : (rs_end & ~3);
             for (int32_t e = max(vhi, k0); e < kst; ++e) sm.val[s][e - vlo] = val[e];
             for (int32_t e = max(chi, k0); e < kst; ++e) sm.col[s][e - clo] = col[e];
             for (int32_t e = max(rhi, r0); e < rs_end; ++e) sm.rp[s][e - rlo] = row_ptr[e];
@@ -337,7 +346,7 @@ static gbsp_status launch_stream_T(const Mat &A, const VecArgs &v, cudaStream_t 
     per_sm = std::max(per_sm, 1);
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(A.n_tiles, (int64_t)num_sms() * per_sm));
     crs_stream_kernel<VM, T, S><<<(unsigned)grid, kStreamThreads, smem, st>>>(
-        A.n_tiles, A.tile_meta, A.row_ptr, A.col, static_cast<const V *>(A.val),
+        A.n_tiles, A.tile_meta, A.n_rows, A.nnz, A.row_ptr, A.col, static_cast<const V *>(A.val),
         static_cast<const V *>(v.x), v.ldx, static_cast<V *>(v.y), v.ldy, v.accumulate, A.status);
     return GBSP_OK;
 }

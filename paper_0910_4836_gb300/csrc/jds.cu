@@ -54,16 +54,27 @@ __device__ __forceinline__ void store_row(const JdsArgs &a, int64_t r, int c, Ac
     *yp = acc.result();
 }
 
-// JDS (U = 1) and NUJDS (U > 1): one thread per permuted row.
-template <int VM, int U>
+// JDS (U = 1) and NUJDS (U > 1): one thread per permuted row, U diagonals
+// per step.  With R > 1 a warp owns 32*R consecutive rows and each thread R
+// of them (rows base + 32 i + lane): the loads of all R rows and U diagonals
+// are issued together, while each warp-wide load still covers 32
+// consecutive entries of one diagonal.
+template <int VM, int U, int R>
 __global__ void __launch_bounds__(256) jds_row_kernel(JdsArgs a) {
     typedef typename ValT<VM>::T T;
     const T *__restrict__ val = static_cast<const T *>(a.val);
     const T *__restrict__ x = static_cast<const T *>(a.x);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.n_rows; r += stride) {
-        Acc<VM> acc;
-        acc.init();
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * 32 * R; base < a.n_rows; base += nwarp * 32 * R) {
+        int64_t rr[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) rr[i] = base + 32 * i + lane;
+        if (rr[0] >= a.n_rows) continue;
+        Acc<VM> acc[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) acc[i].init();
         int32_t st = __ldg(a.jd_ptr);
         for (int64_t d0 = 0; d0 < a.n_diag; d0 += U) {
             int32_t e[U + 1];
@@ -71,21 +82,28 @@ __global__ void __launch_bounds__(256) jds_row_kernel(JdsArgs a) {
 #pragma unroll
             for (int j = 0; j < U; ++j)
                 e[j + 1] = (d0 + j < a.n_diag) ? __ldg(a.jd_ptr + d0 + j + 1) : e[j];
-            if (e[1] - e[0] <= r) break;  // row r has no entry in diagonal d0
-            int c[U];
-            T v[U];
+            // rr[0] is the thread's longest row (rows are sorted by length)
+            if (e[1] - e[0] <= rr[0]) break;
+            int c[R][U];
+            T v[R][U];
 #pragma unroll
-            for (int j = 0; j < U; ++j) {
-                const bool ok = e[j + 1] - e[j] > r;
-                c[j] = ok ? ld_stream(a.col + e[j] + r) : -1;
-                v[j] = ok ? ld_stream(val + e[j] + r) : T(0);
-            }
+            for (int i = 0; i < R; ++i)
 #pragma unroll
-            for (int j = 0; j < U; ++j)
-                if (c[j] >= 0) acc.add(v[j], ld_vec(x + xidx(a.x_perm, c[j]) * a.ldx));
+                for (int j = 0; j < U; ++j) {
+                    const bool ok = e[j + 1] - e[j] > rr[i];
+                    c[i][j] = ok ? ld_stream(a.col + e[j] + rr[i]) : -1;
+                    v[i][j] = ok ? ld_stream(val + e[j] + rr[i]) : T(0);
+                }
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+#pragma unroll
+                for (int j = 0; j < U; ++j)
+                    if (c[i][j] >= 0) acc[i].add(v[i][j], ld_vec(x + xidx(a.x_perm, c[i][j]) * a.ldx));
             st = e[U];
         }
-        store_row<VM>(a, r, 0, acc);
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+            if (rr[i] < a.n_rows) store_row<VM>(a, rr[i], 0, acc[i]);
     }
 }
 
@@ -192,8 +210,10 @@ static int row_grid(int64_t rows) {
 }
 
 template <int VM, int U>
-static void launch_row(const JdsArgs &a, cudaStream_t s) {
-    jds_row_kernel<VM, U><<<row_grid(a.n_rows), 256, 0, s>>>(a);
+static void launch_row(const JdsArgs &a, int R, cudaStream_t s) {
+    if (R >= 4) jds_row_kernel<VM, U, 4><<<row_grid(ceil_div(a.n_rows, 4)), 256, 0, s>>>(a);
+    else if (R >= 2) jds_row_kernel<VM, U, 2><<<row_grid(ceil_div(a.n_rows, 2)), 256, 0, s>>>(a);
+    else jds_row_kernel<VM, U, 1><<<row_grid(a.n_rows), 256, 0, s>>>(a);
 }
 
 template <int VM, bool CONTIG>
@@ -257,11 +277,12 @@ static gbsp_status launch_family(const Mat &A, JdsArgs a, cudaStream_t s) {
         return GBSP_OK;
     }
     const int u = fmt == GBSP_NUJDS ? A.unroll : 1;
-    if (u <= 1) launch_row<VM, 1>(a, s);
-    else if (u <= 2) launch_row<VM, 2>(a, s);
-    else if (u <= 4) launch_row<VM, 4>(a, s);
-    else if (u <= 8) launch_row<VM, 8>(a, s);
-    else launch_row<VM, 16>(a, s);
+    const int R = A.kopt.rows_per_warp > 1 ? A.kopt.rows_per_warp : 1;  // rows per thread
+    if (u <= 1) launch_row<VM, 1>(a, R, s);
+    else if (u <= 2) launch_row<VM, 2>(a, R, s);
+    else if (u <= 4) launch_row<VM, 4>(a, R, s);
+    else if (u <= 8) launch_row<VM, 8>(a, std::min(R, 2), s);
+    else launch_row<VM, 16>(a, 1, s);
     return GBSP_OK;
 }
 

@@ -106,15 +106,20 @@ static std::vector<Cand> candidates(const Mat &A, int k) {
         if (k == 1) {
             Cand c = base;
             c.format = GBSP_JDS;
+            c.k.rows_per_warp = 1;
             out.push_back(c);
-            for (int u : {2, 4, 8}) {
-                c = base;
-                c.format = GBSP_NUJDS;
-                c.unroll = u;
-                out.push_back(c);
-            }
+            for (int u : {2, 4, 8})
+                for (int r : {1, 2, 4}) {
+                    if (u == 8 && r == 4) continue;
+                    c = base;
+                    c.format = GBSP_NUJDS;
+                    c.unroll = u;
+                    c.k.rows_per_warp = r;
+                    out.push_back(c);
+                }
             for (int b : {256, 1024, 2048}) {
                 c = base;
+                c.k.rows_per_warp = 1;
                 c.format = GBSP_NBJDS;
                 c.block = b;
                 out.push_back(c);

@@ -115,14 +115,14 @@ def test_spmv_function_gradcheck(adjoint):
     assert torch.autograd.gradcheck(lambda v, xx: spmv(p, v, xx), (val, x), eps=1e-6, atol=1e-9)
 
 
-@pytest.mark.parametrize("adjoint", ["crs", "jds"])
-def test_power_gradients_against_oracle(adjoint):
+@pytest.mark.parametrize("adjoint,forward", [("crs", "crs"), ("jds", "jds"), ("auto", "auto")])
+def test_power_gradients_against_oracle(adjoint, forward):
     from paper_0910_4836_gb300.autograd import power_apply
     A = S.stencil27(8, 4)
     x = S.vector(A.n_cols, 85)
     m = 6
     L_ref, dv_ref, dx_ref = O.power_loss_grad(A, x, m)
-    p = _pattern(A, adjoint=adjoint)
+    p = _pattern(A, adjoint=adjoint, forward=forward)
     grads = []
     for c in (1, 2, 4, 6):
         val = dev(A.val).requires_grad_(True)

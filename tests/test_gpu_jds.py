@@ -80,12 +80,20 @@ def test_golden_example_on_gpu():
 
 
 def variants():
-    yield "JDS", 0, 0
-    yield "JDS_LITERAL", 0, 0
+    """(format, block, unroll, rows per thread)"""
+    yield "JDS", 0, 0, 1
+    yield "JDS", 0, 0, 4
+    yield "JDS_LITERAL", 0, 0, 1
     for u in (2, 3, 4, 8, 16):
-        yield "NUJDS", 0, u
+        for r in (1, 2, 4):
+            yield "NUJDS", 0, u, r
     for b in (32, 100, 256, 1000, 2048, 5000):
-        yield "NBJDS", b, 0
+        yield "NBJDS", b, 0, 1
+
+
+def set_variant(J, fmt, b, u, r):
+    J.set_format(fmt, block=b, unroll=u)
+    J.set_kernel("vector", rows_per_warp=r)
 
 
 @pytest.mark.parametrize("mi", range(len(MATS)))
@@ -102,12 +110,12 @@ def test_products_permuted_and_original(mi):
         J = M.to_jds("JDS", perm)
         xd, xpd = dev(x), dev(xp)
         first = None
-        for fmt, b, u in variants():
-            J.set_format(fmt, block=b, unroll=u)
+        for fmt, b, u, r in variants():
+            set_variant(J, fmt, b, u, r)
             yp = host(J.spmv(xpd))
-            assert_close64(yp, ref_p, s_p, f"{perm} {fmt} b={b} u={u} permuted")
+            assert_close64(yp, ref_p, s_p, f"{perm} {fmt} b={b} u={u} r={r} permuted")
             yo = host(J.spmv_original(xd))
-            assert_close64(yo, ref, s, f"{perm} {fmt} b={b} u={u} original")
+            assert_close64(yo, ref, s, f"{perm} {fmt} b={b} u={u} r={r} original")
             # every JDS-family kernel adds a row in slot order: identical bits
             if first is None:
                 first = yp
@@ -130,9 +138,9 @@ def test_integer_bit_exact_against_literal_loop():
     ref = O.jds_spmv(Oj, xp)
     J = M.to_jds("JDS", "symmetric")
     xpd = dev(xp)
-    for fmt, b, u in variants():
-        J.set_format(fmt, block=b, unroll=u)
-        assert np.array_equal(host(J.spmv(xpd)), ref), fmt
+    for fmt, b, u, r in variants():
+        set_variant(J, fmt, b, u, r)
+        assert np.array_equal(host(J.spmv(xpd)), ref), (fmt, b, u, r)
     for fmt in ("RBJDS", "SOJDS"):
         assert np.array_equal(host(M.to_jds(fmt, "symmetric", block=500).spmv(xpd)), ref), fmt
     # unpermuted result equals CRS
