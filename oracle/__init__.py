@@ -57,13 +57,16 @@ def lib():
             "orc_rbjds_spmv": [_I64, _I64, _I32, _I32, _I32, _F64, _I64, _F64, _F64, _INT],
             "orc_sojds_build": [_I64, _I64, _I32, _I32, _F64, _I64, _I32, _I32, _F64],
             "orc_permute": [_I64, _I32, _F64, _F64, _INT],
+            "orc_sell_build": [_I64, _I64, _I32, _I32, _F64, _INT, _I64, _I32, _I32, _I32, _I32, _I32,
+                               _F64],
+            "orc_sell_spmv": [_I64, _I32, _I32, _I32, _F64, _F64, _F64],
             "orc_num_threads": [],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = _I64 if name in ("orc_max_row_len", "orc_jds_build") else (
-                _INT if name == "orc_num_threads" else None)
+                _INT if name in ("orc_num_threads", "orc_sell_build") else None)
         _lib = L
     return _lib
 
@@ -239,6 +242,38 @@ def sojds_build(J, block):
     val = np.zeros(len(J.val))
     lib().orc_sojds_build(J.n_rows, J.n_diag, J.jd_ptr, J.col, J.val, block, blk_ptr, col, val)
     return blk_ptr, col, val
+
+
+class SELL:
+    """SELL-32-sigma arrays as built by :func:`sell_build`."""
+
+    def __init__(self, n_rows, symmetric, window, perm, iperm, rlen, blk_ptr, col, val):
+        self.n_rows, self.symmetric, self.window = n_rows, symmetric, window
+        self.perm, self.iperm, self.rlen, self.blk_ptr, self.col, self.val = perm, iperm, rlen, blk_ptr, col, val
+
+
+def sell_build(A, window, symmetric=True):
+    """RBJDS with 32-row blocks and the row sort restricted to windows."""
+    n = A.n_rows
+    perm = np.zeros(n, np.int32)
+    iperm = np.zeros(n, np.int32)
+    rlen = np.zeros(n, np.int32)
+    blk = np.zeros((n + 31) // 32 + 1, np.int32)
+    col = np.zeros(A.nnz, np.int32)
+    val = np.zeros(A.nnz)
+    r = lib().orc_sell_build(n, A.n_cols, _i32(A.row_ptr), _i32(A.col), _f64(A.val), int(symmetric),
+                             window, perm, iperm, rlen, blk, col, val)
+    if r == -1:
+        raise ValueError("symmetric permutation needs a square matrix")
+    if r == -2:
+        raise ValueError("window must be a positive multiple of 32")
+    return SELL(n, symmetric, window, perm, iperm, rlen, blk, col, val)
+
+
+def sell_spmv(S_, x_p):
+    out = np.zeros(S_.n_rows)
+    lib().orc_sell_spmv(S_.n_rows, S_.rlen, S_.blk_ptr, S_.col, S_.val, _f64(x_p), out)
+    return out
 
 
 def permute(perm, v, to_permuted=True):

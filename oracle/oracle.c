@@ -432,3 +432,71 @@ void orc_permute(int64_t n, const int32_t *perm, const double *in, double *out, 
         else out[perm[r]] = in[r];
     }
 }
+
+/* ------------------------------------------------------------------------
+ * SELL-32-sigma (Kreutzer, Hager, Wellein, Fehske & Bishop, SIAM J. Sci.
+ * Comput. 36, 2014): the RBJDS layout with blocks of C = 32 rows, where the
+ * decreasing-length row sort is restricted to windows of `window` rows
+ * (window a multiple of 32).  With window >= n_rows it is exactly RBJDS with
+ * block 32 of the JDS construction above.
+ *   perm      stable sort by (window index, decreasing length)
+ *   rlen[r]   length of permuted row r
+ *   blk_ptr   start of each block of 32 permuted rows
+ *   inside a block: slot 0 of the block's rows, then slot 1 of the rows
+ *   that have one, ... (rows are sorted inside a block, so those rows are
+ *   always the first ones of the block)
+ * Columns are renumbered by iperm when `symmetric`.
+ * ---------------------------------------------------------------------- */
+int orc_sell_build(int64_t n_rows, int64_t n_cols, const int32_t *row_ptr, const int32_t *col_idx,
+                   const double *val, int symmetric, int64_t window, int32_t *perm, int32_t *iperm,
+                   int32_t *rlen, int32_t *blk_ptr, int32_t *col_out, double *val_out)
+{
+    if (symmetric && n_rows != n_cols) return -1;
+    if (window < 32 || window % 32) return -2;
+    int64_t nj = orc_max_row_len(n_rows, row_ptr);
+    int64_t *count = (int64_t *)calloc((size_t)(nj + 2), sizeof(int64_t));
+    int64_t *start = (int64_t *)calloc((size_t)(nj + 2), sizeof(int64_t));
+    for (int64_t w0 = 0; w0 < n_rows; w0 += window) {
+        int64_t w1 = w0 + window < n_rows ? w0 + window : n_rows;
+        for (int64_t l = 0; l <= nj; ++l) count[l] = 0;
+        for (int64_t i = w0; i < w1; ++i) count[row_ptr[i + 1] - row_ptr[i]]++;
+        int64_t pos = w0;
+        for (int64_t l = nj; l >= 0; --l) { start[l] = pos; pos += count[l]; }
+        for (int64_t i = w0; i < w1; ++i) perm[start[row_ptr[i + 1] - row_ptr[i]]++] = (int32_t)i;
+    }
+    for (int64_t r = 0; r < n_rows; ++r) {
+        iperm[perm[r]] = (int32_t)r;
+        rlen[r] = row_ptr[perm[r] + 1] - row_ptr[perm[r]];
+    }
+    int64_t nb = (n_rows + 31) / 32, pos = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        int64_t b0 = 32 * b, b1 = b0 + 32 < n_rows ? b0 + 32 : n_rows;
+        blk_ptr[b] = (int32_t)pos;
+        int64_t width = rlen[b0];
+        for (int64_t d = 0; d < width; ++d)
+            for (int64_t r = b0; r < b1 && rlen[r] > d; ++r, ++pos) {
+                int64_t src = (int64_t)row_ptr[perm[r]] + d;
+                val_out[pos] = val[src];
+                col_out[pos] = symmetric ? iperm[col_idx[src]] : col_idx[src];
+            }
+    }
+    blk_ptr[nb] = (int32_t)pos;
+    free(count);
+    free(start);
+    return 0;
+}
+
+/* SELL kernel in the permuted basis: block after block, slot after slot. */
+void orc_sell_spmv(int64_t n_rows, const int32_t *rlen, const int32_t *blk_ptr,
+                   const int32_t *col_s, const double *val_s, const double *invec, double *resvec)
+{
+    for (int64_t i = 0; i < n_rows; ++i) resvec[i] = 0.0;
+    int64_t nb = (n_rows + 31) / 32;
+    for (int64_t b = 0; b < nb; ++b) {
+        int64_t b0 = 32 * b, b1 = b0 + 32 < n_rows ? b0 + 32 : n_rows;
+        int64_t pos = blk_ptr[b];
+        for (int64_t d = 0; d < rlen[b0]; ++d)
+            for (int64_t r = b0; r < b1 && rlen[r] > d; ++r, ++pos)
+                resvec[r] = resvec[r] + val_s[pos] * invec[col_s[pos]];
+    }
+}

@@ -294,6 +294,46 @@ def test_empty_and_degenerate():
     assert y.tolist() == [0.0, 5000.0, 0.0]
 
 
+# ------------------------------------------------------------- SELL -----
+
+@pytest.mark.parametrize("sym", [True, False])
+def test_sell_one_window_is_rbjds_block32(sym):
+    """With a single window the row sort is the JDS sort, so SELL-32 is the
+    paper's RBJDS with block size 32 (Sect. 2), array for array."""
+    A = S.hh_like(3000, 91)
+    J = O.jds_build(A, symmetric=sym)
+    bp, c, v = O.rbjds_build(J, 32)
+    Sl = O.sell_build(A, window=32 * ((A.n_rows + 31) // 32), symmetric=sym)
+    assert np.array_equal(Sl.perm, J.perm) and np.array_equal(Sl.iperm, J.iperm)
+    assert np.array_equal(Sl.blk_ptr, bp)
+    assert np.array_equal(Sl.col, c) and np.array_equal(Sl.val, v)
+    assert np.array_equal(Sl.rlen, A.row_lengths()[J.perm])
+
+
+@pytest.mark.parametrize("window", [32, 64, 1024])
+def test_sell_windows(window):
+    A = S.zipf_rows(5000, 92, lmax=300)
+    Sl = O.sell_build(A, window, symmetric=False)
+    lens = A.row_lengths()
+    # perm only moves rows inside their window, longest first, stable
+    assert np.array_equal(np.sort(Sl.perm), np.arange(A.n_rows))
+    assert np.all(Sl.perm // window == np.arange(A.n_rows) // window)
+    for w0 in range(0, A.n_rows, window):
+        pl = lens[Sl.perm[w0:w0 + window]]
+        assert np.all(np.diff(pl) <= 0)
+        same = np.diff(pl) == 0
+        assert np.all(np.diff(Sl.perm[w0:w0 + window])[same] > 0)
+    # each permuted row's entries are the CRS row's entries in slot order
+    x = S.vector(A.n_cols, 93)
+    P = permuted_crs(A, O.JDS(A.n_rows, A.n_cols, False, Sl.perm, Sl.iperm, None, None, None))
+    assert np.array_equal(O.sell_spmv(Sl, x), O.crs_spmv(P, x))
+    Ai = S.integer_values(A, 94, 1000)
+    xi = S.int_vector(A.n_cols, 94, 1000)
+    Si = O.sell_build(Ai, window, symmetric=True)
+    y = O.permute(Si.perm, O.sell_spmv(Si, O.permute(Si.perm, xi)), to_permuted=False)
+    assert np.array_equal(y, O.crs_spmv(Ai, xi))
+
+
 # ------------------------------------------------------------ SOJDS -----
 
 def test_sojds_is_row_permutation_and_same_product():
