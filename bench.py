@@ -186,6 +186,15 @@ def candidates(M, A, x, only=None):
         out.append((f"CRS vector l{l} r{r}", M, x, crs_b, ("vector", l, r)))
     for t in (1024, 2048):
         out.append((f"CRS tiled {t}", M, x, crs_b, ("tiled", t)))
+    for perm in ("row_only", "symmetric"):
+        for w in (256, 1024, 4096):
+            for u in (2, 4):
+                name = f"SELL {perm} w={w} u={u}"
+                if want(name):
+                    G = M.to_jds("SELL", perm, window=w, unroll=u)
+                    xs = G.permute(x) if perm == "symmetric" else x
+                    gb = 12 * A.nnz + 4 * (G.n_blocks + 1) + 4 * A.n_rows + 8 * A.n_cols + 8 * A.n_rows
+                    out.append((name, G, xs, gb, ("fixed",)))
     for perm in ("symmetric", "row_only"):
         if only is not None and not any(f"{f} {perm}".startswith(only) or only.startswith(f"{f} {perm}")
                                         for f in ("JDS", "NUJDS", "NBJDS", "JDS_LITERAL", "RBJDS", "SOJDS")):

@@ -54,7 +54,13 @@ typedef enum { GBSP_F64 = 0, GBSP_F32 = 1 } gbsp_dtype;
 /* Storage schemes (Sect. 2).  JDS, NBJDS and NUJDS share one storage
  * pattern and differ in how the kernel walks it; RBJDS and SOJDS store each
  * row block consecutively.  JDS_LITERAL is the paper's diagonal-after-
- * diagonal loop with a result-vector round trip per diagonal. */
+ * diagonal loop with a result-vector round trip per diagonal.  SELL is the
+ * RBJDS layout with blocks of 32 rows (one warp) and the decreasing-length
+ * row sort restricted to windows of `window` rows -- SELL-32-sigma of
+ * Kreutzer, Hager, Wellein, Fehske & Bishop (SIAM J. Sci. Comput. 2014),
+ * the same group's follow-up; with one window it is RBJDS with block 32.
+ * Rows stay near their original position, so the gathers of x keep the
+ * matrix's locality while the lanes of a warp still do equal work. */
 typedef enum {
     GBSP_CRS = 0,
     GBSP_JDS = 1,
@@ -62,7 +68,8 @@ typedef enum {
     GBSP_RBJDS = 3,
     GBSP_NUJDS = 4,
     GBSP_SOJDS = 5,
-    GBSP_JDS_LITERAL = 6
+    GBSP_JDS_LITERAL = 6,
+    GBSP_SELL = 7
 } gbsp_format;
 
 /* Sect. 2: JDS permutes rows AND columns (A_{p(i),p(j)}), so all work runs in
@@ -180,19 +187,20 @@ typedef struct {
     int32_t format;     /* gbsp_format, one of the JDS family */
     int32_t perm_mode;  /* gbsp_perm_mode */
     int32_t block;      /* NBJDS / RBJDS / SOJDS: rows per block (>= 1; 0 = 256) */
-    int32_t unroll;     /* NUJDS: diagonals per step u (>= 1; 0 = 4) */
+    int32_t unroll;     /* NUJDS / SELL: diagonals per step u (>= 1; 0 = 4) */
+    int32_t window;     /* SELL: rows per sorting window, a multiple of 32 (0 = 1024) */
 } gbsp_jds_opts;
 
 typedef struct {
     int64_t n_rows, n_cols, nnz;
     int64_t n_diag;           /* N_j = longest row */
-    int64_t n_blocks;         /* RBJDS / SOJDS blocks, else 0 */
+    int64_t n_blocks;         /* RBJDS / SOJDS blocks, SELL 32-row blocks, else 0 */
     int64_t workspace_bytes;  /* scratch for gbsp_jds_build only */
 } gbsp_jds_sizes;
 
 /* Caller-allocated outputs of the conversion (device memory). */
 typedef struct {
-    int32_t *jd_ptr;   /* [n_diag+1] start of each jagged diagonal (Sect. 2 jd_ptr) */
+    int32_t *jd_ptr;   /* [n_diag+1] start of each jagged diagonal (Sect. 2 jd_ptr); SELL: unused */
     int32_t *col;      /* [nnz] column indices in storage order */
     void *val;         /* [nnz] values, same dtype as the CRS handle */
     int32_t *perm;     /* [n_rows] perm[new] = old row */
@@ -201,6 +209,7 @@ typedef struct {
     void *workspace;   /* [workspace_bytes] scratch, free after the build completes */
     int32_t *vmap;     /* optional [nnz]: CRS entry index of every stored entry, kept by the
                           handle for gbsp_jds_values (NULL: not built) */
+    int32_t *rlen;     /* SELL only: [n_rows] length of every permuted row */
 } gbsp_jds_buffers;
 
 /* Sizes for converting `crs` (Sect. 2 JDS construction).  Reads the row

@@ -21,7 +21,8 @@ GBSP_OK = 0
 STATUS = {0: "GBSP_OK", -1: "GBSP_ERR_ARG", -2: "GBSP_ERR_MATRIX", -3: "GBSP_ERR_CUDA",
           -4: "GBSP_ERR_NOMEM", -5: "GBSP_ERR_UNSUPPORTED", -6: "GBSP_ERR_TIMEOUT"}
 F64, F32 = 0, 1
-FORMATS = {"CRS": 0, "JDS": 1, "NBJDS": 2, "RBJDS": 3, "NUJDS": 4, "SOJDS": 5, "JDS_LITERAL": 6}
+FORMATS = {"CRS": 0, "JDS": 1, "NBJDS": 2, "RBJDS": 3, "NUJDS": 4, "SOJDS": 5, "JDS_LITERAL": 6,
+           "SELL": 7}
 PERM = {"symmetric": 0, "row_only": 1}
 OP_N, OP_T = 0, 1
 BASIS_PERMUTED, BASIS_ORIGINAL = 0, 1
@@ -36,7 +37,8 @@ class KernelOpts(ctypes.Structure):
 
 
 class JdsOpts(ctypes.Structure):
-    _fields_ = [("format", c_i32), ("perm_mode", c_i32), ("block", c_i32), ("unroll", c_i32)]
+    _fields_ = [("format", c_i32), ("perm_mode", c_i32), ("block", c_i32), ("unroll", c_i32),
+                ("window", c_i32)]
 
 
 class JdsSizes(ctypes.Structure):
@@ -46,7 +48,7 @@ class JdsSizes(ctypes.Structure):
 
 class JdsBuffers(ctypes.Structure):
     _fields_ = [("jd_ptr", c_vp), ("col", c_vp), ("val", c_vp), ("perm", c_vp), ("iperm", c_vp),
-                ("blk_ptr", c_vp), ("workspace", c_vp), ("vmap", c_vp)]
+                ("blk_ptr", c_vp), ("workspace", c_vp), ("vmap", c_vp), ("rlen", c_vp)]
 
 
 class TransposeBuffers(ctypes.Structure):

@@ -28,7 +28,7 @@ struct BatchMat {
     int32_t block;     // RBJDS / SOJDS block
     int32_t pad;
     int64_t n_rows, n_diag;
-    const int32_t *row_ptr, *col, *jd_ptr, *blk_ptr;
+    const int32_t *row_ptr, *col, *jd_ptr, *blk_ptr, *rlen;
     const void *val;
     const void *x;
     void *y;
@@ -134,8 +134,62 @@ __device__ void batch_jds_rows(const BatchMat &m, int64_t rb, int64_t re, int c0
     }
 }
 
+// SELL rows [rb, re) (whole 32-row blocks): one warp per block, lane = row
+// (same arithmetic as sell_kernel).
+template <int VM, int KT>
+__device__ void batch_sell_rows(const BatchMat &m, int64_t rb, int64_t re, int c0) {
+    typedef typename ValT<VM>::T T;
+    const T *val = static_cast<const T *>(m.val);
+    const T *x = static_cast<const T *>(m.x);
+    T *y = static_cast<T *>(m.y);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t b = rb / 32 + wid; b * 32 < re; b += kBatchThreads / 32) {
+        const int64_t r = b * 32 + lane;
+        const int32_t len = r < m.n_rows ? __ldg(m.rlen + r) : 0;
+        const int32_t width = __shfl_sync(0xffffffffu, len, 0);
+        int64_t off = __ldg(m.blk_ptr + b);
+        Acc<VM> acc[KT];
+#pragma unroll
+        for (int q = 0; q < KT; ++q) acc[q].init();
+        for (int32_t d = 0; d < width; ++d) {
+            const int64_t pos = off + lane;
+            off += __popc(__ballot_sync(0xffffffffu, len > d));
+            if (len > d) {
+                const int ci = ld_stream(m.col + pos);
+                const T vi = ld_stream(val + pos);
+                const T *xr = x + (int64_t)ci * m.ldx + c0;
+#pragma unroll
+                for (int q = 0; q < KT; ++q)
+                    if (c0 + q < m.k) acc[q].add(vi, ld_vec(xr + q));
+            }
+        }
+        if (r < m.n_rows) {
+#pragma unroll
+            for (int q = 0; q < KT; ++q)
+                if (c0 + q < m.k) y[r * m.ldy + c0 + q] = acc[q].result();
+        }
+    }
+}
+
 template <int VM>
 __device__ void batch_item(const BatchMat &m, int64_t rb, int64_t re) {
+    if (m.kind == KIND_JDS && m.format == GBSP_SELL) {
+        int KT = 1;
+        if (m.k > 1) {
+            KT = 2;
+            while (KT < min(m.k, m.rhs_tile > 0 ? min(m.rhs_tile, 16) : 16)) KT <<= 1;
+        }
+        for (int c0 = 0; c0 < m.k; c0 += KT) {
+            switch (KT) {
+                case 1: batch_sell_rows<VM, 1>(m, rb, re, c0); break;
+                case 2: batch_sell_rows<VM, 2>(m, rb, re, c0); break;
+                case 4: batch_sell_rows<VM, 4>(m, rb, re, c0); break;
+                case 8: batch_sell_rows<VM, 8>(m, rb, re, c0); break;
+                default: batch_sell_rows<VM, 16>(m, rb, re, c0); break;
+            }
+        }
+        return;
+    }
     if (m.kind == KIND_CRS) {
         if (m.k == 1) {
             switch (m.lanes) {
@@ -263,6 +317,7 @@ gbsp_status make_work(int32_t n, const gbsp_batch_item *items, int32_t chunk, cu
         m.col = A.col;
         m.jd_ptr = A.jd_ptr;
         m.blk_ptr = A.blk_ptr;
+        m.rlen = A.rlen;
         m.val = A.val;
         m.x = it.X;
         m.y = it.Y;
@@ -292,6 +347,18 @@ gbsp_status make_work(int32_t n, const gbsp_batch_item *items, int32_t chunk, cu
                 re = std::max(std::min(re, A.n_rows), lo);
                 work->push_back(BatchWork{b, 0, rb, re});
                 rb = re;
+            }
+        } else if (A.format == GBSP_SELL) {
+            // whole 32-row blocks of about `chunk` entries
+            std::vector<int32_t> bp((size_t)A.n_blocks + 1);
+            GBSP_CUDA(cudaMemcpyAsync(bp.data(), A.blk_ptr, 4 * (A.n_blocks + 1), cudaMemcpyDeviceToHost, s));
+            GBSP_CUDA(cudaStreamSynchronize(s));
+            int64_t b0 = 0;
+            while (b0 < A.n_blocks) {
+                int64_t b1 = b0 + 1;
+                while (b1 < A.n_blocks && (int64_t)bp[(size_t)b1 + 1] - bp[(size_t)b0] <= chunk) ++b1;
+                work->push_back(BatchWork{b, 0, b0 * 32, std::min(b1 * 32, A.n_rows)});
+                b0 = b1;
             }
         } else {
             // JDS family: rows are sorted by decreasing length; entries of

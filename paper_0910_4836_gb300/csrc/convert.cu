@@ -435,6 +435,62 @@ __global__ void sojds_kernel(int64_t n_rows, int64_t n_diag, int64_t block, int6
     }
 }
 
+// --------------------------------------------------------------- SELL ----
+// Sort key: window index in the high bits, (max_len - len) in the low bits,
+// so a stable ascending sort groups rows by window and, inside a window,
+// orders them by decreasing length with ties in row order.
+__global__ void sell_key_kernel(int64_t n, const int32_t *__restrict__ len, int32_t max_len,
+                                int64_t window, int lbits, uint32_t *keys) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) keys[i] = ((uint32_t)(i / window) << lbits) | (uint32_t)(max_len - len[i]);
+}
+
+__global__ void sell_rlen_kernel(int64_t n, const int32_t *__restrict__ perm,
+                                 const int32_t *__restrict__ len, int32_t *rlen) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) rlen[r] = len[perm[r]];
+}
+
+// entries per block of 32 permuted rows (one warp per block)
+__global__ void sell_block_nnz_kernel(int64_t n, int64_t nb, const int32_t *__restrict__ rlen,
+                                      int32_t *blk_nnz) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t l = r < n ? rlen[r] : 0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+    if ((threadIdx.x & 31) == 0 && (r >> 5) < nb) blk_nnz[r >> 5] = l;
+}
+
+// Thread per permuted row, warps aligned to 32-row blocks: slot d of the
+// block holds the rows with length > d, which are the block's first rows
+// (sorted), so the position of row r's slot d is
+// blk_ptr[b] + (entries of slots < d in the block) + (r mod 32).
+template <typename T>
+__global__ void sell_scatter_kernel(int64_t n, const int32_t *__restrict__ perm,
+                                    const int32_t *__restrict__ iperm, const int32_t *__restrict__ rlen,
+                                    const int32_t *__restrict__ blk_ptr,
+                                    const int32_t *__restrict__ row_ptr,
+                                    const int32_t *__restrict__ col, const T *__restrict__ val,
+                                    int symmetric, int32_t *col_out, T *val_out, int32_t *vmap) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int32_t len = r < n ? rlen[r] : 0;
+    const int64_t src = r < n ? (int64_t)row_ptr[perm[r]] : 0;
+    int64_t off = (r >> 5) <= (n - 1) / 32 ? blk_ptr[r >> 5] : 0;
+    for (int32_t d = 0;; ++d) {
+        const unsigned mask = __ballot_sync(0xffffffffu, len > d);
+        if (!mask) break;
+        if (len > d) {
+            const int64_t dst = off + lane;
+            const int32_t c = col[src + d];
+            col_out[dst] = symmetric ? iperm[c] : c;
+            val_out[dst] = val[src + d];
+            if (vmap) vmap[dst] = (int32_t)(src + d);
+        }
+        off += __popc(mask);
+    }
+}
+
 // ------------------------------------------------------------- host side --
 
 static int bits_for(uint64_t maxv) {
@@ -460,6 +516,21 @@ gbsp_status jds_plan_impl(const Mat &A, const gbsp_jds_opts &o, int32_t *d_scrat
     out->n_diag = max_len;
     const bool blocked = o.format == GBSP_RBJDS || o.format == GBSP_SOJDS;
     out->n_blocks = blocked ? ceil_div(A.n_rows, block) : 0;
+    if (o.format == GBSP_SELL) {
+        const int64_t window = o.window > 0 ? o.window : 1024;
+        if (window % 32) {
+            set_error("gbsp_jds_plan: the SELL window must be a multiple of 32");
+            return GBSP_ERR_ARG;
+        }
+        if (bits_for((uint64_t)std::max<int64_t>(A.n_rows - 1, 0) / window) + bits_for((uint64_t)max_len) > 32) {
+            set_error("gbsp_jds_plan: SELL sort key exceeds 32 bits; use a larger window");
+            return GBSP_ERR_UNSUPPORTED;
+        }
+        out->n_blocks = ceil_div(A.n_rows, 32);
+        out->workspace_bytes = align256(4 * A.n_rows) * 2 + sort_ws_bytes(A.n_rows) +
+                               align256(4 * (out->n_blocks + 1)) + align256(scan_ws_bytes(out->n_blocks + 1)) + 256;
+        return GBSP_OK;
+    }
     // workspace: lengths, keys, sort buffers, diagLen (+ RBJDS staging)
     int64_t ws = align256(4 * A.n_rows) + align256(4 * A.n_rows) + sort_ws_bytes(A.n_rows) +
                  align256(4 * (max_len + 1)) + align256(scan_ws_bytes(max_len + 1)) + 256;
@@ -512,8 +583,85 @@ static gbsp_status relayout_blocked(const Mat &J, int64_t block, int format, con
     return GBSP_OK;
 }
 
+static gbsp_status sell_build_impl(const Mat &A, const gbsp_jds_opts &o, const gbsp_jds_buffers &b,
+                                   const gbsp_jds_sizes &sz, cudaStream_t s, Mat *J) {
+    const int64_t n = A.n_rows;
+    const int symmetric = o.perm_mode == GBSP_PERM_SYMMETRIC;
+    const int64_t window = o.window > 0 ? o.window : 1024;
+    const int64_t nb = ceil_div(n, 32);
+    char *p = static_cast<char *>(b.workspace);
+    int32_t *len = reinterpret_cast<int32_t *>(p);
+    p += align256(4 * n);
+    uint32_t *keys = reinterpret_cast<uint32_t *>(p);
+    p += align256(4 * n);
+    SortWs sw = carve_sort_ws(p, n);
+    int32_t *blk_nnz = reinterpret_cast<int32_t *>(p);
+    p += align256(4 * (nb + 1));
+    int32_t *scan_ws = reinterpret_cast<int32_t *>(p);
+    p += align256(scan_ws_bytes(nb + 1));
+    int32_t *max_len_d = reinterpret_cast<int32_t *>(p);
+    GBSP_CUDA(cudaMemsetAsync(max_len_d, 0, 4, s));
+    if (n > 0) {
+        const unsigned gr = (unsigned)ceil_div(n, 256);
+        row_len_kernel<<<gr, 256, 0, s>>>(n, A.row_ptr, len, max_len_d);
+        const int lbits = bits_for((uint64_t)sz.n_diag);
+        const int wbits = bits_for((uint64_t)(n - 1) / window);
+        sell_key_kernel<<<gr, 256, 0, s>>>(n, len, (int32_t)sz.n_diag, window, lbits, keys);
+        GBSP_LAUNCH_CHECK("sell keys");
+        uint32_t *ks = nullptr;
+        int32_t *vs = nullptr;
+        gbsp_status st = radix_sort_index(keys, n, lbits + wbits, sw, s, &ks, &vs);
+        if (st != GBSP_OK) return st;
+        GBSP_CUDA(cudaMemcpyAsync(b.perm, vs, 4 * n, cudaMemcpyDeviceToDevice, s));
+        inverse_perm_kernel<<<gr, 256, 0, s>>>(n, b.perm, b.iperm);
+        sell_rlen_kernel<<<gr, 256, 0, s>>>(n, b.perm, len, b.rlen);
+        sell_block_nnz_kernel<<<(unsigned)ceil_div(nb * 32, 256), 256, 0, s>>>(n, nb, b.rlen, blk_nnz);
+        GBSP_LAUNCH_CHECK("sell perm / lengths");
+        st = scan_exclusive(blk_nnz, nb, b.blk_ptr, b.blk_ptr + nb, scan_ws, s);
+        if (st != GBSP_OK) return st;
+        if (A.dtype == GBSP_F64)
+            sell_scatter_kernel<double><<<(unsigned)ceil_div(nb * 32, 256), 256, 0, s>>>(
+                n, b.perm, b.iperm, b.rlen, b.blk_ptr, A.row_ptr, A.col, static_cast<const double *>(A.val),
+                symmetric, b.col, static_cast<double *>(b.val), b.vmap);
+        else
+            sell_scatter_kernel<float><<<(unsigned)ceil_div(nb * 32, 256), 256, 0, s>>>(
+                n, b.perm, b.iperm, b.rlen, b.blk_ptr, A.row_ptr, A.col, static_cast<const float *>(A.val),
+                symmetric, b.col, static_cast<float *>(b.val), b.vmap);
+        GBSP_LAUNCH_CHECK("sell_scatter_kernel");
+    } else {
+        GBSP_CUDA(cudaMemsetAsync(b.blk_ptr, 0, 4, s));
+    }
+    J->kind = KIND_JDS;
+    J->n_rows = A.n_rows;
+    J->n_cols = A.n_cols;
+    J->nnz = A.nnz;
+    J->dtype = A.dtype;
+    J->device = A.device;
+    J->col = b.col;
+    J->val = b.val;
+    J->format = GBSP_SELL;
+    J->perm_mode = o.perm_mode;
+    J->block = 32;
+    J->built_block = 32;
+    J->unroll = o.unroll > 0 ? o.unroll : 4;
+    J->window = (int32_t)window;
+    J->n_diag = sz.n_diag;
+    J->n_blocks = nb;
+    J->jd_ptr = nullptr;
+    J->perm = b.perm;
+    J->iperm = b.iperm;
+    J->blk_ptr = b.blk_ptr;
+    J->rlen = b.rlen;
+    J->vmap = b.vmap;
+    J->kopt = A.kopt;
+    J->kopt.rows_per_warp = 1;
+    GBSP_CUDA(cudaStreamSynchronize(s));
+    return GBSP_OK;
+}
+
 gbsp_status jds_build_impl(const Mat &A, const gbsp_jds_opts &o, const gbsp_jds_buffers &b,
                            const gbsp_jds_sizes &sz, cudaStream_t s, Mat *J) {
+    if (o.format == GBSP_SELL) return sell_build_impl(A, o, b, sz, s, J);
     const int64_t n = A.n_rows;
     const int symmetric = o.perm_mode == GBSP_PERM_SYMMETRIC;
     const bool blocked = o.format == GBSP_RBJDS || o.format == GBSP_SOJDS;

@@ -45,6 +45,8 @@ struct Mat {
     int64_t n_diag = 0, n_blocks = 0;
     const int32_t *jd_ptr = nullptr, *perm = nullptr, *iperm = nullptr, *blk_ptr = nullptr;
     const int32_t *vmap = nullptr;  // JDS position -> CRS entry (optional)
+    const int32_t *rlen = nullptr;  // SELL: length of every permuted row
+    int32_t window = 0;             // SELL: rows per sorting window
     std::vector<int32_t> h_jd_ptr;  // host copy, read back once at build (literal launches)
 
     // transposed structure (CRS handle built by gbsp_transpose_build)

@@ -39,6 +39,7 @@ struct JdsArgs {
     int32_t block;
     const int32_t *x_perm;  // x index = x_perm[col] (ORIGINAL basis, symmetric storage)
     const int32_t *y_perm;  // y row = y_perm[r]      (ORIGINAL basis)
+    const int32_t *rlen;    // SELL: permuted row lengths
 };
 
 __device__ __forceinline__ int64_t xidx(const int32_t *x_perm, int32_t c) {
@@ -75,31 +76,47 @@ __global__ void __launch_bounds__(256) jds_row_kernel(JdsArgs a) {
         Acc<VM> acc[R];
 #pragma unroll
         for (int i = 0; i < R; ++i) acc[i].init();
-        int32_t st = __ldg(a.jd_ptr);
+        // offsets of step 0 and its loads; each step then fetches the next
+        // step's offsets before forming its own products, so the small
+        // jd_ptr loads overlap the gathers instead of preceding them
+        int32_t e[U + 1];
+        e[0] = __ldg(a.jd_ptr);
+#pragma unroll
+        for (int j = 0; j < U; ++j) e[j + 1] = (j < a.n_diag) ? __ldg(a.jd_ptr + j + 1) : e[j];
+        int c[R][U];
+        T v[R][U];
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const bool ok = e[j + 1] - e[j] > rr[i];
+                c[i][j] = ok ? ld_stream(a.col + e[j] + rr[i]) : -1;
+                v[i][j] = ok ? ld_stream(val + e[j] + rr[i]) : T(0);
+            }
         for (int64_t d0 = 0; d0 < a.n_diag; d0 += U) {
-            int32_t e[U + 1];
-            e[0] = st;
+            int32_t en[U + 1];
+            en[0] = e[U];
 #pragma unroll
             for (int j = 0; j < U; ++j)
-                e[j + 1] = (d0 + j < a.n_diag) ? __ldg(a.jd_ptr + d0 + j + 1) : e[j];
+                en[j + 1] = (d0 + U + j < a.n_diag) ? __ldg(a.jd_ptr + d0 + U + j + 1) : en[j];
             // rr[0] is the thread's longest row (rows are sorted by length)
-            if (e[1] - e[0] <= rr[0]) break;
-            int c[R][U];
-            T v[R][U];
-#pragma unroll
-            for (int i = 0; i < R; ++i)
-#pragma unroll
-                for (int j = 0; j < U; ++j) {
-                    const bool ok = e[j + 1] - e[j] > rr[i];
-                    c[i][j] = ok ? ld_stream(a.col + e[j] + rr[i]) : -1;
-                    v[i][j] = ok ? ld_stream(val + e[j] + rr[i]) : T(0);
-                }
+            const bool more = d0 + U < a.n_diag && en[1] - en[0] > rr[0];
 #pragma unroll
             for (int i = 0; i < R; ++i)
 #pragma unroll
                 for (int j = 0; j < U; ++j)
                     if (c[i][j] >= 0) acc[i].add(v[i][j], ld_vec(x + xidx(a.x_perm, c[i][j]) * a.ldx));
-            st = e[U];
+            if (!more) break;
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+#pragma unroll
+                for (int j = 0; j < U; ++j) {
+                    const bool ok = en[j + 1] - en[j] > rr[i];
+                    c[i][j] = ok ? ld_stream(a.col + en[j] + rr[i]) : -1;
+                    v[i][j] = ok ? ld_stream(val + en[j] + rr[i]) : T(0);
+                }
+#pragma unroll
+            for (int j = 0; j <= U; ++j) e[j] = en[j];
         }
 #pragma unroll
         for (int i = 0; i < R; ++i)
@@ -162,6 +179,63 @@ __global__ void __launch_bounds__(256) jds_block_kernel(JdsArgs a) {
                 for (int q = 0; q < KT; ++q)
                     if (KT == 1 || a.c0 + q < a.k) store_row<VM>(a, rr[i], a.c0 + q, acc[i][q]);
             }
+        }
+    }
+}
+
+// SELL-32-sigma: one warp per block of 32 permuted rows, lane = row.  Slot
+// d of the block holds the rows with length > d, which are its first
+// popc(ballot(len > d)) rows, so lane l's entry of slot d sits at
+// (start of slot d) + l: every warp-wide load is one contiguous segment.
+// A CTA's warps take consecutive blocks, so a 1024-thread CTA works on one
+// 1024-row window at a time and its gathers of x stay local.  U slots per
+// step; KT right-hand sides per thread (SpMM).  Row entries are added in
+// slot order, as in every JDS-family kernel.
+template <int VM, int U, int KT>
+__global__ void __launch_bounds__(1024) sell_kernel(JdsArgs a) {
+    typedef typename ValT<VM>::T T;
+    const T *__restrict__ val = static_cast<const T *>(a.val);
+    const T *__restrict__ x = static_cast<const T *>(a.x);
+    const int lane = threadIdx.x & 31;
+    const int64_t nb = ceil_div_dev(a.n_rows, 32);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = warp; b < nb; b += nwarp) {
+        const int64_t r = b * 32 + lane;
+        const int32_t len = r < a.n_rows ? __ldg(a.rlen + r) : 0;
+        const int32_t width = __shfl_sync(0xffffffffu, len, 0);  // lane 0 holds the longest row
+        int64_t off = __ldg(a.blk_ptr + b);
+        Acc<VM> acc[KT];
+#pragma unroll
+        for (int q = 0; q < KT; ++q) acc[q].init();
+        for (int32_t d0 = 0; d0 < width; d0 += U) {
+            int64_t pos[U];
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                pos[j] = off + lane;
+                off += __popc(__ballot_sync(0xffffffffu, len > d0 + j));
+            }
+            int c[U];
+            T v[U];
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const bool ok = len > d0 + j;
+                c[j] = ok ? ld_stream(a.col + pos[j]) : -1;
+                v[j] = ok ? ld_stream(val + pos[j]) : T(0);
+            }
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                if (c[j] < 0) continue;
+                const T *xr = x + xidx(a.x_perm, c[j]) * a.ldx + a.c0;
+#pragma unroll
+                for (int q = 0; q < KT; ++q)
+                    if (KT == 1 || a.c0 + q < a.k) acc[q].add(v[j], ld_vec(xr + q));
+            }
+        }
+        if (r < a.n_rows) {
+#pragma unroll
+            for (int q = 0; q < KT; ++q)
+                if (KT == 1 || a.c0 + q < a.k) store_row<VM>(a, r, a.c0 + q, acc[q]);
         }
     }
 }
@@ -238,10 +312,45 @@ static void launch_block(const JdsArgs &a, int KT, cudaStream_t s) {
     else jds_block_kernel<VM, CONTIG, 8, 1><<<grid, threads, 0, s>>>(a);
 }
 
+template <int VM, int U>
+static void launch_sell_U(JdsArgs a, int KT, cudaStream_t s) {
+    const int64_t nb = ceil_div(a.n_rows, 32);
+    const int threads = 1024;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(nb * 32, threads), (int64_t)num_sms() * 2));
+    switch (KT) {
+        case 1: sell_kernel<VM, U, 1><<<(unsigned)grid, threads, 0, s>>>(a); break;
+        case 2: sell_kernel<VM, U, 2><<<(unsigned)grid, threads, 0, s>>>(a); break;
+        case 4: sell_kernel<VM, U, 4><<<(unsigned)grid, threads, 0, s>>>(a); break;
+        case 8: sell_kernel<VM, U, 8><<<(unsigned)grid, threads, 0, s>>>(a); break;
+        default: sell_kernel<VM, U, 16><<<(unsigned)grid, threads, 0, s>>>(a); break;
+    }
+}
+
+template <int VM>
+static void launch_sell(const Mat &A, JdsArgs a, cudaStream_t s) {
+    int KT = 1;
+    if (a.k > 1) {
+        const int tile = A.kopt.rhs_tile > 0 ? std::min(A.kopt.rhs_tile, 16) : 16;
+        const int cols = std::min(a.k, tile);
+        KT = 2;
+        while (KT < cols) KT <<= 1;
+    }
+    for (int c0 = 0; c0 < a.k; c0 += KT) {
+        a.c0 = c0;
+        if (KT > 1 || A.unroll <= 1) launch_sell_U<VM, 1>(a, KT, s);
+        else if (A.unroll <= 2) launch_sell_U<VM, 2>(a, KT, s);
+        else launch_sell_U<VM, 4>(a, KT, s);
+    }
+}
+
 template <int VM>
 static gbsp_status launch_family(const Mat &A, JdsArgs a, cudaStream_t s) {
     typedef typename ValT<VM>::T T;
     const int fmt = A.format;
+    if (fmt == GBSP_SELL) {
+        launch_sell<VM>(A, a, s);
+        return GBSP_OK;
+    }
     if (a.k > 1 || fmt == GBSP_NBJDS || fmt == GBSP_RBJDS || fmt == GBSP_SOJDS) {
         const bool contig = fmt == GBSP_RBJDS || fmt == GBSP_SOJDS;
         if (!contig && fmt != GBSP_NBJDS) a.block = 256;  // JDS / NUJDS walked per 256-row block
@@ -306,6 +415,7 @@ gbsp_status jds_launch(const Mat &A, const VecArgs &v, cudaStream_t s) {
                                                                  : std::max(A.block, 1);
     a.x_perm = v.x_perm;
     a.y_perm = v.y_perm;
+    a.rlen = A.rlen;
     gbsp_status st;
     if (A.dtype == GBSP_F64) st = launch_family<VM_F64>(A, a, s);
     else if (A.kopt.accum == GBSP_ACC_COMPENSATED) st = launch_family<VM_F32C>(A, a, s);

@@ -178,8 +178,10 @@ class CRSMatrix(_Product):
         self.set_kernel("tiled")
 
     def to_jds(self, fmt: str = "JDS", perm: str = "symmetric", block: int = 256, unroll: int = 4,
-               stream=None, value_map: bool = False) -> "JDSMatrix":
-        return JDSMatrix(self, fmt, perm, block, unroll, stream, value_map)
+               stream=None, value_map: bool = False, window: int = 1024) -> "JDSMatrix":
+        """Convert on the GPU to a JDS-family format (JDS, NBJDS, NUJDS,
+        RBJDS, SOJDS, JDS_LITERAL, or SELL with a sorting `window`)."""
+        return JDSMatrix(self, fmt, perm, block, unroll, stream, value_map, window)
 
     def transpose(self, stream=None) -> "CRSMatrix":
         """Build the transposed structure (a CRS of A^T with its entry map)
@@ -250,13 +252,13 @@ class JDSMatrix(_Product):
     (rows and columns permuted, the paper's scheme) or 'row_only'."""
 
     def __init__(self, A: CRSMatrix, fmt="JDS", perm="symmetric", block=256, unroll=4, stream=None,
-                 value_map: bool = False):
+                 value_map: bool = False, window: int = 1024):
         super().__init__()
         lib = L.load()
         dev = A._device
         self.dtype, self.n_rows, self.n_cols, self.nnz = A.dtype, A.n_rows, A.n_cols, A.nnz
         self._device = dev
-        opts = L.JdsOpts(L.FORMATS[fmt], L.PERM[perm], block, unroll)
+        opts = L.JdsOpts(L.FORMATS[fmt], L.PERM[perm], block, unroll, window)
         sizes = L.JdsSizes()
         scratch = torch.empty(16, dtype=torch.int32, device=dev)
         L.check(lib.gbsp_jds_plan(A.handle, ctypes.byref(opts), _vp(scratch), _stream(stream),
@@ -269,17 +271,19 @@ class JDSMatrix(_Product):
         self.perm = torch.empty(A.n_rows, dtype=torch.int32, device=dev)
         self.iperm = torch.empty(A.n_rows, dtype=torch.int32, device=dev)
         self.blk_ptr = (torch.empty(sizes.n_blocks + 1, dtype=torch.int32, device=dev)
-                        if fmt in ("RBJDS", "SOJDS") else None)
+                        if fmt in ("RBJDS", "SOJDS", "SELL") else None)
+        self.rlen = torch.empty(A.n_rows, dtype=torch.int32, device=dev) if fmt == "SELL" else None
         work = torch.empty(max(sizes.workspace_bytes, 1), dtype=torch.uint8, device=dev)
         self.vmap = torch.empty(A.nnz, dtype=torch.int32, device=dev) if value_map else None
         bufs = L.JdsBuffers(_vp(self.jd_ptr).value, _vp(self.col).value, _vp(self.val).value,
                             _vp(self.perm).value, _vp(self.iperm).value, _vp(self.blk_ptr).value,
-                            _vp(work).value, _vp(self.vmap).value)
+                            _vp(work).value, _vp(self.vmap).value, _vp(self.rlen).value)
         L.check(lib.gbsp_jds_build(A.handle, ctypes.byref(opts), ctypes.byref(bufs),
                                    ctypes.byref(sizes), _stream(stream), ctypes.byref(self._h)),
                 "gbsp_jds_build")
         del work  # the build synchronised the stream
         self.fmt, self.perm_mode, self.block, self.unroll = fmt, perm, block, unroll
+        self.window = window if fmt == "SELL" else None
         self.symmetric = perm == "symmetric"
 
     def refresh_values(self, crs_val: torch.Tensor, stream=None) -> None:

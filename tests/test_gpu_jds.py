@@ -53,6 +53,49 @@ def test_conversion_bit_exact(mi, perm):
         check_arrays(J, Oj, fmt, block)
 
 
+@pytest.mark.parametrize("mi", range(len(MATS)))
+@pytest.mark.parametrize("perm", ["symmetric", "row_only"])
+def test_sell_conversion_and_products(mi, perm):
+    A = MATS[mi]()
+    M = crs(A)
+    x = S.vector(A.n_cols, 51 + mi)
+    ref, s = O.crs_spmv_exact(A, x)
+    Jref = None
+    for window in (32, 256, 1024, 32 * ((A.n_rows + 31) // 32)):
+        Os = O.sell_build(A, window, symmetric=perm == "symmetric")
+        G = M.to_jds("SELL", perm, window=window, value_map=True)
+        assert np.array_equal(host(G.perm), Os.perm)
+        assert np.array_equal(host(G.iperm), Os.iperm)
+        assert np.array_equal(host(G.rlen), Os.rlen)
+        assert np.array_equal(host(G.blk_ptr), Os.blk_ptr)
+        assert np.array_equal(host(G.col), Os.col)
+        assert np.array_equal(host(G.val).view(np.int64), Os.val.view(np.int64))
+        xp = O.permute(Os.perm, x) if perm == "symmetric" else x
+        for u in (1, 2, 4):
+            G.set_format("SELL", unroll=u)
+            yp = host(G.spmv(dev(xp)))
+            assert_close64(yp, O.permute(Os.perm, ref), O.permute(Os.perm, s), f"SELL w={window} u={u}")
+            assert_close64(host(G.spmv_original(dev(x))), ref, s, f"SELL w={window} u={u} original")
+        # the value map re-gathers new values
+        G.refresh_values(dev(A.val * 2.0))
+        assert_close64(host(G.spmv_original(dev(x))) / 2.0, ref, s, "SELL refreshed values")
+        if window >= A.n_rows:
+            # one window: the JDS sort, so per-row sums match the JDS kernels bit for bit
+            J = M.to_jds("JDS", perm)
+            G2 = M.to_jds("SELL", perm, window=window)
+            assert torch.equal(G2.spmv(dev(xp)), J.spmv(dev(xp)))
+
+
+def test_sell_spmm_and_integer():
+    A = S.integer_values(S.hh_like(50_000, 53), 53, 512)
+    X = np.stack([S.int_vector(A.n_cols, 60 + c, 512) for c in range(16)], axis=1)
+    ref = O.crs_spmm(A, X)
+    G = crs(A).to_jds("SELL", "row_only", window=512)
+    for k in (1, 4, 16):
+        Y = host(G.spmm(dev(X[:, :k].copy()), basis=1))
+        assert np.array_equal(Y, ref[:, :k]), k
+
+
 def test_golden_example_on_gpu():
     import json
     import os
