@@ -334,6 +334,8 @@ def run_ours(args):
             result["batched"] = batched_speedups(dev, time_launches)
             torch.cuda.empty_cache()
             result["fwd_bwd"] = fwd_bwd_speedup(dev, time_launches)
+            torch.cuda.empty_cache()
+            result["zipf_rows"] = zipf_numbers(dev, time_launches, peak)
         result["cpu_baseline"] = cpu_baseline(A, x_host, args.cpu_seconds)
     if world > 1:
         torch.distributed.barrier()
@@ -388,6 +390,41 @@ def fp32_numbers(M, A, x, y64, dev, time_launches, ms64):
             "max_err_over_sum_abs_compensated": float(((yc - ref).abs() / den).max()),
             "max_err_over_sum_abs_plain": float(((yp - ref).abs() / den).max()),
             "note": "error of FP32 data and FP32 vector against the FP64 product of the FP64 data"}
+
+
+def zipf_numbers(dev, time_launches, peak):
+    """The irregular workload (N = 4e6, Zipf(2) row lengths up to 5000,
+    random columns): FP64 SpMVM in the candidate schemes; JDS needs the
+    deep-diagonal split, since a few rows have thousands of entries."""
+    import torch
+    from paper_0910_4836_gb300 import CRSMatrix, synth as S
+    A = S.config(2)
+    M = CRSMatrix.from_host(A, device=dev)
+    x = torch.as_tensor(S.vector(A.n_cols, 2)).to(dev)
+    y = torch.empty(A.n_rows, dtype=torch.float64, device=dev)
+    crs_b = algorithmic_bytes(A.n_rows, A.n_cols, A.nnz)
+    out = {"n_rows": A.n_rows, "nnz": A.nnz, "max_row": int(A.row_lengths().max())}
+    runs = []
+    M.set_kernel("vector", lanes=4, rows_per_warp=4)
+    runs.append(("CRS vector l4 r4", lambda: M.spmv(x, out=y), crs_b))
+    M2 = CRSMatrix(M.row_ptr, M.col, M.val, A.n_cols)
+    M2.prepare_tiled(1024)
+    runs.append(("CRS tiled 1024", lambda: M2.spmv(x, out=y), crs_b))
+    J = M.to_jds("NUJDS", "row_only", unroll=2)
+    jb = 12 * A.nnz + 4 * (J.n_diag + 1) + 16 * A.n_rows
+    J.split(16, 64)
+    runs.append(("NUJDS row_only u=2 split 16/64", lambda: J.spmv(x, out=y), jb))
+    table, best = {}, None
+    for name, fn, nbytes in runs:
+        t = statistics.median(time_launches(fn, 10))
+        table[name] = {"gflops": round(2.0 * A.nnz / (t * 1e-3) / 1e9, 1), "ms": round(t, 4),
+                       "gbs": round(nbytes / (t * 1e-3) / 1e9, 1),
+                       "frac": round(nbytes / (t * 1e-3) / 1e9 / peak, 3)}
+        if best is None or t < best[0]:
+            best = (t, name)
+    out["kernels"] = table
+    out["best"] = best[1]
+    return out
 
 
 def batched_speedups(dev, time_launches):

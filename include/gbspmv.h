@@ -249,6 +249,22 @@ gbsp_status gbsp_jds_set_format(gbsp_handle jds, int32_t format, int32_t block, 
  * Errors: GBSP_ERR_UNSUPPORTED if the handle was built without vmap. */
 gbsp_status gbsp_jds_values(gbsp_handle jds, const void *d_src_val, void *stream);
 
+/* Deep-diagonal split for the JDS and NUJDS walks (GB300 addition; the
+ * paper has none).  The thread of a permuted row walks its jagged diagonals
+ * one after another, so a few very long rows (heavy-tailed row lengths)
+ * would serialise the whole product.  With a split, diagonals >= depth are
+ * summed by a separate kernel in chunks of `chunk` diagonals -- one thread
+ * per (row, chunk), so the long rows are spread over many threads -- into
+ * partial sums in caller workspace, and the row walk stops at `depth` and
+ * adds the row's partial sums in chunk order (deterministic; the grouping
+ * of the sum differs from the unsplit walk).  Two launches per product;
+ * k = 1 only (SpMM ignores the split).  depth = 0 removes the split.
+ * Workspace bytes from gbsp_jds_split_bytes; 256-byte aligned; borrowed
+ * until destroy or the next gbsp_jds_split.  Synchronises `stream`. */
+gbsp_status gbsp_jds_split_bytes(gbsp_handle jds, int32_t depth, int32_t chunk, int64_t *bytes);
+gbsp_status gbsp_jds_split(gbsp_handle jds, int32_t depth, int32_t chunk, void *d_ws,
+                           int64_t ws_bytes, void *stream);
+
 /* Read back the JDS-family shape (host-side, no device work). */
 gbsp_status gbsp_jds_info(gbsp_handle jds, gbsp_jds_sizes *out, gbsp_jds_opts *opts);
 

@@ -83,6 +83,8 @@ SIGNATURES = {
     "gbsp_jds_build": (c_i32, [c_vp, P(JdsOpts), P(JdsBuffers), P(JdsSizes), c_vp, P(c_vp)]),
     "gbsp_jds_set_format": (c_i32, [c_vp, c_i32, c_i32, c_i32]),
     "gbsp_jds_info": (c_i32, [c_vp, P(JdsSizes), P(JdsOpts)]),
+    "gbsp_jds_split_bytes": (c_i32, [c_vp, c_i32, c_i32, P(c_i64)]),
+    "gbsp_jds_split": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_i64, c_vp]),
     "gbsp_permute_vec": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_i64, c_vp, c_i64, c_vp]),
     "gbsp_spmv": (c_i32, [c_vp, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp]),
     "gbsp_spmm": (c_i32, [c_vp, c_i32, c_i32, c_i32, c_vp, c_i64, c_vp, c_i64, c_i32, c_vp]),

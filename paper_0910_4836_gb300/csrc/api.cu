@@ -286,6 +286,29 @@ gbsp_status gbsp_jds_set_format(gbsp_handle h, int32_t format, int32_t block, in
     return GBSP_OK;
 }
 
+gbsp_status gbsp_jds_split_bytes(gbsp_handle h, int32_t depth, int32_t chunk, int64_t *bytes) {
+    if (!h || !bytes) return arg_error("gbsp_jds_split_bytes: NULL argument");
+    if (h->kind != KIND_JDS || h->built_block > 0)
+        return arg_error("gbsp_jds_split_bytes: needs a JDS / NUJDS handle (JDS storage)");
+    if (depth < 1 || chunk < 1) return arg_error("gbsp_jds_split_bytes: depth and chunk must be >= 1");
+    return jds_split_bytes_impl(*h, depth, chunk, bytes);
+}
+
+gbsp_status gbsp_jds_split(gbsp_handle h, int32_t depth, int32_t chunk, void *d_ws, int64_t ws_bytes,
+                           void *stream) {
+    if (!h) return arg_error("gbsp_jds_split: NULL handle");
+    if (h->kind != KIND_JDS || h->built_block > 0)
+        return arg_error("gbsp_jds_split: needs a JDS / NUJDS handle (JDS storage)");
+    if (depth == 0) {
+        h->split_k = 0;
+        h->split_depth = 0;
+        return GBSP_OK;
+    }
+    if (depth < 1 || chunk < 1 || !d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255))
+        return arg_error("gbsp_jds_split: bad depth / chunk, or workspace not 256-byte aligned");
+    return jds_split_impl(*h, depth, chunk, d_ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
 gbsp_status gbsp_jds_info(gbsp_handle h, gbsp_jds_sizes *out, gbsp_jds_opts *opts) {
     if (!h) return arg_error("gbsp_jds_info: NULL handle");
     if (h->kind != KIND_JDS) return arg_error("gbsp_jds_info: not a JDS-family handle");

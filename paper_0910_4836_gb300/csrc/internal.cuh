@@ -47,6 +47,14 @@ struct Mat {
     const int32_t *vmap = nullptr;  // JDS position -> CRS entry (optional)
     const int32_t *rlen = nullptr;  // SELL: length of every permuted row
     int32_t window = 0;             // SELL: rows per sorting window
+
+    // JDS / NUJDS deep-diagonal split (caller workspace): diagonals >= split_depth
+    // are summed in chunks by a separate kernel into ragged partial sums
+    int32_t split_depth = 0, split_chunk = 0, split_k = 0;
+    int64_t split_items_total = 0;
+    const int4 *split_table = nullptr;  // per chunk {d_begin, d_end, rows, partial offset}
+    const int32_t *split_items = nullptr;  // per chunk: first CTA item (k+1 entries)
+    void *split_part = nullptr;
     std::vector<int32_t> h_jd_ptr;  // host copy, read back once at build (literal launches)
 
     // transposed structure (CRS handle built by gbsp_transpose_build)
@@ -114,6 +122,8 @@ void crs_default_opts(Mat &A);
 gbsp_status jds_launch(const Mat &A, const VecArgs &v, cudaStream_t s);
 gbsp_status permute_launch(const Mat &A, int32_t dir, int32_t k, const void *in, int64_t ld_in,
                            void *out, int64_t ld_out, cudaStream_t s);
+gbsp_status jds_split_bytes_impl(const Mat &A, int32_t depth, int32_t chunk, int64_t *bytes);
+gbsp_status jds_split_impl(Mat &A, int32_t depth, int32_t chunk, void *ws, int64_t bytes, cudaStream_t s);
 
 // convert.cu ------------------------------------------------------------
 gbsp_status jds_plan_impl(const Mat &A, const gbsp_jds_opts &o, int32_t *d_scratch,

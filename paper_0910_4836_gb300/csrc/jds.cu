@@ -40,6 +40,13 @@ struct JdsArgs {
     const int32_t *x_perm;  // x index = x_perm[col] (ORIGINAL basis, symmetric storage)
     const int32_t *y_perm;  // y row = y_perm[r]      (ORIGINAL basis)
     const int32_t *rlen;    // SELL: permuted row lengths
+    // deep-diagonal split (JDS / NUJDS): the walk stops at d_limit and adds
+    // the chunk partial sums of rows that go deeper
+    int64_t d_limit;
+    int32_t split_k;
+    const int4 *split_table;
+    const int32_t *split_items;
+    const void *split_part;
 };
 
 __device__ __forceinline__ int64_t xidx(const int32_t *x_perm, int32_t c) {
@@ -82,7 +89,7 @@ __global__ void __launch_bounds__(256) jds_row_kernel(JdsArgs a) {
         int32_t e[U + 1];
         e[0] = __ldg(a.jd_ptr);
 #pragma unroll
-        for (int j = 0; j < U; ++j) e[j + 1] = (j < a.n_diag) ? __ldg(a.jd_ptr + j + 1) : e[j];
+        for (int j = 0; j < U; ++j) e[j + 1] = (j < a.d_limit) ? __ldg(a.jd_ptr + j + 1) : e[j];
         int c[R][U];
         T v[R][U];
 #pragma unroll
@@ -93,14 +100,15 @@ __global__ void __launch_bounds__(256) jds_row_kernel(JdsArgs a) {
                 c[i][j] = ok ? ld_stream(a.col + e[j] + rr[i]) : -1;
                 v[i][j] = ok ? ld_stream(val + e[j] + rr[i]) : T(0);
             }
-        for (int64_t d0 = 0; d0 < a.n_diag; d0 += U) {
+        const int64_t dlim = a.d_limit;
+        for (int64_t d0 = 0; d0 < dlim; d0 += U) {
             int32_t en[U + 1];
             en[0] = e[U];
 #pragma unroll
             for (int j = 0; j < U; ++j)
-                en[j + 1] = (d0 + U + j < a.n_diag) ? __ldg(a.jd_ptr + d0 + U + j + 1) : en[j];
+                en[j + 1] = (d0 + U + j < dlim) ? __ldg(a.jd_ptr + d0 + U + j + 1) : en[j];
             // rr[0] is the thread's longest row (rows are sorted by length)
-            const bool more = d0 + U < a.n_diag && en[1] - en[0] > rr[0];
+            const bool more = d0 + U < dlim && en[1] - en[0] > rr[0];
 #pragma unroll
             for (int i = 0; i < R; ++i)
 #pragma unroll
@@ -118,9 +126,56 @@ __global__ void __launch_bounds__(256) jds_row_kernel(JdsArgs a) {
 #pragma unroll
             for (int j = 0; j <= U; ++j) e[j] = en[j];
         }
+        // deeper diagonals: the chunk partial sums, in chunk order
+        if (a.split_k > 0) {
+            const Acc<VM> *part = static_cast<const Acc<VM> *>(a.split_part);
+            for (int32_t k = 0; k < a.split_k; ++k) {
+                const int4 t = __ldg(a.split_table + k);
+                if (rr[0] >= t.z) break;  // rows of chunk k are [0, t.z)
+#pragma unroll
+                for (int i = 0; i < R; ++i)
+                    if (rr[i] < t.z) acc[i].merge(part[(int64_t)t.w + rr[i]]);
+            }
+        }
 #pragma unroll
         for (int i = 0; i < R; ++i)
             if (rr[i] < a.n_rows) store_row<VM>(a, rr[i], 0, acc[i]);
+    }
+}
+
+// Deep part of a split JDS walk: CTA items are (chunk k, 256 rows); thread
+// row r sums its entries in diagonals [d_begin, d_end) of chunk k, in slot
+// order, into part[offset_k + r].
+template <int VM>
+__global__ void __launch_bounds__(256) jds_deep_kernel(JdsArgs a, int64_t n_items) {
+    typedef typename ValT<VM>::T T;
+    const T *__restrict__ val = static_cast<const T *>(a.val);
+    const T *__restrict__ x = static_cast<const T *>(a.x);
+    Acc<VM> *part = static_cast<Acc<VM> *>(const_cast<void *>(a.split_part));
+    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+        int32_t k = 0;
+        while (k + 1 < a.split_k && __ldg(a.split_items + k + 1) <= it) ++k;
+        const int4 t = __ldg(a.split_table + k);
+        const int64_t r = (it - __ldg(a.split_items + k)) * 256 + threadIdx.x;
+        if (r >= t.z) continue;
+        Acc<VM> acc;
+        acc.init();
+        int32_t st = __ldg(a.jd_ptr + t.x);
+        for (int32_t d = t.x; d < t.y; d += 2) {
+            const int32_t e1 = __ldg(a.jd_ptr + d + 1);
+            const int32_t e2 = d + 1 < t.y ? __ldg(a.jd_ptr + d + 2) : e1;
+            const bool ok0 = e1 - st > r, ok1 = d + 1 < t.y && e2 - e1 > r;
+            if (!ok0) break;
+            const int c0 = ld_stream(a.col + st + r);
+            const T v0 = ld_stream(val + st + r);
+            const int c1 = ok1 ? ld_stream(a.col + e1 + r) : 0;
+            const T v1 = ok1 ? ld_stream(val + e1 + r) : T(0);
+            acc.add(v0, ld_vec(x + xidx(a.x_perm, c0) * a.ldx));
+            if (ok1) acc.add(v1, ld_vec(x + xidx(a.x_perm, c1) * a.ldx));
+            if (!ok1) break;
+            st = e2;
+        }
+        part[(int64_t)t.w + r] = acc;
     }
 }
 
@@ -387,6 +442,17 @@ static gbsp_status launch_family(const Mat &A, JdsArgs a, cudaStream_t s) {
     }
     const int u = fmt == GBSP_NUJDS ? A.unroll : 1;
     const int R = A.kopt.rows_per_warp > 1 ? A.kopt.rows_per_warp : 1;  // rows per thread
+    if (A.split_k > 0) {
+        // deep diagonals first (chunk partial sums), then the walk that stops
+        // at the split depth and merges them
+        a.d_limit = A.split_depth;
+        a.split_k = A.split_k;
+        a.split_table = A.split_table;
+        a.split_items = A.split_items;
+        a.split_part = A.split_part;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(A.split_items_total, (int64_t)num_sms() * 16));
+        jds_deep_kernel<VM><<<(unsigned)grid, 256, 0, s>>>(a, A.split_items_total);
+    }
     if (u <= 1) launch_row<VM, 1>(a, R, s);
     else if (u <= 2) launch_row<VM, 2>(a, R, s);
     else if (u <= 4) launch_row<VM, 4>(a, R, s);
@@ -416,12 +482,82 @@ gbsp_status jds_launch(const Mat &A, const VecArgs &v, cudaStream_t s) {
     a.x_perm = v.x_perm;
     a.y_perm = v.y_perm;
     a.rlen = A.rlen;
+    a.d_limit = A.n_diag;
+    a.split_k = 0;
     gbsp_status st;
     if (A.dtype == GBSP_F64) st = launch_family<VM_F64>(A, a, s);
     else if (A.kopt.accum == GBSP_ACC_COMPENSATED) st = launch_family<VM_F32C>(A, a, s);
     else st = launch_family<VM_F32>(A, a, s);
     if (st != GBSP_OK) return st;
     GBSP_LAUNCH_CHECK("jds product kernel");
+    return GBSP_OK;
+}
+
+// Split set-up: chunks of `chunk` diagonals from `depth` on; chunk k holds
+// the rows [0, diagLen(d_begin)).  Workspace: the chunk table, the per-chunk
+// first CTA item, then the ragged partial sums (one accumulator per row and
+// chunk).
+static int64_t acc_bytes(int dtype, int accum) {
+    return dtype == GBSP_F64 ? 8 : (accum == GBSP_ACC_COMPENSATED ? 8 : 4);
+}
+
+static void split_plan(const Mat &A, int32_t depth, int32_t chunk, std::vector<int4> *table,
+                       std::vector<int32_t> *items, int64_t *parts) {
+    table->clear();
+    items->clear();
+    int64_t off = 0, it = 0;
+    for (int64_t d0 = depth; d0 < A.n_diag; d0 += chunk) {
+        const int64_t d1 = std::min<int64_t>(d0 + chunk, A.n_diag);
+        const int64_t rows = A.h_jd_ptr[d0 + 1] - A.h_jd_ptr[d0];
+        if (rows <= 0) break;
+        table->push_back(make_int4((int)d0, (int)d1, (int)rows, (int)off));
+        items->push_back((int32_t)it);
+        off += rows;
+        it += ceil_div(rows, 256);
+    }
+    items->push_back((int32_t)it);
+    *parts = off;
+}
+
+gbsp_status jds_split_bytes_impl(const Mat &A, int32_t depth, int32_t chunk, int64_t *bytes) {
+    std::vector<int4> t;
+    std::vector<int32_t> it;
+    int64_t parts = 0;
+    split_plan(A, depth, chunk, &t, &it, &parts);
+    *bytes = 256 + 16 * (int64_t)t.size() + 4 * (int64_t)it.size() + 16 + parts * acc_bytes(A.dtype, GBSP_ACC_COMPENSATED);
+    return GBSP_OK;
+}
+
+gbsp_status jds_split_impl(Mat &A, int32_t depth, int32_t chunk, void *ws, int64_t bytes, cudaStream_t s) {
+    if (depth <= 0 || depth >= A.n_diag) {
+        A.split_k = 0;
+        A.split_depth = 0;
+        return GBSP_OK;
+    }
+    std::vector<int4> t;
+    std::vector<int32_t> it;
+    int64_t parts = 0;
+    split_plan(A, depth, chunk, &t, &it, &parts);
+    int64_t need = 0;
+    jds_split_bytes_impl(A, depth, chunk, &need);
+    if (bytes < need) {
+        set_error("gbsp_jds_split: workspace needs %lld bytes", (long long)need);
+        return GBSP_ERR_NOMEM;
+    }
+    char *p = static_cast<char *>(ws);
+    int4 *dt = reinterpret_cast<int4 *>(p);
+    int32_t *di = reinterpret_cast<int32_t *>(p + 16 * t.size());
+    const int64_t po = ((16 * (int64_t)t.size() + 4 * (int64_t)it.size()) + 255) & ~int64_t(255);
+    GBSP_CUDA(cudaMemcpyAsync(dt, t.data(), 16 * t.size(), cudaMemcpyHostToDevice, s));
+    GBSP_CUDA(cudaMemcpyAsync(di, it.data(), 4 * it.size(), cudaMemcpyHostToDevice, s));
+    GBSP_CUDA(cudaStreamSynchronize(s));
+    A.split_depth = depth;
+    A.split_chunk = chunk;
+    A.split_k = (int32_t)t.size();
+    A.split_table = dt;
+    A.split_items = di;
+    A.split_items_total = it.back();
+    A.split_part = p + po;
     return GBSP_OK;
 }
 

@@ -291,6 +291,20 @@ class JDSMatrix(_Product):
         crs_val = _need_cuda(crs_val, "crs_val", self.dtype)
         L.check(L.load().gbsp_jds_values(self._h, _vp(crs_val), _stream(stream)), "gbsp_jds_values")
 
+    def split(self, depth: int = 64, chunk: int = 128, stream=None) -> None:
+        """Sum diagonals >= depth in chunks by a separate kernel (long rows
+        spread over many threads); depth=0 removes the split."""
+        lib = L.load()
+        if depth == 0:
+            L.check(lib.gbsp_jds_split(self._h, 0, 0, None, 0, _stream(stream)), "gbsp_jds_split")
+            self._split_ws = None
+            return
+        nb = ctypes.c_int64()
+        L.check(lib.gbsp_jds_split_bytes(self._h, depth, chunk, ctypes.byref(nb)), "gbsp_jds_split_bytes")
+        self._split_ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device=self._device)
+        L.check(lib.gbsp_jds_split(self._h, depth, chunk, _vp(self._split_ws), self._split_ws.numel(),
+                                   _stream(stream)), "gbsp_jds_split")
+
     def set_format(self, fmt: str, block: int = 0, unroll: int = 0) -> None:
         L.check(L.load().gbsp_jds_set_format(self._h, L.FORMATS[fmt], block, unroll),
                 "gbsp_jds_set_format")

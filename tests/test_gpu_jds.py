@@ -86,6 +86,28 @@ def test_sell_conversion_and_products(mi, perm):
             assert torch.equal(G2.spmv(dev(xp)), J.spmv(dev(xp)))
 
 
+@pytest.mark.parametrize("perm", ["symmetric", "row_only"])
+def test_deep_split(perm):
+    """Long rows split over chunk threads: same product within tolerance,
+    exact on integer data, for every walk that honours the split."""
+    A = S.zipf_rows(50_000, 57, lmax=5000)
+    x = S.vector(A.n_cols, 57)
+    ref, s = O.crs_spmv_exact(A, x)
+    M = crs(A)
+    J = M.to_jds("JDS", perm)
+    for depth, chunk in ((1, 1), (8, 32), (64, 128), (256, 64), (J.n_diag - 1, 7)):
+        J.split(depth, chunk)
+        for fmt, b, u, r in (("JDS", 0, 0, 1), ("NUJDS", 0, 2, 2), ("NUJDS", 0, 4, 1)):
+            set_variant(J, fmt, b, u, r)
+            assert_close64(host(J.spmv_original(dev(x))), ref, s, f"split {depth}/{chunk} {fmt} u{u} r{r}")
+    J.split(0)
+    Ai = S.integer_values(A, 58, 1000)
+    xi = S.int_vector(A.n_cols, 58, 1000)
+    Ji = crs(Ai).to_jds("NUJDS", perm, unroll=2)
+    Ji.split(32, 100)
+    assert np.array_equal(host(Ji.spmv_original(dev(xi))), O.crs_spmv(Ai, xi))
+
+
 def test_sell_spmm_and_integer():
     A = S.integer_values(S.hh_like(50_000, 53), 53, 512)
     X = np.stack([S.int_vector(A.n_cols, 60 + c, 512) for c in range(16)], axis=1)
