@@ -139,6 +139,23 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """Largest `value` over all ranks (the job's time is the slowest
+    replica's); the identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job rate: the units all ranks processed over the slowest time."""
+    return world * units_per_rank / (max_ms * 1e-3)
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0910_4836_gb300", "csrc")
@@ -276,14 +293,10 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(times), dev)
     ms = total_ms / args.steps
     flops = 2.0 * A.nnz
-    gflops = world * flops / (ms * 1e-3) / 1e9
+    gflops = job_throughput(flops, world, ms) / 1e9
     gbs = alg / (ms * 1e-3) / 1e9
     h = kernel_source_hash()
     traffic = NCU_TRAFFIC.get((args.config, kname, h))
