@@ -253,9 +253,16 @@ __global__ void __launch_bounds__(1024) sell_kernel(JdsArgs a) {
     const T *__restrict__ x = static_cast<const T *>(a.x);
     const int lane = threadIdx.x & 31;
     const int64_t nb = ceil_div_dev(a.n_rows, 32);
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t b = warp; b < nb; b += nwarp) {
+    const int wpc = blockDim.x >> 5;  // warps per CTA
+    const int wid = threadIdx.x >> 5;
+    // A CTA takes wpc consecutive blocks per iteration.  Blocks are sorted by
+    // length inside their window, so the warp's pick among them rotates from
+    // one iteration to the next: otherwise warp 0 would always get the
+    // longest rows and warp wpc-1 the shortest.
+    int64_t it = 0;
+    for (int64_t g = blockIdx.x; g * wpc < nb; g += gridDim.x, ++it) {
+        const int64_t b = g * wpc + (int64_t)((wid + it * 7) % wpc);
+        if (b >= nb) continue;
         const int64_t r = b * 32 + lane;
         const int32_t len = r < a.n_rows ? __ldg(a.rlen + r) : 0;
         const int32_t width = __shfl_sync(0xffffffffu, len, 0);  // lane 0 holds the longest row
@@ -263,21 +270,18 @@ __global__ void __launch_bounds__(1024) sell_kernel(JdsArgs a) {
         Acc<VM> acc[KT];
 #pragma unroll
         for (int q = 0; q < KT; ++q) acc[q].init();
+        // step 0 loads; each step then issues the next step's loads after
+        // forming its own products
+        int c[U];
+        T v[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const bool ok = len > j;
+            c[j] = ok ? ld_stream(a.col + off + lane) : -1;
+            v[j] = ok ? ld_stream(val + off + lane) : T(0);
+            off += __popc(__ballot_sync(0xffffffffu, len > j));
+        }
         for (int32_t d0 = 0; d0 < width; d0 += U) {
-            int64_t pos[U];
-#pragma unroll
-            for (int j = 0; j < U; ++j) {
-                pos[j] = off + lane;
-                off += __popc(__ballot_sync(0xffffffffu, len > d0 + j));
-            }
-            int c[U];
-            T v[U];
-#pragma unroll
-            for (int j = 0; j < U; ++j) {
-                const bool ok = len > d0 + j;
-                c[j] = ok ? ld_stream(a.col + pos[j]) : -1;
-                v[j] = ok ? ld_stream(val + pos[j]) : T(0);
-            }
 #pragma unroll
             for (int j = 0; j < U; ++j) {
                 if (c[j] < 0) continue;
@@ -285,6 +289,14 @@ __global__ void __launch_bounds__(1024) sell_kernel(JdsArgs a) {
 #pragma unroll
                 for (int q = 0; q < KT; ++q)
                     if (KT == 1 || a.c0 + q < a.k) acc[q].add(v[j], ld_vec(xr + q));
+            }
+            if (d0 + U >= width) break;
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const bool ok = len > d0 + U + j;
+                c[j] = ok ? ld_stream(a.col + off + lane) : -1;
+                v[j] = ok ? ld_stream(val + off + lane) : T(0);
+                off += __popc(__ballot_sync(0xffffffffu, len > d0 + U + j));
             }
         }
         if (r < a.n_rows) {
