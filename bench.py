@@ -203,15 +203,14 @@ def candidates(M, A, x, only=None):
         out.append((f"CRS vector l{l} r{r}", M, x, crs_b, ("vector", l, r)))
     for t in (1024, 2048):
         out.append((f"CRS tiled {t}", M, x, crs_b, ("tiled", t)))
-    for perm in ("row_only", "symmetric"):
-        for w in (256, 1024, 4096):
-            for u in (2, 4):
-                name = f"SELL {perm} w={w} u={u}"
-                if want(name):
-                    G = M.to_jds("SELL", perm, window=w, unroll=u)
-                    xs = G.permute(x) if perm == "symmetric" else x
-                    gb = 12 * A.nnz + 4 * (G.n_blocks + 1) + 4 * A.n_rows + 8 * A.n_cols + 8 * A.n_rows
-                    out.append((name, G, xs, gb, ("fixed",)))
+    for perm, w, u in (("row_only", 128, 2), ("row_only", 128, 4), ("row_only", 512, 4),
+                       ("row_only", 4096, 4), ("symmetric", 128, 4)):
+        name = f"SELL {perm} w={w} u={u}"
+        if want(name):
+            G = M.to_jds("SELL", perm, window=w, unroll=u)
+            xs = G.permute(x) if perm == "symmetric" else x
+            gb = 12 * A.nnz + 4 * (G.n_blocks + 1) + 4 * A.n_rows + 8 * A.n_cols + 8 * A.n_rows
+            out.append((name, G, xs, gb, ("fixed",)))
     for perm in ("symmetric", "row_only"):
         if only is not None and not any(f"{f} {perm}".startswith(only) or only.startswith(f"{f} {perm}")
                                         for f in ("JDS", "NUJDS", "NBJDS", "JDS_LITERAL", "RBJDS", "SOJDS")):
@@ -349,6 +348,8 @@ def run_ours(args):
             result["fwd_bwd"] = fwd_bwd_speedup(dev, time_launches)
             torch.cuda.empty_cache()
             result["zipf_rows"] = zipf_numbers(dev, time_launches, peak)
+            torch.cuda.empty_cache()
+            result["laplace_64x64"] = small_numbers(dev, time_launches)
         result["cpu_baseline"] = cpu_baseline(A, x_host, args.cpu_seconds)
     if world > 1:
         torch.distributed.barrier()
@@ -403,6 +404,36 @@ def fp32_numbers(M, A, x, y64, dev, time_launches, ms64):
             "max_err_over_sum_abs_compensated": float(((yc - ref).abs() / den).max()),
             "max_err_over_sum_abs_plain": float(((yp - ref).abs() / den).max()),
             "note": "error of FP32 data and FP32 vector against the FP64 product of the FP64 data"}
+
+
+def small_numbers(dev, time_launches):
+    """The 64x64 Laplacian (N=4096, fits in L2): latency-bound, so the figures
+    are microseconds per SpMVM, eager (one launch each) and as one replay of
+    a CUDA graph holding 100 SpMVMs."""
+    import torch
+    from paper_0910_4836_gb300 import CRSMatrix, synth as S
+    A = S.config(0)
+    M = CRSMatrix.from_host(A, device=dev)
+    x = torch.as_tensor(S.vector(A.n_cols, 0)).to(dev)
+    out = {"n_rows": A.n_rows, "nnz": A.nnz}
+    for name, H, xin in (("CRS vector", M, x), ("SELL row_only w=128 u=4", M.to_jds("SELL", "row_only", window=128, unroll=4), x),
+                         ("NUJDS row_only u=2", M.to_jds("NUJDS", "row_only", unroll=2), x)):
+        if name.startswith("CRS"):
+            H.autotune()
+        y = torch.empty(A.n_rows, dtype=torch.float64, device=dev)
+        eager = statistics.median(time_launches(lambda: H.spmv(xin, out=y), 200))
+        s = torch.cuda.Stream(dev)
+        s.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(s):
+            H.spmv(xin, out=y)
+        torch.cuda.current_stream(dev).wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(100):
+                H.spmv(xin, out=y)
+        replay = statistics.median(time_launches(g.replay, 20)) / 100
+        out[name] = {"eager_us": round(eager * 1e3, 2), "graph_us": round(replay * 1e3, 2)}
+    return out
 
 
 def zipf_numbers(dev, time_launches, peak):

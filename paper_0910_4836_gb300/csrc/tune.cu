@@ -93,7 +93,13 @@ static std::vector<Cand> candidates(const Mat &A, int k) {
             }
         }
     } else if (A.built_block > 0) {
-        if (k == 1) {
+        if (k == 1 && A.format == GBSP_SELL) {
+            for (int u : {1, 2, 4}) {
+                Cand c = base;
+                c.unroll = u;
+                out.push_back(c);
+            }
+        } else if (k == 1) {
             out.push_back(base);
         } else {
             for (int t : {4, 8, 16}) {
