@@ -13,7 +13,10 @@ rational sums, identity / diagonal / integer inputs, Laplacian closed forms,
 the JDS special cases the paper states (NUJDS with u = N_j is CRS in the
 permuted basis; RBJDS with block 1 is row-by-row access; JDS is NBJDS with
 block = N), a hand-worked JDS example, the adjoint identity and finite
-differences.  SOJDS: parity unpinned (the paper fixes no sorting rule), only
+differences; the basic gather sums of Sect. 3.1 against closed forms
+(dense and constant-stride sums of integers), exact rational sums and
+math.fsum, with the IR index law checked against the paper's per-position
+draw.  SOJDS: parity unpinned (the paper fixes no sorting rule), only
 invariants and a closed-form banded case.
 """
 from __future__ import annotations
@@ -60,13 +63,16 @@ def lib():
             "orc_sell_build": [_I64, _I64, _I32, _I32, _F64, _INT, _I64, _I32, _I32, _I32, _I32, _I32,
                                _F64],
             "orc_sell_spmv": [_I64, _I32, _I32, _I32, _F64, _F64, _F64],
+            "orc_gather_sum": [_INT, _INT, _I64, _I64, _F64, _F64, _I32],
+            "orc_gather_sum_exact": [_INT, _INT, _I64, _I64, _F64, _F64, _I32, _F64],
             "orc_num_threads": [],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = _I64 if name in ("orc_max_row_len", "orc_jds_build") else (
-                _INT if name in ("orc_num_threads", "orc_sell_build") else None)
+                _INT if name in ("orc_num_threads", "orc_sell_build") else (
+                    ctypes.c_double if name == "orc_gather_sum" else None))
         _lib = L
     return _lib
 
@@ -304,3 +310,46 @@ def power_loss_grad(A, x, m):
         dv = dval(A, g, xs[t - 1], dv, accumulate=True)
         g = crs_spmv_t(A, g)
     return L, dv, g
+
+
+# ---------------------------------------------------------------------------
+# Basic sparse vector operations (Sect. 3.1): ADD / SCP over PD, CS, IS / IR
+# ---------------------------------------------------------------------------
+
+GATHER_OPS = {"ADD": 0, "SCP": 1}
+GATHER_ACCESS = {"PD": 0, "CS": 1, "IND": 2}
+
+
+def gather_sum(op: str, access: str, n: int, b, a=None, k: int = 1, ind=None) -> float:
+    """s = sum_i B(idx(i)) (ADD) or sum_i A(i) B(idx(i)) (SCP) in loop order,
+    idx(i) = i (PD), k*i (CS) or ind(i) (IND)."""
+    a_, b_, ind_ = _gather_inputs(op, access, n, b, a, k, ind)
+    return float(lib().orc_gather_sum(GATHER_OPS[op], GATHER_ACCESS[access], n, k, a_, b_, ind_))
+
+
+def gather_sum_exact(op: str, access: str, n: int, b, a=None, k: int = 1, ind=None):
+    """(accurate sum, sum of |term|) for the same loop."""
+    a_, b_, ind_ = _gather_inputs(op, access, n, b, a, k, ind)
+    out = np.zeros(2)
+    lib().orc_gather_sum_exact(GATHER_OPS[op], GATHER_ACCESS[access], n, k, a_, b_, ind_, out)
+    return float(out[0]), float(out[1])
+
+
+def _gather_inputs(op, access, n, b, a, k, ind):
+    b_ = _f64(b)
+    if op == "SCP":
+        a_ = _f64(a)
+        if len(a_) < n:
+            raise ValueError("gather: A shorter than n")
+    else:
+        a_ = np.zeros(1)
+    if access == "IND":
+        ind_ = _i32(ind)
+        if len(ind_) < n or (n and (ind_[:n].min() < 0 or ind_[:n].max() >= len(b_))):
+            raise ValueError("gather: ind out of range")
+    else:
+        ind_ = np.zeros(1, dtype=np.int32)
+        last = (n - 1) * (k if access == "CS" else 1)
+        if n and last >= len(b_):
+            raise ValueError("gather: B shorter than the strided range")
+    return a_, b_, ind_

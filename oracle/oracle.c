@@ -500,3 +500,46 @@ void orc_sell_spmv(int64_t n_rows, const int32_t *rlen, const int32_t *blk_ptr,
                 resvec[r] = resvec[r] + val_s[pos] * invec[col_s[pos]];
     }
 }
+
+/* ------------------------------------------------------------------------
+ * Basic sparse vector operations (Sect. 3.1, the table of ADD and SCP
+ * kernels): one running sum over i < n of
+ *     ADD:  s = s + B(idx(i))          SCP:  s = s + A(i) * B(idx(i))
+ * with idx(i) = i (PD, packed dense), k*i (CS, constant stride computed in
+ * the loop) or ind(i) (IS / IR, indirect: the two differ only in how ind
+ * was generated).  op: 0 = ADD, 1 = SCP.  access: 0 = PD, 1 = CS, 2 = IND.
+ * ---------------------------------------------------------------------- */
+static inline int64_t gather_index(int access, int64_t i, int64_t k, const int32_t *ind)
+{
+    return access == 0 ? i : (access == 1 ? k * i : (int64_t)ind[i]);
+}
+
+double orc_gather_sum(int op, int access, int64_t n, int64_t k, const double *a,
+                      const double *b, const int32_t *ind)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double bj = b[gather_index(access, i, k, ind)];
+        s = op == 0 ? s + bj : s + a[i] * bj;
+    }
+    return s;
+}
+
+/* The same sum, accurately (Dot2: exact product split and TwoSum, as in
+ * orc_crs_spmv_exact).  out[0] = the sum, out[1] = sum of |term|. */
+void orc_gather_sum_exact(int op, int access, int64_t n, int64_t k, const double *a,
+                          const double *b, const int32_t *ind, double *out)
+{
+    double s = 0.0, c = 0.0, abs_sum = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double bj = b[gather_index(access, i, k, ind)];
+        double p = op == 0 ? bj : a[i] * bj;
+        double e = op == 0 ? 0.0 : fma(a[i], bj, -p);
+        double err;
+        two_sum(s, p, &s, &err);
+        c = c + (err + e);
+        abs_sum = abs_sum + fabs(p);
+    }
+    out[0] = s + c;
+    out[1] = abs_sum;
+}

@@ -161,6 +161,53 @@ def int_vector(n: int, seed: int, bound: int, stream: int = 103) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
+# Index arrays for the basic gather operations (Sect. 3.1: dense, constant
+# stride, indirect with constant or random stride)
+# --------------------------------------------------------------------------
+
+def stride_indices(n: int, k: int) -> np.ndarray:
+    """ind(i) = k*i for i < n (the IS case), int32."""
+    if n > 0 and k * (n - 1) >= 2 ** 31:
+        raise ValueError("stride_indices: k*(n-1) exceeds int32")
+    return (np.arange(n, dtype=np.int64) * k).astype(np.int32)
+
+
+def bernoulli_indices(length: int, p: float, seed: int, stream: int = 211) -> np.ndarray:
+    """The IR index array as Sect. 3.1 draws it: every position j < length
+    of the gathered vector is taken when a uniform draw is below p = 1/k."""
+    j = np.arange(length, dtype=np.int64)
+    return j[uniform01(seed, stream, j) < p].astype(np.int32)
+
+
+def geometric_indices(n: int, p: float, seed: int, stream: int = 213) -> np.ndarray:
+    """n indices with the gap law of ``bernoulli_indices`` (gaps Geometric(p)
+    on {1, 2, ...}: mean 1/p, variance (1-p)/p^2), drawn gap by gap by
+    inversion, so that long index arrays need no draw per skipped position.
+    The first index is the first gap minus one."""
+    if p >= 1.0:
+        gaps = np.ones(n, dtype=np.int64)
+    else:
+        u = 1.0 - uniform01(seed, stream, np.arange(n))      # (0, 1]
+        gaps = 1 + np.floor(np.log(u) / np.log1p(-p)).astype(np.int64)
+    ind = np.cumsum(gaps) - 1
+    if n > 0 and ind[-1] >= 2 ** 31:
+        raise ValueError("geometric_indices: indices exceed int32")
+    return ind.astype(np.int32)
+
+
+def gaussian_indices(n: int, mean: float, var: float, length: int, seed: int,
+                     stream: int = 217) -> np.ndarray:
+    """Indices whose strides are normal(mean, var) rounded to integers, so
+    that backward jumps occur once the variance is large enough (the
+    mean/variance plane of Sect. 3.1).  ind(0) = 0 and every step wraps
+    modulo `length`, which keeps the walk inside the vector."""
+    z = normal(seed, stream, np.arange(1, n))
+    steps = np.rint(mean + np.sqrt(var) * z).astype(np.int64)
+    ind = np.concatenate([[0], np.cumsum(steps)]) % length
+    return ind.astype(np.int32)
+
+
+# --------------------------------------------------------------------------
 # Workload recipes
 # --------------------------------------------------------------------------
 

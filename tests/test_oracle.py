@@ -493,3 +493,96 @@ def test_generator_shapes():
         mask = np.ones(len(d), bool)
         mask[starts[(starts > 0) & (starts <= len(d))] - 1] = False
         assert np.all(d[mask] > 0)
+
+
+# --------------------------------------------------------------------------
+# Basic sparse vector operations (Sect. 3.1 table: ADD / SCP over PD, CS,
+# IS, IR)
+# --------------------------------------------------------------------------
+
+def test_gather_dense_add_closed_form():
+    n = 100_000
+    b = np.arange(1, n + 1, dtype=np.float64)
+    assert O.gather_sum("ADD", "PD", n, b) == n * (n + 1) // 2
+    assert O.gather_sum_exact("ADD", "PD", n, b) == (n * (n + 1) // 2, n * (n + 1) // 2)
+
+
+@pytest.mark.parametrize("k", [1, 8, 530])
+def test_gather_constant_stride_closed_forms(k):
+    """B(j) = j, A(i) = i + 1: ADD gives k n(n-1)/2, SCP gives
+    k (sum i^2 + sum i) = k (n-1) n (2n-1)/6 + k n(n-1)/2 -- integers below
+    2^53, so exact in every order."""
+    n = 3000
+    b = np.arange(k * (n - 1) + 1, dtype=np.float64)
+    a = np.arange(1, n + 1, dtype=np.float64)
+    add = k * n * (n - 1) // 2
+    scp = k * (n - 1) * n * (2 * n - 1) // 6 + add
+    assert O.gather_sum("ADD", "CS", n, b, k=k) == add
+    assert O.gather_sum("SCP", "CS", n, b, a=a, k=k) == scp
+    # IS: the same loop through an index array ind(i) = k i
+    ind = S.stride_indices(n, k)
+    assert O.gather_sum("ADD", "IND", n, b, ind=ind) == add
+    assert O.gather_sum("SCP", "IND", n, b, a=a, ind=ind) == scp
+
+
+def test_gather_scp_with_unit_a_is_add():
+    n = 5000
+    b = S.vector(4 * n, 7)
+    ind = S.geometric_indices(n, 0.25, 7)
+    ind = ind[ind < len(b)]
+    m = len(ind)
+    ones = np.ones(m)
+    assert O.gather_sum("SCP", "IND", m, b, a=ones, ind=ind) == O.gather_sum("ADD", "IND", m, b, ind=ind)
+
+
+def test_gather_exact_against_rationals():
+    """Random A, B, IR indices: the accurate sum is within one rounding of
+    the exact rational sum; the loop-order sum within n u sum|t|."""
+    n = 600
+    b = S.vector(5000, 11)
+    a = S.vector(n, 12)
+    ind = S.bernoulli_indices(5000, 0.15, 13)[:n]
+    n = len(ind)
+    exact = sum(Fraction(float(a[i])) * Fraction(float(b[ind[i]])) for i in range(n))
+    s, abs_sum = O.gather_sum_exact("SCP", "IND", n, b, a=a, ind=ind)
+    assert abs(Fraction(s) - exact) <= Fraction(2.0 ** -52) * abs(exact) + Fraction(2.0 ** -100) * Fraction(abs_sum)
+    assert math.isclose(abs_sum, float(sum(abs(Fraction(float(a[i])) * Fraction(float(b[ind[i]])))
+                                           for i in range(n))), rel_tol=1e-12)
+    plain = O.gather_sum("SCP", "IND", n, b, a=a, ind=ind)
+    assert abs(Fraction(plain) - exact) <= Fraction(n * 2.0 ** -53) * Fraction(abs_sum)
+    # the ADD sum against math.fsum (correctly rounded)
+    add_s, _ = O.gather_sum_exact("ADD", "IND", n, b, ind=ind)
+    assert add_s == math.fsum(b[ind[:n]])
+
+
+def test_bernoulli_indices_p1_is_dense():
+    assert np.array_equal(S.bernoulli_indices(1000, 1.0, 3), np.arange(1000, dtype=np.int32))
+    b = S.vector(1000, 3)
+    assert O.gather_sum("ADD", "IND", 1000, b, ind=S.bernoulli_indices(1000, 1.0, 3)) == \
+        O.gather_sum("ADD", "PD", 1000, b)
+
+
+@pytest.mark.parametrize("k", [2, 8, 64])
+def test_geometric_indices_follow_the_bernoulli_gap_law(k):
+    """The IR arrays drawn gap by gap have the gap law of the paper's
+    per-position draw: mean k, variance k(k-1), P(gap = 1) = 1/k."""
+    p = 1.0 / k
+    n = 200_000
+    g = np.diff(np.concatenate([[-1], S.geometric_indices(n, p, 21).astype(np.int64)]))
+    gb = np.diff(np.concatenate([[-1], S.bernoulli_indices(n * k, p, 22).astype(np.int64)]))
+    for gaps in (g, gb):
+        assert gaps.min() >= 1
+        assert abs(gaps.mean() - k) < 0.02 * k
+        assert abs(gaps.var() - k * (k - 1)) < 0.05 * k * k + 0.02
+        assert abs(np.mean(gaps == 1) - p) < 0.01
+
+
+def test_gaussian_indices_zero_variance_is_constant_stride():
+    n, m = 10_000, 7
+    ind = S.gaussian_indices(n, m, 0.0, 10 ** 6, 5)
+    assert np.array_equal(ind, (np.arange(n, dtype=np.int64) * m % 10 ** 6).astype(np.int32))
+    ind = S.gaussian_indices(n, 4.0, 400.0, 10 ** 6, 5)
+    L = 10 ** 6
+    steps = (np.diff(ind.astype(np.int64)) + L // 2) % L - L // 2  # undo the wrap
+    assert (steps < 0).mean() > 0.3  # backward jumps appear at large variance
+    assert abs(steps.mean() - 4.0) < 0.5 and abs(steps.var() - 400.0) < 20.0
