@@ -33,6 +33,7 @@ _lib = None
 _I32 = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _F64 = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _F32 = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
+_I64P = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
 _I64 = ctypes.c_int64
 _INT = ctypes.c_int
 
@@ -65,6 +66,10 @@ def lib():
             "orc_sell_spmv": [_I64, _I32, _I32, _I32, _F64, _F64, _F64],
             "orc_gather_sum": [_INT, _INT, _I64, _I64, _F64, _F64, _I32],
             "orc_gather_sum_exact": [_INT, _INT, _I64, _I64, _F64, _F64, _I32, _F64],
+            "orc_stride_hist": [_I64, _I32, _I64P],
+            "orc_warp_sectors_crs": [_I64, _I32, _I32, _INT, _INT, _I64P],
+            "orc_warp_sectors_jds": [_I64, _I64, _I32, _I32, _INT, _I64P],
+            "orc_warp_sectors_sell": [_I64, _I32, _I32, _I32, _INT, _I64P],
             "orc_num_threads": [],
         }
         for name, args in sig.items():
@@ -353,3 +358,36 @@ def _gather_inputs(op, access, n, b, a, k, ind):
         if n and last >= len(b_):
             raise ValueError("gather: B shorter than the strided range")
     return a_, b_, ind_
+
+
+# ---------------------------------------------------------------------------
+# Stride distribution (Sect. 4, Fig. 4a) and sectors per warp-wide gather
+# ---------------------------------------------------------------------------
+
+def stride_hist(col):
+    """(forward[33], backward[33]) counts of the jumps col[i+1] - col[i] in
+    storage order; bin 0 = no jump, bin b = 2^(b-1) <= |jump| < 2^b."""
+    c = _i32(col)
+    h = np.zeros(66, dtype=np.int64)
+    lib().orc_stride_hist(len(c), c, h)
+    return h[:33], h[33:]
+
+
+def warp_sectors_crs(A, lanes, elem_bytes=8):
+    """hist[c] = warp accesses touching c distinct 32-byte sectors of x, for
+    the CRS kernel with `lanes` lanes per row."""
+    h = np.zeros(33, dtype=np.int64)
+    lib().orc_warp_sectors_crs(A.n_rows, _i32(A.row_ptr), _i32(A.col), lanes, elem_bytes, h)
+    return h
+
+
+def warp_sectors_jds(J, elem_bytes=8):
+    h = np.zeros(33, dtype=np.int64)
+    lib().orc_warp_sectors_jds(J.n_rows, J.n_diag, _i32(J.jd_ptr), _i32(J.col), elem_bytes, h)
+    return h
+
+
+def warp_sectors_sell(S_, elem_bytes=8):
+    h = np.zeros(33, dtype=np.int64)
+    lib().orc_warp_sectors_sell(S_.n_rows, _i32(S_.rlen), _i32(S_.blk_ptr), _i32(S_.col), elem_bytes, h)
+    return h

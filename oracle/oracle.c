@@ -543,3 +543,110 @@ void orc_gather_sum_exact(int op, int access, int64_t n, int64_t k, const double
     out[0] = s + c;
     out[1] = abs_sum;
 }
+
+/* ------------------------------------------------------------------------
+ * Stride distribution of the invec accesses (Sect. 4, Fig. 4a): walking a
+ * column-index array in storage order -- the order in which the paper's
+ * serial CRS, JDS, RBJDS and SOJDS loops read invec -- every jump
+ * s = col[i+1] - col[i] is counted once.  Bins by size: bin 0 holds s = 0,
+ * bin b >= 1 holds 2^(b-1) <= |s| < 2^b (for 8-byte elements: strides of
+ * 8*2^(b-1) to 8*2^b - 1 bytes).  hist[0..32] counts forward jumps (s >= 0),
+ * hist[33..65] backward jumps (s < 0; bin 0 stays empty).
+ * ---------------------------------------------------------------------- */
+static int stride_bin(int64_t s)
+{
+    uint64_t a = (uint64_t)(s < 0 ? -s : s);
+    int b = 0;
+    while (a) {
+        ++b;
+        a >>= 1;
+    }
+    return b;
+}
+
+void orc_stride_hist(int64_t nnz, const int32_t *col, int64_t *hist)
+{
+    for (int i = 0; i < 66; ++i) hist[i] = 0;
+    for (int64_t i = 0; i + 1 < nnz; ++i) {
+        int64_t s = (int64_t)col[i + 1] - (int64_t)col[i];
+        hist[(s < 0 ? 33 : 0) + stride_bin(s)] += 1;
+    }
+}
+
+/* Distinct 32-byte sectors of invec touched by one warp-wide gather: the
+ * columns cols[0..m) of the active lanes, elem_bytes per entry. */
+static int64_t distinct_sectors(const int64_t *cols, int m, int elem_bytes)
+{
+    int64_t seen[32];
+    int n = 0;
+    for (int l = 0; l < m; ++l) {
+        int64_t sec = cols[l] * elem_bytes / 32;
+        int dup = 0;
+        for (int q = 0; q < n; ++q) dup |= seen[q] == sec;
+        if (!dup) seen[n++] = sec;
+    }
+    return n;
+}
+
+/* Sectors per warp-wide gather, histogram hist[0..32] (hist[c] = number of
+ * warp accesses touching c distinct sectors), for the warp access patterns
+ * of the GPU kernels:
+ *   CRS, `lanes` lanes per row: a warp holds 32/lanes consecutive rows; at
+ *     step t lane l of row group g reads entry row_ptr[r] + t*lanes + l.
+ *   JDS storage, thread per permuted row: a warp holds 32 consecutive rows;
+ *     for diagonal d it reads jd_ptr[d] + r for its rows r < diagLen(d).
+ *   SELL-32: a warp holds one 32-row block; slot d is read by the rows
+ *     with rlen > d, from consecutive storage. */
+void orc_warp_sectors_crs(int64_t n_rows, const int32_t *row_ptr, const int32_t *col, int lanes,
+                          int elem_bytes, int64_t *hist)
+{
+    int groups = 32 / lanes;
+    for (int i = 0; i < 33; ++i) hist[i] = 0;
+    for (int64_t r0 = 0; r0 < n_rows; r0 += groups) {
+        int64_t maxlen = 0;
+        for (int g = 0; g < groups && r0 + g < n_rows; ++g) {
+            int64_t len = row_ptr[r0 + g + 1] - row_ptr[r0 + g];
+            if (len > maxlen) maxlen = len;
+        }
+        for (int64_t t = 0; t * lanes < maxlen; ++t) {
+            int64_t cols[32];
+            int m = 0;
+            for (int g = 0; g < groups && r0 + g < n_rows; ++g)
+                for (int l = 0; l < lanes; ++l) {
+                    int64_t e = (int64_t)row_ptr[r0 + g] + t * lanes + l;
+                    if (e < row_ptr[r0 + g + 1]) cols[m++] = col[e];
+                }
+            if (m) hist[distinct_sectors(cols, m, elem_bytes)] += 1;
+        }
+    }
+}
+
+void orc_warp_sectors_jds(int64_t n_rows, int64_t n_diag, const int32_t *jd_ptr, const int32_t *col,
+                          int elem_bytes, int64_t *hist)
+{
+    for (int i = 0; i < 33; ++i) hist[i] = 0;
+    for (int64_t r0 = 0; r0 < n_rows; r0 += 32)
+        for (int64_t d = 0; d < n_diag && DIAGLEN(jd_ptr, d) > r0; ++d) {
+            int64_t cols[32];
+            int m = 0;
+            for (int64_t r = r0; r < r0 + 32 && r < DIAGLEN(jd_ptr, d); ++r) cols[m++] = col[jd_ptr[d] + r];
+            hist[distinct_sectors(cols, m, elem_bytes)] += 1;
+        }
+}
+
+void orc_warp_sectors_sell(int64_t n_rows, const int32_t *rlen, const int32_t *blk_ptr, const int32_t *col,
+                           int elem_bytes, int64_t *hist)
+{
+    for (int i = 0; i < 33; ++i) hist[i] = 0;
+    int64_t nb = (n_rows + 31) / 32;
+    for (int64_t b = 0; b < nb; ++b) {
+        int64_t b0 = 32 * b, b1 = b0 + 32 < n_rows ? b0 + 32 : n_rows;
+        int64_t pos = blk_ptr[b];
+        for (int64_t d = 0; d < rlen[b0]; ++d) {
+            int64_t cols[32];
+            int m = 0;
+            for (int64_t r = b0; r < b1 && rlen[r] > d; ++r, ++pos) cols[m++] = col[pos];
+            hist[distinct_sectors(cols, m, elem_bytes)] += 1;
+        }
+    }
+}

@@ -586,3 +586,91 @@ def test_gaussian_indices_zero_variance_is_constant_stride():
     steps = (np.diff(ind.astype(np.int64)) + L // 2) % L - L // 2  # undo the wrap
     assert (steps < 0).mean() > 0.3  # backward jumps appear at large variance
     assert abs(steps.mean() - 4.0) < 0.5 and abs(steps.var() - 400.0) < 20.0
+
+
+# --------------------------------------------------------------------------
+# Stride distribution (Sect. 4, Fig. 4a) and sectors per warp-wide gather
+# --------------------------------------------------------------------------
+
+def tridiagonal(n):
+    rows, cols = [], []
+    for i in range(n):
+        for j in (i - 1, i, i + 1):
+            if 0 <= j < n:
+                rows.append(i)
+                cols.append(j)
+    return S.from_coo(n, n, rows, cols, np.ones(len(rows)))
+
+
+def test_stride_hist_tridiagonal_closed_form():
+    """CRS of a tridiagonal matrix read row by row: every jump inside a row
+    is +1 (2n-2 of them) and every row change jumps back by 1 (n-1)."""
+    n = 1000
+    fwd, bwd = O.stride_hist(tridiagonal(n).col)
+    assert fwd[1] == 2 * n - 2 and fwd.sum() == 2 * n - 2
+    assert bwd[1] == n - 1 and bwd.sum() == n - 1
+
+
+def test_stride_hist_power_of_two_bins():
+    col = np.array([2 ** b - 1 for b in range(31)], dtype=np.int32)  # jumps 1, 2, 4, ..., 2^29
+    fwd, bwd = O.stride_hist(col)
+    assert list(fwd) == [0] + [1] * 30 + [0, 0] and bwd.sum() == 0
+    fwd, bwd = O.stride_hist(col[::-1].copy())
+    assert list(bwd) == [0] + [1] * 30 + [0, 0] and fwd.sum() == 0
+    fwd, bwd = O.stride_hist(np.array([5, 5, 5, 4, 7], dtype=np.int32))  # 0, 0, -1, +3
+    assert fwd[0] == 2 and fwd[2] == 1 and bwd[1] == 1 and fwd.sum() + bwd.sum() == 4
+    # extremes of int32: one jump of 2^31 - 1 and one of -(2^31 - 1)
+    fwd, bwd = O.stride_hist(np.array([0, 2 ** 31 - 1, 0], dtype=np.int32))
+    assert fwd[31] == 1 and bwd[31] == 1
+
+
+def test_warp_sectors_identity_closed_form():
+    """A warp reading 32 consecutive aligned FP64 entries touches 256 bytes,
+    i.e. 8 sectors (4 for FP32), in CRS with one lane per row, JDS and SELL."""
+    n = 32 * 50
+    A = S.from_coo(n, n, np.arange(n), np.arange(n), np.ones(n))
+    for h in (O.warp_sectors_crs(A, 1), O.warp_sectors_jds(O.jds_build(A, True)),
+              O.warp_sectors_sell(O.sell_build(A, 64, True))):
+        assert h[8] == n // 32 and h.sum() == n // 32
+    assert O.warp_sectors_crs(A, 1, elem_bytes=4)[4] == n // 32
+
+
+def test_warp_sectors_crs_lanes_closed_forms():
+    """Rows of 64 consecutive columns starting at multiples of 64: with 32
+    lanes a row is read in two accesses of 8 sectors; with 8 lanes a warp
+    reads 4 rows x 8 consecutive columns = 4 x 2 sectors per access.  Rows
+    whose columns are 1000 apart: every lane its own sector."""
+    n_rows = 40
+    rows = np.repeat(np.arange(n_rows), 64)
+    cols = (np.arange(n_rows)[:, None] * 64 + np.arange(64)[None, :]).ravel()
+    A = S.from_coo(n_rows, 64 * n_rows, rows, cols, np.ones(len(rows)))
+    h32 = O.warp_sectors_crs(A, 32)
+    assert h32[8] == 2 * n_rows and h32.sum() == 2 * n_rows
+    h8 = O.warp_sectors_crs(A, 8)
+    assert h8[8] == (n_rows // 4) * 8 and h8.sum() == (n_rows // 4) * 8
+    cols = (np.arange(n_rows)[:, None] * 32000 + np.arange(32)[None, :] * 1000).ravel()
+    B = S.from_coo(n_rows, 32000 * n_rows, np.repeat(np.arange(n_rows), 32), cols, np.ones(32 * n_rows))
+    h = O.warp_sectors_crs(B, 32)
+    assert h[32] == n_rows and h.sum() == n_rows
+
+
+def test_warp_sectors_sell_one_window_is_jds():
+    """With one window SELL-32 reads, per 32-row block and slot, exactly the
+    rows and columns the thread-per-row JDS walk reads per warp and
+    diagonal (two loops over two different layouts)."""
+    A = S.small_random(700, 700, 5, density=0.02)
+    for sym in (True, False):
+        hj = O.warp_sectors_jds(O.jds_build(A, sym))
+        hs = O.warp_sectors_sell(O.sell_build(A, 704, sym))
+        assert np.array_equal(hj, hs)
+        assert hj.sum() > 0
+
+
+def test_warp_sectors_crs_one_lane_equal_rows_is_jds():
+    """Rows of equal length keep their order under the stable JDS sort, so
+    the row-only JDS warp walk and CRS with one lane per row coincide."""
+    n = 64 * 5
+    rows = np.repeat(np.arange(n), 3)
+    cols = ((np.arange(n)[:, None] + np.array([0, 97, 1003])[None, :]) % n).ravel()
+    A = S.from_coo(n, n, rows, cols, np.ones(3 * n))
+    assert np.array_equal(O.warp_sectors_crs(A, 1), O.warp_sectors_jds(O.jds_build(A, False)))
