@@ -47,6 +47,12 @@ def parse():
     p.add_argument("--ncu-case", action="store_true",
                    help="no timing: run 3 launches of the --kernel candidate on a 2,000,000-row "
                         "HH-like matrix (larger than L2, small enough for an ncu capture)")
+    p.add_argument("--micro", action="store_true",
+                   help="instead of the SpMVM step: the basic gather operations of Sect. 3.1 "
+                        "(ADD/SCP over PD, CS, IS, IR; stride sweep; Gaussian stride plane), one JSON line")
+    p.add_argument("--analysis", action="store_true",
+                   help="instead of the SpMVM step: stride distribution and sectors per warp gather of "
+                        "every storage scheme, and block / lanes / window sweeps (Sect. 4), one JSON line")
     return p.parse_args()
 
 
@@ -616,6 +622,156 @@ def run_reference(args):
             "e2e": {"value": val, "unit": "GFlop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_micro(args):
+    """The basic sparse vector operations of Sect. 3.1 on the device: the
+    table of ADD / SCP over packed dense (PD), constant stride (CS) and
+    indirect (IS: ind(i) = k i; IR: random strides of mean k, as the paper
+    draws them) access at the paper's strides 1, 8 and 530; the IS / IR
+    stride sweep; and IR with Gaussian strides over a mean/variance plane.
+    Each point: median of 7 launches, L2 flushed (a 512 MB write) before
+    each, CUDA events around the launch only."""
+    import torch
+    from paper_0910_4836_gb300 import build, synth as S
+    from paper_0910_4836_gb300.gather import GatherSum
+    build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 2 ** 20, dtype=torch.float64, device=dev)
+    i32max = 2 ** 31 - 1
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(11)
+    B = torch.rand(i32max + 1, dtype=torch.float64, device=dev, generator=gen)
+    A = torch.rand(2 ** 26, dtype=torch.float64, device=dev, generator=gen)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(g):
+        t = []
+        for _ in range(7):
+            flush.fill_(1.0)
+            e0.record(stream)
+            g()
+            e1.record(stream)
+            e1.synchronize()
+            t.append(e0.elapsed_time(e1))
+        return statistics.median(t)
+
+    def point(op, access, n, k=1, ind=None):
+        ind_d = None if ind is None else torch.as_tensor(ind).to(dev)
+        g = GatherSum(op, access, n, B, a=A[:n] if op == "SCP" else None, k=k, ind=ind_d)
+        ms = timed(g)
+        useful = n * (8 + (8 if op == "SCP" else 0) + (4 if access == "IND" else 0))
+        res = {"n": n, "us": round(ms * 1e3, 2), "gups": round(n / (ms * 1e-3) / 1e9, 2),
+               "useful_gbs": round(useful / (ms * 1e-3) / 1e9, 1)}
+        return res
+
+    def n_for(k, cap=2 ** 26):
+        return int(min(cap, 0.9 * i32max / k))
+
+    table = {}
+    for op in ("ADD", "SCP"):
+        table[f"PD{op}"] = point(op, "PD", 2 ** 26)
+        for k in (8, 530):
+            n = n_for(k)
+            table[f"CS{op} k={k}"] = point(op, "CS", n, k=k)
+            table[f"IS{op} k={k}"] = point(op, "IND", n, ind=S.stride_indices(n, k))
+        for k in (1, 8, 530):
+            n = n_for(k)
+            table[f"IR{op} k={k}"] = point(op, "IND", n, ind=S.geometric_indices(n, 1.0 / k, 100 + k))
+    sweep = {}
+    for k in (1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 530, 1024):
+        n = n_for(k, 2 ** 25)
+        sweep[str(k)] = {"ISSCP": point("SCP", "IND", n, ind=S.stride_indices(n, k)),
+                         "IRSCP": point("SCP", "IND", n, ind=S.geometric_indices(n, 1.0 / k, 200 + k))}
+    plane = {}
+    n = 2 ** 23
+    for mean in (1, 4, 16, 64, 256):
+        length = min(n * mean, i32max)
+        for var in (0, 1, 16, 256, 4096, 65536):
+            ind = S.gaussian_indices(n, float(mean), float(var), length, 300 + mean)
+            plane[f"mean={mean} var={var}"] = point("SCP", "IND", n, ind=ind)
+    return {"metric": "basic gather operations (Sect. 3.1): G element updates/s", "unit": "G updates/s",
+            "dtype": "f64", "data": "synthetic (torch.rand values; SplitMix64 index arrays)",
+            "l2": "flushed before every launch", "table": table, "stride_sweep": sweep,
+            "gaussian_plane": plane}
+
+
+def run_analysis(args):
+    """Sect. 4's analysis of the storage schemes on the bench workload: the
+    stride distribution of the x accesses in storage order (Fig. 4a: CRS,
+    JDS, RBJDS with block 1 and 1024, SOJDS 1024, plus SELL-32-sigma), the
+    sectors per warp-wide gather of the GPU kernels, and the block-size
+    sweep of NBJDS / RBJDS / SOJDS (Fig. 5) with the GPU's own knobs (CRS
+    lanes x rows per warp, NUJDS unroll x rows, SELL window x unroll)."""
+    import torch
+    from paper_0910_4836_gb300 import CRSMatrix, build
+    from paper_0910_4836_gb300.analysis import mean_sectors, stride_hist, summary, warp_sectors
+    build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    time_launches = _timer(dev)
+    A, x_host = make_workload(args.config)
+    M = CRSMatrix.from_host(A, device=dev)
+    x = torch.as_tensor(x_host).to(dev)
+    y = torch.empty(A.n_rows, dtype=torch.float64, device=dev)
+    out = {"workload": WORKLOAD, "n_rows": A.n_rows, "nnz": A.nnz, "stride_dist": {}, "warp_sectors": {},
+           "sweep": {}}
+
+    def strides(name, col):
+        f, b = stride_hist(col)
+        out["stride_dist"][name] = {"forward": f.tolist(), "backward": b.tolist(), **summary(f, b)}
+
+    def sectors(name, H, lanes=32):
+        h = warp_sectors(H, lanes)
+        out["warp_sectors"][name] = {"mean": round(mean_sectors(h), 3), "hist": h.tolist()}
+
+    def timed(name, H, xin, configure_fn=None):
+        if configure_fn:
+            configure_fn()
+        t = statistics.median(time_launches(lambda: H.spmv(xin, out=y), 10))
+        out["sweep"][name] = {"us": round(t * 1e3, 1), "gflops": round(2.0 * A.nnz / (t * 1e-3) / 1e9, 1)}
+
+    strides("CRS", M.col)
+    for l, r in ((1, 1), (2, 2), (4, 4), (8, 2), (16, 2), (32, 1)):
+        if r == 1 or l in (2, 4):
+            sectors(f"CRS lanes={l}", M, l)
+        timed(f"CRS vector l{l} r{r}", M, x, lambda l=l, r=r: M.set_kernel("vector", lanes=l, rows_per_warp=r))
+    for perm in ("symmetric", "row_only"):
+        J = M.to_jds("JDS", perm)
+        xp = J.permute(x) if perm == "symmetric" else x
+        strides(f"JDS {perm}", J.col)
+        sectors(f"JDS {perm}", J)
+        for u, r in ((1, 1), (2, 1), (4, 1), (8, 1), (2, 2), (4, 2), (2, 4)):
+            timed(f"NUJDS {perm} u={u} r={r}", J, xp,
+                  lambda u=u, r=r: (J.set_format("NUJDS" if u > 1 else "JDS", unroll=u),
+                                    J.set_kernel("vector", rows_per_warp=r)))
+        for b in (64, 128, 256, 512, 1024, 2048, 4096):
+            timed(f"NBJDS {perm} b={b}", J, xp, lambda b=b: (J.set_format("NBJDS", block=b),
+                                                            J.set_kernel("vector", rows_per_warp=1)))
+        del J
+        torch.cuda.empty_cache()
+        for fmt in ("RBJDS", "SOJDS"):
+            for b in ((1, 1024) if perm == "symmetric" else ()):
+                R = M.to_jds(fmt, perm, block=b)
+                strides(f"{fmt} {perm} b={b}", R.col)
+                del R
+            for b in (64, 256, 1024, 4096):
+                R = M.to_jds(fmt, perm, block=b)
+                timed(f"{fmt} {perm} b={b}", R, xp)
+                del R
+            torch.cuda.empty_cache()
+        for w in (32, 128, 1024, 8192):
+            G = M.to_jds("SELL", perm, window=w)
+            strides(f"SELL {perm} w={w}", G.col)
+            sectors(f"SELL {perm} w={w}", G)
+            xs = G.permute(x) if perm == "symmetric" else x
+            for u in (1, 2, 4):
+                timed(f"SELL {perm} w={w} u={u}", G, xs, lambda u=u, G=G: G.set_format("SELL", unroll=u))
+            del G
+            torch.cuda.empty_cache()
+    return out
+
+
 def run_ncu_case(args):
     """A few launches of one kernel on a 2e6-row HH-like matrix (~350 MB,
     above the 129 MB L2) for an ncu capture; prints nothing to time."""
@@ -643,6 +799,12 @@ def main():
     args = parse()
     if args.ncu_case:
         run_ncu_case(args)
+        return
+    if args.micro:
+        print(json.dumps(run_micro(args)), flush=True)
+        return
+    if args.analysis:
+        print(json.dumps(run_analysis(args)), flush=True)
         return
     res = run_reference(args) if args.impl == "reference" else run_ours(args)
     if res is not None:

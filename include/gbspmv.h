@@ -413,6 +413,67 @@ gbsp_status gbsp_crs_spmv_noalloc(int64_t n_rows, int64_t n_cols, int64_t nnz,
                                   const void *d_val, gbsp_dtype dtype, int32_t accumulate,
                                   const void *d_x, void *d_y, void *stream);
 
+/* ------------------------------------------------ basic gather operations -- */
+
+/* The basic sparse vector operations of Sect. 3.1 (its table of ADD and SCP
+ * kernels), which isolate the cost of the indirect x access of the SpMVM
+ * inner loop:
+ *     ADD:  s = sum_{i<n} B(idx(i))        SCP:  s = sum_{i<n} A(i) * B(idx(i))
+ * with idx(i) = i (PD, packed dense), stride*i (CS, constant stride computed
+ * in the loop) or ind(i) (IND: the paper's IS with ind(i) = k*i and IR with
+ * random strides differ only in the index array the caller passes). */
+typedef enum { GBSP_GATHER_ADD = 0, GBSP_GATHER_SCP = 1 } gbsp_gather_op;
+typedef enum { GBSP_ACCESS_PD = 0, GBSP_ACCESS_CS = 1, GBSP_ACCESS_IND = 2 } gbsp_access;
+
+/* Number of FP64 partial sums gbsp_gather_sum needs for n elements on the
+ * current device (one per CTA of its grid). */
+gbsp_status gbsp_gather_partials(int64_t n, int32_t *n_partials);
+
+/* *d_out = the sum above, FP64.  d_a [n] (SCP only), d_b [len_b], d_ind [n]
+ * (IND only) int32, all device memory borrowed for the call; d_partials is
+ * caller scratch of n_partials doubles (>= gbsp_gather_partials(n)).  Each
+ * thread sums its elements in ascending i, then fixed reduction trees: the
+ * result is the same on every run on a given device.  Two launches on
+ * `stream`, asynchronous.  n = 0 gives 0.
+ * Errors: GBSP_ERR_ARG for an unknown op or access, NULL pointers, PD with
+ * n > len_b, CS with stride < 1 or (n-1)*stride >= len_b, or n_partials
+ * too small.  IND entries outside [0, len_b) are skipped (they add nothing)
+ * and set *d_status = GBSP_ERR_ARG when d_status (device int32) is given;
+ * the call never clears *d_status. */
+gbsp_status gbsp_gather_sum(int32_t op, int32_t access, int64_t n, int64_t stride,
+                            const double *d_a, const double *d_b, int64_t len_b,
+                            const int32_t *d_ind, double *d_partials, int32_t n_partials,
+                            double *d_out, int32_t *d_status, void *stream);
+
+/* -------------------------------------------------- access-pattern analysis -- */
+
+/* Stride distribution of the x accesses (Sect. 4, Fig. 4a).  For a
+ * column-index array read in storage order -- the order in which the
+ * paper's serial CRS, JDS, RBJDS and SOJDS loops read x -- counts every jump
+ * s = col[i+1] - col[i] by size: bin 0 is s = 0, bin b >= 1 holds
+ * 2^(b-1) <= |s| < 2^b (x strides of 8*2^(b-1) to 8*2^b - 1 bytes for
+ * FP64).  d_hist: int64 [66] device memory, overwritten: [0..32] forward
+ * jumps (s >= 0), [33..65] backward jumps (s < 0).  d_col: int32 [nnz]
+ * device.  Exact counts (integer atomics).  Asynchronous on `stream`.
+ * Errors: GBSP_ERR_ARG for NULL pointers or nnz < 0. */
+gbsp_status gbsp_stride_hist(const int32_t *d_col, int64_t nnz, int64_t *d_hist, void *stream);
+
+/* Sectors per warp-wide gather of x (GB300 counterpart of the stride
+ * analysis; the paper has none).  For every warp-wide load of x that the
+ * handle's product kernel issues, the number c of distinct 32-byte sectors
+ * it touches (elem_bytes per x entry: 8 for FP64, 4 for FP32);
+ * d_hist[c] (int64 [33], device memory, overwritten) counts such loads.
+ * Patterns: CRS with `lanes` lanes per row (1, 2, 4, ..., 32; a warp holds
+ * 32/lanes consecutive rows, lane l of a row reads entries l, l+lanes, ...);
+ * JDS / NUJDS / NBJDS / JDS_LITERAL storage with a thread per permuted row
+ * (a warp holds 32 consecutive rows, one load per jagged diagonal); SELL
+ * (a warp holds one 32-row block, one load per slot).  `lanes` is ignored
+ * for JDS-family handles.  Asynchronous on `stream`.
+ * Errors: GBSP_ERR_ARG (bad lanes or elem_bytes), GBSP_ERR_UNSUPPORTED for
+ * RBJDS / SOJDS handles. */
+gbsp_status gbsp_warp_sectors(gbsp_handle A, int32_t lanes, int32_t elem_bytes, int64_t *d_hist,
+                              void *stream);
+
 /* ------------------------------------------------------------ autotuner -- */
 
 /* Time the candidate kernels for `A` with k right-hand sides on the device

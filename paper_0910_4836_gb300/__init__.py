@@ -13,11 +13,12 @@ from __future__ import annotations
 import importlib
 
 __all__ = ["CRSMatrix", "JDSMatrix", "GbspError", "SpMVFunction", "power_apply", "Batch",
-           "build", "synth"]
+           "gather_sum", "build", "synth"]
 
 _LAZY = {
     "CRSMatrix": "sparse", "JDSMatrix": "sparse", "GbspError": "_lib",
     "SpMVFunction": "autograd", "power_apply": "autograd", "Batch": "batch",
+    "gather_sum": "gather",
 }
 
 

@@ -102,6 +102,11 @@ SIGNATURES = {
     "gbsp_autotune": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp, P(KernelOpts), P(c_f32)]),
     "gbsp_crs_spmv_noalloc": (c_i32, [c_i64, c_i64, c_i64, c_vp, c_vp, c_vp, c_i32, c_i32, c_vp, c_vp,
                                       c_vp]),
+    "gbsp_gather_partials": (c_i32, [c_i64, ctypes.POINTER(c_i32)]),
+    "gbsp_stride_hist": (c_i32, [c_vp, c_i64, c_vp, c_vp]),
+    "gbsp_warp_sectors": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_vp]),
+    "gbsp_gather_sum": (c_i32, [c_i32, c_i32, c_i64, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_i32, c_vp,
+                                c_vp, c_vp]),
 }
 
 _lib = None

@@ -259,8 +259,13 @@ __global__ void __launch_bounds__(1024) sell_kernel(JdsArgs a) {
     // length inside their window, so the warp's pick among them rotates from
     // one iteration to the next: otherwise warp 0 would always get the
     // longest rows and warp wpc-1 the shortest.
+    // The group a CTA takes also rotates (by one per iteration): with a
+    // window longer than a group, a fixed stride of gridDim.x groups would
+    // hand every CTA the same position in every window.
     int64_t it = 0;
-    for (int64_t g = blockIdx.x; g * wpc < nb; g += gridDim.x, ++it) {
+    for (int64_t g0 = 0; g0 * wpc < nb; g0 += gridDim.x, ++it) {
+        const int64_t g = g0 + (int64_t)((blockIdx.x + it) % gridDim.x);
+        if (g * wpc >= nb) continue;
         const int64_t b = g * wpc + (int64_t)((wid + it * 7) % wpc);
         if (b >= nb) continue;
         const int64_t r = b * 32 + lane;

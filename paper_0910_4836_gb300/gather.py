@@ -1,0 +1,57 @@
+"""The basic sparse vector operations of Sect. 3.1 (ADD / SCP over packed
+dense, constant-stride and indirect access) on the device: argument
+marshalling over ``gbsp_gather_sum``."""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib as L
+from .sparse import _need_cuda, _stream, _vp
+
+OPS = {"ADD": 0, "SCP": 1}
+ACCESS = {"PD": 0, "CS": 1, "IND": 2}
+
+
+def partials_needed(n: int) -> int:
+    c = ctypes.c_int32()
+    L.check(L.load().gbsp_gather_partials(n, ctypes.byref(c)), "gbsp_gather_partials")
+    return int(c.value)
+
+
+class GatherSum:
+    """One configured gather sum with its scratch, for repeated launches:
+    ``s = GatherSum("SCP", "IND", n, b, a=a, ind=ind); s(); s.out``."""
+
+    def __init__(self, op: str, access: str, n: int, b: torch.Tensor, a: torch.Tensor | None = None,
+                 k: int = 1, ind: torch.Tensor | None = None, status: torch.Tensor | None = None):
+        if op not in OPS or access not in ACCESS:
+            raise ValueError(f"unknown op {op!r} or access {access!r}")
+        self.b = _need_cuda(b, "b", torch.float64)
+        self.a = _need_cuda(a, "a", torch.float64) if op == "SCP" else None
+        self.ind = _need_cuda(ind, "ind", torch.int32) if access == "IND" else None
+        if self.a is not None and self.a.numel() < n:
+            raise ValueError("a shorter than n")
+        if self.ind is not None and self.ind.numel() < n:
+            raise ValueError("ind shorter than n")
+        self.op, self.access, self.n, self.k = OPS[op], ACCESS[access], int(n), int(k)
+        dev = self.b.device
+        self.n_partials = partials_needed(self.n)
+        self.partials = torch.empty(self.n_partials, dtype=torch.float64, device=dev)
+        self.out = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.status = status
+
+    def __call__(self, stream=None) -> torch.Tensor:
+        L.check(L.load().gbsp_gather_sum(self.op, self.access, self.n, self.k, _vp(self.a), _vp(self.b),
+                                         self.b.numel(), _vp(self.ind), _vp(self.partials), self.n_partials,
+                                         _vp(self.out), _vp(self.status), _stream(stream)),
+                "gbsp_gather_sum")
+        return self.out
+
+
+def gather_sum(op: str, access: str, n: int, b: torch.Tensor, a: torch.Tensor | None = None, k: int = 1,
+               ind: torch.Tensor | None = None, status: torch.Tensor | None = None) -> torch.Tensor:
+    """s = sum_i B(idx(i)) (ADD) or sum_i A(i) B(idx(i)) (SCP), idx(i) = i
+    (PD), k i (CS) or ind(i) (IND), as a 1-element FP64 device tensor."""
+    return GatherSum(op, access, n, b, a, k, ind, status)()

@@ -1,0 +1,123 @@
+"""The basic gather sums of Sect. 3.1 (ADD / SCP over PD, CS, IS, IR and
+Gaussian strides) on the GPU against the oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from gpu_util import dev, host
+from paper_0910_4836_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+U64 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    import paper_0910_4836_gb300 as g
+    g.build()
+
+
+def bound(n, n_partials, abs_sum):
+    """Error bound of the kernel's summation: a chain of ceil(n/T) terms per
+    thread (T = 256 threads x CTAs), a 5-level shuffle tree, a chain over 8
+    warps, then the partials (a chain of ceil(P/256) per thread and the same
+    trees), plus the SCP product rounding: gamma_m sum|t|."""
+    T = 256 * n_partials
+    m = math.ceil(n / T) + 5 + 8 + math.ceil(n_partials / 256) + 5 + 8 + 1
+    return m * U64 / (1 - m * U64) * abs_sum
+
+
+def run(op, access, n, b, a=None, k=1, ind=None, status=None):
+    from paper_0910_4836_gb300.gather import GatherSum
+    g = GatherSum(op, access, n, dev(b), a=None if a is None else dev(a), k=k,
+                  ind=None if ind is None else dev(ind, torch.int32), status=status)
+    return float(host(g())[0]), g.n_partials
+
+
+def cases():
+    """(name, access, n, k, ind, len_b): sizes span many CTAs and end in a
+    ragged tail."""
+    n = 300_001
+    yield "PD", "PD", n, 1, None, n
+    for k in (8, 530):
+        m = 20_011 if k == 530 else n
+        yield f"CS k={k}", "CS", m, k, None, k * (m - 1) + 1
+        yield f"IS k={k}", "IND", m, 1, S.stride_indices(m, k), k * (m - 1) + 1
+    for k in (1, 8, 530):
+        ind = S.geometric_indices(n if k < 530 else 20_011, 1.0 / k, 31 + k)
+        yield f"IR k={k}", "IND", len(ind), 1, ind, int(ind[-1]) + 1
+    ind = S.gaussian_indices(n, 16.0, 256.0, 16 * n, 41)
+    yield "Gauss mean=16 var=256", "IND", n, 1, ind, 16 * n
+
+
+@pytest.mark.parametrize("op", ["ADD", "SCP"])
+@pytest.mark.parametrize("case", list(cases()), ids=lambda c: c[0])
+def test_gather_random_within_bound(op, case):
+    name, access, n, k, ind, len_b = case
+    b = S.vector(len_b, 51)
+    a = S.vector(n, 52) if op == "SCP" else None
+    s, npart = run(op, access, n, b, a, k, ind)
+    ref, abs_sum = O.gather_sum_exact(op, access, n, b, a=a, k=k, ind=ind)
+    assert abs(s - ref) <= bound(n, npart, abs_sum), (name, s, ref)
+
+
+@pytest.mark.parametrize("op", ["ADD", "SCP"])
+@pytest.mark.parametrize("case", list(cases()), ids=lambda c: c[0])
+def test_gather_integers_bit_exact(op, case):
+    """Integer inputs with every partial sum below 2^53: any summation
+    order is exact, so the GPU sum equals the oracle's bit for bit."""
+    name, access, n, k, ind, len_b = case
+    b = S.int_vector(len_b, 61, 1000)
+    a = S.int_vector(n, 62, 1000) if op == "SCP" else None
+    s, _ = run(op, access, n, b, a, k, ind)
+    assert s == O.gather_sum(op, access, n, b, a=a, k=k, ind=ind), name
+
+
+def test_gather_is_deterministic():
+    n = 1_000_003
+    b = S.vector(4 * n, 71)
+    a = S.vector(n, 72)
+    ind = S.geometric_indices(n, 0.25, 73)
+    first, _ = run("SCP", "IND", n, b[: int(ind[-1]) + 1], a, 1, ind)
+    for _ in range(3):
+        assert run("SCP", "IND", n, b[: int(ind[-1]) + 1], a, 1, ind)[0] == first
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 255, 256, 2047, 2049])
+def test_gather_small_and_empty(n):
+    b = S.int_vector(max(n, 1), 81, 1000)
+    a = S.int_vector(max(n, 1), 82, 1000)
+    s, _ = run("SCP", "PD", n, b, a)
+    assert s == (O.gather_sum("SCP", "PD", n, b, a=a) if n else 0.0)
+
+
+def test_gather_bad_index_is_skipped_and_reported():
+    """Entries of ind outside [0, len_b) add nothing and set the status
+    word (the kernel's own bounds check; nothing is read out of range)."""
+    n = 10_000
+    b = S.int_vector(n, 91, 1000)
+    ind = np.arange(n, dtype=np.int32)
+    ind[17] = -5
+    ind[9_000] = n
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s, _ = run("ADD", "IND", n, b, ind=ind, status=status)
+    keep = np.ones(n, bool)
+    keep[[17, 9_000]] = False
+    assert s == float(b[keep].sum())
+    assert int(host(status)[0]) == -1  # GBSP_ERR_ARG
+
+
+def test_gather_argument_errors():
+    from paper_0910_4836_gb300 import GbspError
+    from paper_0910_4836_gb300.gather import GatherSum
+    b = torch.zeros(100, dtype=torch.float64, device="cuda")
+    with pytest.raises(GbspError):
+        GatherSum("ADD", "CS", 11, b, k=10)()   # (n-1)*k = 100 >= len_b
+    with pytest.raises(GbspError):
+        GatherSum("ADD", "PD", 101, b)()
+    with pytest.raises(GbspError):
+        GatherSum("ADD", "CS", 5, b, k=0)()
