@@ -66,6 +66,9 @@ def lib():
             "orc_sell_spmv": [_I64, _I32, _I32, _I32, _F64, _F64, _F64],
             "orc_gather_sum": [_INT, _INT, _I64, _I64, _F64, _F64, _I32],
             "orc_gather_sum_exact": [_INT, _INT, _I64, _I64, _F64, _F64, _I32, _F64],
+            "orc_psell_build": [_I64, _I64, _I32, _I32, _F64, _INT, _I64, _I32, _I32, _I32, _I32, _I32,
+                                _F64],
+            "orc_psell_spmv": [_I64, _I32, _I32, _I32, _F64, _F64, _F64],
             "orc_stride_hist": [_I64, _I32, _I64P],
             "orc_warp_sectors_crs": [_I64, _I32, _I32, _INT, _INT, _I64P],
             "orc_warp_sectors_jds": [_I64, _I64, _I32, _I32, _INT, _I64P],
@@ -76,7 +79,7 @@ def lib():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = _I64 if name in ("orc_max_row_len", "orc_jds_build") else (
-                _INT if name in ("orc_num_threads", "orc_sell_build") else (
+                _INT if name in ("orc_num_threads", "orc_sell_build", "orc_psell_build") else (
                     ctypes.c_double if name == "orc_gather_sum" else None))
         _lib = L
     return _lib
@@ -391,3 +394,31 @@ def warp_sectors_sell(S_, elem_bytes=8):
     h = np.zeros(33, dtype=np.int64)
     lib().orc_warp_sectors_sell(S_.n_rows, _i32(S_.rlen), _i32(S_.blk_ptr), _i32(S_.col), elem_bytes, h)
     return h
+
+
+# ---------------------------------------------------------------------------
+# Paired SELL (rows of rank q and m-1-q of a sorted window share a lane)
+# ---------------------------------------------------------------------------
+
+def psell_build(A, window, symmetric=True):
+    """Window sort, pairing and slot-major storage, see orc_psell_build."""
+    n = A.n_rows
+    perm = np.zeros(n, np.int32)
+    iperm = np.zeros(n, np.int32)
+    rlen = np.zeros(n, np.int32)
+    blk = np.zeros((n + 63) // 64 + 1, np.int32)
+    col = np.zeros(A.nnz, np.int32)
+    val = np.zeros(A.nnz)
+    r = lib().orc_psell_build(n, A.n_cols, _i32(A.row_ptr), _i32(A.col), _f64(A.val), int(symmetric),
+                              window, perm, iperm, rlen, blk, col, val)
+    if r == -1:
+        raise ValueError("symmetric permutation needs a square matrix")
+    if r == -2:
+        raise ValueError("window must be a positive multiple of 64")
+    return SELL(n, symmetric, window, perm, iperm, rlen, blk, col, val)
+
+
+def psell_spmv(P, x_p):
+    out = np.zeros(P.n_rows)
+    lib().orc_psell_spmv(P.n_rows, _i32(P.rlen), _i32(P.blk_ptr), _i32(P.col), _f64(P.val), _f64(x_p), out)
+    return out

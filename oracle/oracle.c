@@ -650,3 +650,103 @@ void orc_warp_sectors_sell(int64_t n_rows, const int32_t *rlen, const int32_t *b
         }
     }
 }
+
+/* ------------------------------------------------------------------------
+ * Paired SELL (a GB300 layout of this library, not the paper's): the rows of
+ * every window of `window` rows (a multiple of 64) are sorted by decreasing
+ * length (stable), and the row of rank q is paired with the row of rank
+ * m-1-q (m = rows in the window), so that one lane walks a long row and a
+ * short one: lane q < ceil(m/2) owns row a = rank q and, when m-1-q > q,
+ * row b = rank m-1-q.  Lanes form blocks of 32 consecutive lanes of a
+ * window; block g (counted over the whole matrix) owns the permuted rows
+ * 64g .. 64g+R-1 (R = min(64, n - 64g)): with L = ceil(R/2) lanes, the
+ * a-row of lane p is permuted row 64g + p and its b-row, if any,
+ * 64g + L + p.  Storage of block g, slot by slot: slot t holds, in lane
+ * order, every lane whose total length len_a + len_b exceeds t, with entry
+ * t of the lane's concatenated rows (row a's entries, then row b's).
+ * Returns 0, -1 (symmetric and not square) or -2 (bad window).
+ * ---------------------------------------------------------------------- */
+int orc_psell_build(int64_t n_rows, int64_t n_cols, const int32_t *row_ptr, const int32_t *col_idx,
+                    const double *val, int symmetric, int64_t window, int32_t *perm, int32_t *iperm,
+                    int32_t *rlen, int32_t *blk_ptr, int32_t *col_out, double *val_out)
+{
+    if (symmetric && n_rows != n_cols) return -1;
+    if (window < 64 || window % 64) return -2;
+    int64_t nj = orc_max_row_len(n_rows, row_ptr);
+    int64_t *count = (int64_t *)calloc((size_t)(nj + 2), sizeof(int64_t));
+    int64_t *start = (int64_t *)calloc((size_t)(nj + 2), sizeof(int64_t));
+    int32_t *sorted = (int32_t *)malloc((size_t)(window > 0 ? window : 1) * sizeof(int32_t));
+    for (int64_t w0 = 0; w0 < n_rows; w0 += window) {
+        int64_t w1 = w0 + window < n_rows ? w0 + window : n_rows, m = w1 - w0;
+        /* stable counting sort of the window by decreasing length */
+        for (int64_t l = 0; l <= nj; ++l) count[l] = 0;
+        for (int64_t i = w0; i < w1; ++i) count[row_ptr[i + 1] - row_ptr[i]]++;
+        int64_t pos = 0;
+        for (int64_t l = nj; l >= 0; --l) { start[l] = pos; pos += count[l]; }
+        for (int64_t i = w0; i < w1; ++i) sorted[start[row_ptr[i + 1] - row_ptr[i]]++] = (int32_t)i;
+        /* pair rank q with rank m-1-q; place the rows by block */
+        int64_t lanes = (m + 1) / 2;
+        for (int64_t q = 0; q < lanes; ++q) {
+            int64_t g = w0 / 64 + q / 32, p = q % 32;
+            int64_t R = n_rows - 64 * g < 64 ? n_rows - 64 * g : 64, L = (R + 1) / 2;
+            perm[64 * g + p] = sorted[q];
+            if (m - 1 - q > q) perm[64 * g + L + p] = sorted[m - 1 - q];
+        }
+    }
+    for (int64_t r = 0; r < n_rows; ++r) {
+        iperm[perm[r]] = (int32_t)r;
+        rlen[r] = row_ptr[perm[r] + 1] - row_ptr[perm[r]];
+    }
+    int64_t nb = (n_rows + 63) / 64, pos = 0;
+    for (int64_t g = 0; g < nb; ++g) {
+        int64_t R = n_rows - 64 * g < 64 ? n_rows - 64 * g : 64, L = (R + 1) / 2;
+        int64_t width = 0;
+        for (int64_t p = 0; p < L; ++p) {
+            int64_t tot = rlen[64 * g + p] + (L + p < R ? rlen[64 * g + L + p] : 0);
+            if (tot > width) width = tot;
+        }
+        blk_ptr[g] = (int32_t)pos;
+        for (int64_t t = 0; t < width; ++t)
+            for (int64_t p = 0; p < L; ++p) {
+                int64_t ra = 64 * g + p, rb = 64 * g + L + p;
+                int64_t la = rlen[ra], lb = L + p < R ? rlen[rb] : 0;
+                if (t >= la + lb) continue;
+                int64_t src = t < la ? (int64_t)row_ptr[perm[ra]] + t : (int64_t)row_ptr[perm[rb]] + (t - la);
+                val_out[pos] = val[src];
+                col_out[pos] = symmetric ? iperm[col_idx[src]] : col_idx[src];
+                ++pos;
+            }
+    }
+    blk_ptr[nb] = (int32_t)pos;
+    free(count);
+    free(start);
+    free(sorted);
+    return 0;
+}
+
+/* Paired SELL product in the permuted basis: block after block, slot after
+ * slot, every lane adding its slot-t entry to the row it is in. */
+void orc_psell_spmv(int64_t n_rows, const int32_t *rlen, const int32_t *blk_ptr,
+                    const int32_t *col_s, const double *val_s, const double *invec, double *resvec)
+{
+    for (int64_t i = 0; i < n_rows; ++i) resvec[i] = 0.0;
+    int64_t nb = (n_rows + 63) / 64;
+    for (int64_t g = 0; g < nb; ++g) {
+        int64_t R = n_rows - 64 * g < 64 ? n_rows - 64 * g : 64, L = (R + 1) / 2;
+        int64_t width = 0;
+        for (int64_t p = 0; p < L; ++p) {
+            int64_t tot = rlen[64 * g + p] + (L + p < R ? rlen[64 * g + L + p] : 0);
+            if (tot > width) width = tot;
+        }
+        int64_t pos = blk_ptr[g];
+        for (int64_t t = 0; t < width; ++t)
+            for (int64_t p = 0; p < L; ++p) {
+                int64_t ra = 64 * g + p, rb = 64 * g + L + p;
+                int64_t la = rlen[ra], lb = L + p < R ? rlen[rb] : 0;
+                if (t >= la + lb) continue;
+                int64_t r = t < la ? ra : rb;
+                resvec[r] = resvec[r] + val_s[pos] * invec[col_s[pos]];
+                ++pos;
+            }
+    }
+}

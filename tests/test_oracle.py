@@ -674,3 +674,77 @@ def test_warp_sectors_crs_one_lane_equal_rows_is_jds():
     cols = ((np.arange(n)[:, None] + np.array([0, 97, 1003])[None, :]) % n).ravel()
     A = S.from_coo(n, n, rows, cols, np.ones(3 * n))
     assert np.array_equal(O.warp_sectors_crs(A, 1), O.warp_sectors_jds(O.jds_build(A, False)))
+
+
+# --------------------------------------------------------------------------
+# Paired SELL (a GPU layout of this library): rank q pairs with rank m-1-q
+# --------------------------------------------------------------------------
+
+def test_psell_hand_worked_example():
+    """Rows of lengths 1, 3, 2, 0.  Sorted by decreasing length: rows 1, 2,
+    0, 3.  Two lanes: lane 0 = (row 1, row 3), lane 1 = (row 2, row 0).
+    Permuted rows: a-rows 1, 2 at 0, 1; b-rows 3, 0 at 2, 3.  Lane totals
+    3 and 3; slots: t=0 (1.0, 2.0), t=1 (1.1, 2.1), t=2 (1.2, 0.0) where
+    r.e is entry e of row r."""
+    A = S.from_coo(4, 4, [0, 1, 1, 1, 2, 2], [0, 0, 1, 3, 2, 3], [1., 2, 3, 4, 5, 6])
+    P = O.psell_build(A, 64, False)
+    assert list(P.perm) == [1, 2, 3, 0]
+    assert list(P.rlen) == [3, 2, 0, 1]
+    assert list(P.blk_ptr) == [0, 6]
+    assert list(P.col) == [0, 2, 1, 3, 3, 0]
+    assert list(P.val) == [2., 5., 3., 6., 4., 1.]
+    P = O.psell_build(A, 64, True)
+    assert list(P.col) == [3, 1, 0, 2, 2, 3]  # iperm = [3, 0, 1, 2]
+
+
+def test_psell_equal_lengths_closed_form():
+    """Equal row lengths keep their order under the stable sort, so lane q
+    of a full 64-row window pairs rows q and 63-q."""
+    n = 64 * 3 + 10
+    A = S.from_coo(n, n, np.repeat(np.arange(n), 2), np.stack([np.arange(n), (np.arange(n) + 5) % n], 1).ravel(),
+                   np.ones(2 * n))
+    P = O.psell_build(A, 64, False)
+    for g in range(3):
+        assert list(P.perm[64 * g:64 * g + 32]) == list(range(64 * g, 64 * g + 32))
+        assert list(P.perm[64 * g + 32:64 * g + 64]) == list(range(64 * g + 63, 64 * g + 31, -1))
+    # last window, 10 rows: 5 lanes (q, 9-q)
+    assert list(P.perm[192:]) == [192, 193, 194, 195, 196, 201, 200, 199, 198, 197]
+    assert np.array_equal(np.diff(P.blk_ptr), [128, 128, 128, 20])
+
+
+@pytest.mark.parametrize("window", [64, 128, 256])
+@pytest.mark.parametrize("n", [1, 63, 64, 65, 129, 1000])
+def test_psell_product_and_invariants(window, n):
+    A = S.small_random(n, n, 40 + n, density=min(0.5, 12.0 / n), empty_rows=0.1)
+    for sym in (True, False):
+        P = O.psell_build(A, window, sym)
+        assert np.array_equal(np.sort(P.perm), np.arange(n))
+        assert np.array_equal(P.iperm[P.perm], np.arange(n))
+        assert all(P.perm[w0:w0 + window].min() >= w0 and P.perm[w0:w0 + window].max() < w0 + window
+                   for w0 in range(0, n, window))
+        assert P.rlen.sum() == A.nnz and P.blk_ptr[-1] == A.nnz
+        x = S.vector(n, 3)
+        xp = x[P.perm] if sym else x
+        y = np.zeros(n)
+        y[P.perm] = O.psell_spmv(P, xp)
+        ref = A.to_dense() @ x
+        s = np.abs(A.to_dense()) @ np.abs(x)
+        assert np.all(np.abs(y - ref) <= 1e-13 * s + 1e-300)
+        Ai = S.integer_values(A, 9, 1000)
+        xi = S.int_vector(n, 10, 1000)
+        Pi = O.psell_build(Ai, window, sym)
+        yi = np.zeros(n)
+        yi[Pi.perm] = O.psell_spmv(Pi, xi[Pi.perm] if sym else xi)
+        assert np.array_equal(yi, (Ai.to_dense().astype(np.int64) @ xi.astype(np.int64)).astype(np.float64))
+
+
+def test_psell_pairs_long_with_short():
+    """In a full window the a-row of each lane is at least as long as its
+    b-row, and lane totals vary less than row lengths (the point of it)."""
+    A = S.hh_like(20_000, 1)
+    P = O.psell_build(A, 64, False)
+    a = P.rlen.reshape(-1, 64)[:, :32] if len(P.rlen) % 64 == 0 else P.rlen[:len(P.rlen) // 64 * 64].reshape(-1, 64)[:, :32]
+    b = P.rlen[:len(P.rlen) // 64 * 64].reshape(-1, 64)[:, 32:]
+    assert np.all(a >= b)
+    tot = a + b
+    assert tot.std(axis=1).mean() < 0.5 * P.rlen[:len(P.rlen) // 64 * 64].reshape(-1, 64).std(axis=1).mean()
