@@ -217,6 +217,13 @@ def candidates(M, A, x, only=None):
             xs = G.permute(x) if perm == "symmetric" else x
             gb = 12 * A.nnz + 4 * (G.n_blocks + 1) + 4 * A.n_rows + 8 * A.n_cols + 8 * A.n_rows
             out.append((name, G, xs, gb, ("fixed",)))
+    for perm, w, u in (("row_only", 64, 2), ("row_only", 64, 4), ("row_only", 128, 4), ("symmetric", 64, 4)):
+        name = f"PSELL {perm} w={w} u={u}"
+        if want(name):
+            G = M.to_jds("PSELL", perm, window=w, unroll=u)
+            xs = G.permute(x) if perm == "symmetric" else x
+            gb = 12 * A.nnz + 4 * (G.n_blocks + 1) + 4 * A.n_rows + 8 * A.n_cols + 8 * A.n_rows
+            out.append((name, G, xs, gb, ("fixed",)))
     for perm in ("symmetric", "row_only"):
         if only is not None and not any(f"{f} {perm}".startswith(only) or only.startswith(f"{f} {perm}")
                                         for f in ("JDS", "NUJDS", "NBJDS", "JDS_LITERAL", "RBJDS", "SOJDS")):

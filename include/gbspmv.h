@@ -60,7 +60,18 @@ typedef enum { GBSP_F64 = 0, GBSP_F32 = 1 } gbsp_dtype;
  * Kreutzer, Hager, Wellein, Fehske & Bishop (SIAM J. Sci. Comput. 2014),
  * the same group's follow-up; with one window it is RBJDS with block 32.
  * Rows stay near their original position, so the gathers of x keep the
- * matrix's locality while the lanes of a warp still do equal work. */
+ * matrix's locality while the lanes of a warp still do equal work.
+ * PSELL (a GB300 layout of this library; the paper has none) pairs rows
+ * inside each length-sorted window of `window` rows (a multiple of 64): the
+ * row of rank q shares a lane with the row of rank m-1-q (m rows in the
+ * window), so one lane walks a long row and then a short one and the lanes
+ * of a warp do nearly equal work with far fewer idle slots than SELL at the
+ * same window.  Block g holds lanes 32g'..32g'+31 of a window and owns the
+ * permuted rows 64g .. 64g+R-1 (R = min(64, n-64g), L = ceil(R/2) lanes):
+ * lane p's first row is permuted row 64g+p, its second (if any) 64g+L+p.
+ * Storage is slot-major per block: slot t holds, in lane order, each lane
+ * whose two rows together have more than t entries, with the lane's t-th
+ * entry (first row's entries, then the second row's). */
 typedef enum {
     GBSP_CRS = 0,
     GBSP_JDS = 1,
@@ -69,7 +80,8 @@ typedef enum {
     GBSP_NUJDS = 4,
     GBSP_SOJDS = 5,
     GBSP_JDS_LITERAL = 6,
-    GBSP_SELL = 7
+    GBSP_SELL = 7,
+    GBSP_PSELL = 8
 } gbsp_format;
 
 /* Sect. 2: JDS permutes rows AND columns (A_{p(i),p(j)}), so all work runs in
@@ -188,13 +200,13 @@ typedef struct {
     int32_t perm_mode;  /* gbsp_perm_mode */
     int32_t block;      /* NBJDS / RBJDS / SOJDS: rows per block (>= 1; 0 = 256) */
     int32_t unroll;     /* NUJDS / SELL: diagonals per step u (>= 1; 0 = 4) */
-    int32_t window;     /* SELL: rows per sorting window, a multiple of 32 (0 = 1024) */
+    int32_t window;     /* SELL: rows per sorting window, a multiple of 32 (PSELL: of 64) (0 = 1024) */
 } gbsp_jds_opts;
 
 typedef struct {
     int64_t n_rows, n_cols, nnz;
     int64_t n_diag;           /* N_j = longest row */
-    int64_t n_blocks;         /* RBJDS / SOJDS blocks, SELL 32-row blocks, else 0 */
+    int64_t n_blocks;         /* RBJDS / SOJDS blocks, SELL 32-row / PSELL 64-row blocks, else 0 */
     int64_t workspace_bytes;  /* scratch for gbsp_jds_build only */
 } gbsp_jds_sizes;
 
@@ -209,7 +221,7 @@ typedef struct {
     void *workspace;   /* [workspace_bytes] scratch, free after the build completes */
     int32_t *vmap;     /* optional [nnz]: CRS entry index of every stored entry, kept by the
                           handle for gbsp_jds_values (NULL: not built) */
-    int32_t *rlen;     /* SELL only: [n_rows] length of every permuted row */
+    int32_t *rlen;     /* SELL / PSELL only: [n_rows] length of every permuted row */
 } gbsp_jds_buffers;
 
 /* Sizes for converting `crs` (Sect. 2 JDS construction).  Reads the row

@@ -22,7 +22,7 @@ STATUS = {0: "GBSP_OK", -1: "GBSP_ERR_ARG", -2: "GBSP_ERR_MATRIX", -3: "GBSP_ERR
           -4: "GBSP_ERR_NOMEM", -5: "GBSP_ERR_UNSUPPORTED", -6: "GBSP_ERR_TIMEOUT"}
 F64, F32 = 0, 1
 FORMATS = {"CRS": 0, "JDS": 1, "NBJDS": 2, "RBJDS": 3, "NUJDS": 4, "SOJDS": 5, "JDS_LITERAL": 6,
-           "SELL": 7}
+           "SELL": 7, "PSELL": 8}
 PERM = {"symmetric": 0, "row_only": 1}
 OP_N, OP_T = 0, 1
 BASIS_PERMUTED, BASIS_ORIGINAL = 0, 1

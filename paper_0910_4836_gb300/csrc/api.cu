@@ -25,7 +25,8 @@ static size_t elem_size(int dtype) { return dtype == GBSP_F64 ? 8 : 4; }
 
 static bool is_jds_family(int f) {
     return f == GBSP_JDS || f == GBSP_NBJDS || f == GBSP_RBJDS || f == GBSP_NUJDS ||
-           f == GBSP_SOJDS || f == GBSP_JDS_LITERAL || f == GBSP_SELL;
+           f == GBSP_SOJDS || f == GBSP_JDS_LITERAL || f == GBSP_SELL ||
+           f == GBSP_PSELL;
 }
 
 // [a, a+na) and [b, b+nb) in bytes
@@ -250,7 +251,7 @@ gbsp_status gbsp_jds_build(gbsp_handle crs, const gbsp_jds_opts *opts, const gbs
     }
     if (sizes->n_rows != crs->n_rows || sizes->nnz != crs->nnz)
         return arg_error("gbsp_jds_build: sizes do not come from this matrix");
-    const bool sell = opts->format == GBSP_SELL;
+    const bool sell = opts->format == GBSP_SELL || opts->format == GBSP_PSELL;
     const bool blocked = opts->format == GBSP_RBJDS || opts->format == GBSP_SOJDS || sell;
     if (sell && crs->n_rows > 0 && !bufs->rlen) return arg_error("gbsp_jds_build: SELL needs rlen");
     if ((!sell && !bufs->jd_ptr) || (crs->n_rows > 0 && (!bufs->perm || !bufs->iperm)) ||
@@ -274,7 +275,8 @@ gbsp_status gbsp_jds_set_format(gbsp_handle h, int32_t format, int32_t block, in
         return arg_error("gbsp_jds_set_format: not a JDS-family handle / format");
     if (block < 0 || unroll < 0) return arg_error("gbsp_jds_set_format: negative block/unroll");
     const bool was_blocked = h->built_block > 0;
-    const bool to_blocked = format == GBSP_RBJDS || format == GBSP_SOJDS || format == GBSP_SELL;
+    const bool to_blocked =
+        format == GBSP_RBJDS || format == GBSP_SOJDS || format == GBSP_SELL || format == GBSP_PSELL;
     if (was_blocked != to_blocked || (was_blocked && format != h->format) ||
         (was_blocked && block != 0 && block != h->built_block)) {
         set_error("gbsp_jds_set_format: storage layout differs; rebuild instead");

@@ -491,6 +491,88 @@ __global__ void sell_scatter_kernel(int64_t n, const int32_t *__restrict__ perm,
     }
 }
 
+// -------------------------------------------------------- paired SELL ----
+// Thread per sorted position: rank q of a window of m rows is the first row
+// of lane q when q < ceil(m/2), else the second row of lane m-1-q; lane
+// (window w0, lane) lives in block w0/64 + lane/32 at position lane % 32.
+__global__ void psell_pair_kernel(int64_t n, int64_t window, const int32_t *__restrict__ sorted,
+                                  int32_t *perm) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t w0 = i / window * window, m = min(window, n - w0), q = i - w0;
+    const int64_t lanes = (m + 1) / 2;
+    const bool first = q < lanes;
+    const int64_t lane = first ? q : m - 1 - q;
+    const int64_t g = w0 / 64 + lane / 32, p = lane % 32;
+    const int64_t R = min((int64_t)64, n - 64 * g), L = (R + 1) / 2;
+    perm[first ? 64 * g + p : 64 * g + L + p] = sorted[i];
+}
+
+// Lane p of block g: its rows and their lengths (0 for a missing row).
+struct PsellLane {
+    int64_t ra, rb;
+    int32_t la, lb;
+    bool lane_ok, has_b;
+};
+
+__device__ __forceinline__ PsellLane psell_lane(int64_t n, int64_t g, int p, const int32_t *__restrict__ rlen) {
+    PsellLane o;
+    const int64_t R = min((int64_t)64, n - 64 * g), L = (R + 1) / 2;
+    o.lane_ok = p < L;
+    o.has_b = o.lane_ok && L + p < R;
+    o.ra = 64 * g + p;
+    o.rb = 64 * g + L + p;
+    o.la = o.lane_ok ? rlen[o.ra] : 0;
+    o.lb = o.has_b ? rlen[o.rb] : 0;
+    return o;
+}
+
+// entries per 64-row block (one warp per block)
+__global__ void psell_block_nnz_kernel(int64_t n, int64_t nb, const int32_t *__restrict__ rlen,
+                                       int32_t *blk_nnz) {
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (g >= nb) return;  // warp-uniform
+    const PsellLane ln = psell_lane(n, g, threadIdx.x & 31, rlen);
+    int32_t l = ln.la + ln.lb;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+    if ((threadIdx.x & 31) == 0) blk_nnz[g] = l;
+}
+
+// One warp per block: slot t holds the lanes whose two rows have more than
+// t entries, in lane order (position by ballot prefix); entry t of a lane is
+// entry t of its first row, or entry t - la of its second.
+template <typename T>
+__global__ void psell_scatter_kernel(int64_t n, int64_t nb, const int32_t *__restrict__ perm,
+                                     const int32_t *__restrict__ iperm, const int32_t *__restrict__ rlen,
+                                     const int32_t *__restrict__ blk_ptr, const int32_t *__restrict__ row_ptr,
+                                     const int32_t *__restrict__ col, const T *__restrict__ val, int symmetric,
+                                     int32_t *col_out, T *val_out, int32_t *vmap) {
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (g >= nb) return;  // warp-uniform
+    const int lane = threadIdx.x & 31;
+    const PsellLane ln = psell_lane(n, g, lane, rlen);
+    const int32_t total = ln.la + ln.lb;
+    const int32_t width = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)total);
+    const int64_t src_a = ln.lane_ok ? (int64_t)row_ptr[perm[ln.ra]] : 0;
+    const int64_t src_b = ln.has_b ? (int64_t)row_ptr[perm[ln.rb]] : 0;
+    const unsigned lt = (1u << lane) - 1u;
+    int64_t off = blk_ptr[g];
+    for (int32_t t = 0; t < width; ++t) {
+        const bool act = total > t;
+        const unsigned mask = __ballot_sync(0xffffffffu, act);
+        if (act) {
+            const int64_t dst = off + __popc(mask & lt);
+            const int64_t src = t < ln.la ? src_a + t : src_b + (t - ln.la);
+            const int32_t c = col[src];
+            col_out[dst] = symmetric ? iperm[c] : c;
+            val_out[dst] = val[src];
+            if (vmap) vmap[dst] = (int32_t)src;
+        }
+        off += __popc(mask);
+    }
+}
+
 // ------------------------------------------------------------- host side --
 
 static int bits_for(uint64_t maxv) {
@@ -516,17 +598,19 @@ gbsp_status jds_plan_impl(const Mat &A, const gbsp_jds_opts &o, int32_t *d_scrat
     out->n_diag = max_len;
     const bool blocked = o.format == GBSP_RBJDS || o.format == GBSP_SOJDS;
     out->n_blocks = blocked ? ceil_div(A.n_rows, block) : 0;
-    if (o.format == GBSP_SELL) {
+    if (o.format == GBSP_SELL || o.format == GBSP_PSELL) {
         const int64_t window = o.window > 0 ? o.window : 1024;
-        if (window % 32) {
-            set_error("gbsp_jds_plan: the SELL window must be a multiple of 32");
+        const int64_t rows_per_block = o.format == GBSP_PSELL ? 64 : 32;
+        if (window % rows_per_block) {
+            set_error("gbsp_jds_plan: the %s window must be a multiple of %d",
+                      o.format == GBSP_PSELL ? "PSELL" : "SELL", (int)rows_per_block);
             return GBSP_ERR_ARG;
         }
         if (bits_for((uint64_t)std::max<int64_t>(A.n_rows - 1, 0) / window) + bits_for((uint64_t)max_len) > 32) {
             set_error("gbsp_jds_plan: SELL sort key exceeds 32 bits; use a larger window");
             return GBSP_ERR_UNSUPPORTED;
         }
-        out->n_blocks = ceil_div(A.n_rows, 32);
+        out->n_blocks = ceil_div(A.n_rows, rows_per_block);
         out->workspace_bytes = align256(4 * A.n_rows) * 2 + sort_ws_bytes(A.n_rows) +
                                align256(4 * (out->n_blocks + 1)) + align256(scan_ws_bytes(out->n_blocks + 1)) + 256;
         return GBSP_OK;
@@ -588,7 +672,11 @@ static gbsp_status sell_build_impl(const Mat &A, const gbsp_jds_opts &o, const g
     const int64_t n = A.n_rows;
     const int symmetric = o.perm_mode == GBSP_PERM_SYMMETRIC;
     const int64_t window = o.window > 0 ? o.window : 1024;
-    const int64_t nb = ceil_div(n, 32);
+    const bool paired = o.format == GBSP_PSELL;
+    const int64_t rows_per_block = paired ? 64 : 32;
+    const int64_t nb = ceil_div(n, rows_per_block);
+    if (window % rows_per_block) return arg_error("gbsp_jds_build: window is not a multiple of the block rows");
+    if (sz.n_blocks != nb) return arg_error("gbsp_jds_build: sizes do not come from this plan");
     char *p = static_cast<char *>(b.workspace);
     int32_t *len = reinterpret_cast<int32_t *>(p);
     p += align256(4 * n);
@@ -612,14 +700,28 @@ static gbsp_status sell_build_impl(const Mat &A, const gbsp_jds_opts &o, const g
         int32_t *vs = nullptr;
         gbsp_status st = radix_sort_index(keys, n, lbits + wbits, sw, s, &ks, &vs);
         if (st != GBSP_OK) return st;
-        GBSP_CUDA(cudaMemcpyAsync(b.perm, vs, 4 * n, cudaMemcpyDeviceToDevice, s));
+        if (paired)
+            psell_pair_kernel<<<gr, 256, 0, s>>>(n, window, vs, b.perm);
+        else
+            GBSP_CUDA(cudaMemcpyAsync(b.perm, vs, 4 * n, cudaMemcpyDeviceToDevice, s));
         inverse_perm_kernel<<<gr, 256, 0, s>>>(n, b.perm, b.iperm);
         sell_rlen_kernel<<<gr, 256, 0, s>>>(n, b.perm, len, b.rlen);
-        sell_block_nnz_kernel<<<(unsigned)ceil_div(nb * 32, 256), 256, 0, s>>>(n, nb, b.rlen, blk_nnz);
+        if (paired)
+            psell_block_nnz_kernel<<<(unsigned)ceil_div(nb * 32, 256), 256, 0, s>>>(n, nb, b.rlen, blk_nnz);
+        else
+            sell_block_nnz_kernel<<<(unsigned)ceil_div(nb * 32, 256), 256, 0, s>>>(n, nb, b.rlen, blk_nnz);
         GBSP_LAUNCH_CHECK("sell perm / lengths");
         st = scan_exclusive(blk_nnz, nb, b.blk_ptr, b.blk_ptr + nb, scan_ws, s);
         if (st != GBSP_OK) return st;
-        if (A.dtype == GBSP_F64)
+        if (paired && A.dtype == GBSP_F64)
+            psell_scatter_kernel<double><<<(unsigned)ceil_div(nb * 32, 256), 256, 0, s>>>(
+                n, nb, b.perm, b.iperm, b.rlen, b.blk_ptr, A.row_ptr, A.col, static_cast<const double *>(A.val),
+                symmetric, b.col, static_cast<double *>(b.val), b.vmap);
+        else if (paired)
+            psell_scatter_kernel<float><<<(unsigned)ceil_div(nb * 32, 256), 256, 0, s>>>(
+                n, nb, b.perm, b.iperm, b.rlen, b.blk_ptr, A.row_ptr, A.col, static_cast<const float *>(A.val),
+                symmetric, b.col, static_cast<float *>(b.val), b.vmap);
+        else if (A.dtype == GBSP_F64)
             sell_scatter_kernel<double><<<(unsigned)ceil_div(nb * 32, 256), 256, 0, s>>>(
                 n, b.perm, b.iperm, b.rlen, b.blk_ptr, A.row_ptr, A.col, static_cast<const double *>(A.val),
                 symmetric, b.col, static_cast<double *>(b.val), b.vmap);
@@ -639,10 +741,10 @@ static gbsp_status sell_build_impl(const Mat &A, const gbsp_jds_opts &o, const g
     J->device = A.device;
     J->col = b.col;
     J->val = b.val;
-    J->format = GBSP_SELL;
+    J->format = paired ? GBSP_PSELL : GBSP_SELL;
     J->perm_mode = o.perm_mode;
-    J->block = 32;
-    J->built_block = 32;
+    J->block = (int32_t)rows_per_block;
+    J->built_block = (int32_t)rows_per_block;
     J->unroll = o.unroll > 0 ? o.unroll : 4;
     J->window = (int32_t)window;
     J->n_diag = sz.n_diag;
@@ -661,7 +763,7 @@ static gbsp_status sell_build_impl(const Mat &A, const gbsp_jds_opts &o, const g
 
 gbsp_status jds_build_impl(const Mat &A, const gbsp_jds_opts &o, const gbsp_jds_buffers &b,
                            const gbsp_jds_sizes &sz, cudaStream_t s, Mat *J) {
-    if (o.format == GBSP_SELL) return sell_build_impl(A, o, b, sz, s, J);
+    if (o.format == GBSP_SELL || o.format == GBSP_PSELL) return sell_build_impl(A, o, b, sz, s, J);
     const int64_t n = A.n_rows;
     const int symmetric = o.perm_mode == GBSP_PERM_SYMMETRIC;
     const bool blocked = o.format == GBSP_RBJDS || o.format == GBSP_SOJDS;

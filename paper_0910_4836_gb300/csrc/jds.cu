@@ -312,6 +312,95 @@ __global__ void __launch_bounds__(1024) sell_kernel(JdsArgs a) {
     }
 }
 
+// Paired SELL: one warp per block of 64 permuted rows, lane p walks row
+// 64g+p and then, if present, row 64g+L+p (the short partner of its window,
+// L = lanes of the block).  Slot t holds the lanes whose two rows have more
+// than t entries, so lane p's entry sits at (start of slot t) + (active
+// lanes below p).  When a lane reaches the end of its first row it sets that
+// row's sum aside and restarts; both rows are stored at the end.  Entries of
+// every row are added in order.
+template <int VM, int U, int KT>
+__global__ void __launch_bounds__(1024, (KT == 1 ? 2 : 1)) psell_kernel(JdsArgs a) {
+    typedef typename ValT<VM>::T T;
+    const T *__restrict__ val = static_cast<const T *>(a.val);
+    const T *__restrict__ x = static_cast<const T *>(a.x);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t nb = ceil_div_dev(a.n_rows, 64);
+    const int wpc = blockDim.x >> 5;
+    const int wid = threadIdx.x >> 5;
+    // same rotation of blocks over warps and groups over CTAs as SELL
+    int64_t it = 0;
+    for (int64_t g0 = 0; g0 * wpc < nb; g0 += gridDim.x, ++it) {
+        const int64_t g = g0 + (int64_t)((blockIdx.x + it) % gridDim.x);
+        if (g * wpc >= nb) continue;
+        const int64_t b = g * wpc + (int64_t)((wid + it * 7) % wpc);
+        if (b >= nb) continue;
+        const int R = (int)min((int64_t)64, a.n_rows - 64 * b), L = (R + 1) / 2;
+        const bool lane_ok = lane < L, has_b = lane_ok && L + lane < R;
+        const int32_t la = lane_ok ? __ldg(a.rlen + 64 * b + lane) : 0;
+        const int32_t lb = has_b ? __ldg(a.rlen + 64 * b + L + lane) : 0;
+        const int32_t total = la + lb;
+        const int32_t width = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)total);
+        int32_t off = __ldg(a.blk_ptr + b);  // entries fit int32 (CRS row_ptr is int32)
+        Acc<VM> acc[KT], first[KT];
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            acc[q].init();
+            first[q].init();
+        }
+        int c[U];
+        T v[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const bool ok = total > j;
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            const int32_t pos = off + __popc(m & lt);
+            c[j] = ok ? ld_stream(a.col + pos) : -1;
+            v[j] = ok ? ld_stream(val + pos) : T(0);
+            off += __popc(m);
+        }
+        for (int32_t d0 = 0; d0 < width; d0 += U) {
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                if (c[j] < 0) continue;
+                if (d0 + j == la) {  // first row done: set it aside, start the second
+#pragma unroll
+                    for (int q = 0; q < KT; ++q) {
+                        first[q] = acc[q];
+                        acc[q].init();
+                    }
+                }
+                const T *xr = x + xidx(a.x_perm, c[j]) * a.ldx + a.c0;
+#pragma unroll
+                for (int q = 0; q < KT; ++q)
+                    if (KT == 1 || a.c0 + q < a.k) acc[q].add(v[j], ld_vec(xr + q));
+            }
+            if (d0 + U >= width) break;
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const bool ok = total > d0 + U + j;
+                const unsigned m = __ballot_sync(0xffffffffu, ok);
+                const int32_t pos = off + __popc(m & lt);
+                c[j] = ok ? ld_stream(a.col + pos) : -1;
+                v[j] = ok ? ld_stream(val + pos) : T(0);
+                off += __popc(m);
+            }
+        }
+        if (lane_ok) {
+            // lb > 0: `first` holds row a and `acc` row b; else `acc` holds
+            // row a and row b (if any) is empty, its sum the zero in `first`
+            const int64_t ra = 64 * b + lane, rb = 64 * b + L + lane;
+#pragma unroll
+            for (int q = 0; q < KT; ++q) {
+                if (KT > 1 && a.c0 + q >= a.k) continue;
+                store_row<VM>(a, ra, a.c0 + q, lb > 0 ? first[q] : acc[q]);
+                if (has_b) store_row<VM>(a, rb, a.c0 + q, lb > 0 ? acc[q] : first[q]);
+            }
+        }
+    }
+}
+
 // JDS_LITERAL: the paper's loop, one launch per diagonal d:
 //   resvec(i) = resvec(i) + val(off+i) * invec(col_idx(off+i)), i < diagLen(d).
 template <typename T>
@@ -398,6 +487,37 @@ static void launch_sell_U(JdsArgs a, int KT, cudaStream_t s) {
     }
 }
 
+template <int VM, int U>
+static void launch_psell_U(JdsArgs a, int KT, cudaStream_t s) {
+    const int64_t nb = ceil_div(a.n_rows, 64);
+    const int threads = 1024;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(nb * 32, threads), (int64_t)num_sms() * 2));
+    switch (KT) {
+        case 1: psell_kernel<VM, U, 1><<<(unsigned)grid, threads, 0, s>>>(a); break;
+        case 2: psell_kernel<VM, U, 2><<<(unsigned)grid, threads, 0, s>>>(a); break;
+        case 4: psell_kernel<VM, U, 4><<<(unsigned)grid, threads, 0, s>>>(a); break;
+        case 8: psell_kernel<VM, U, 8><<<(unsigned)grid, threads, 0, s>>>(a); break;
+        default: psell_kernel<VM, U, 16><<<(unsigned)grid, threads, 0, s>>>(a); break;
+    }
+}
+
+template <int VM>
+static void launch_psell(const Mat &A, JdsArgs a, cudaStream_t s) {
+    int KT = 1;
+    if (a.k > 1) {
+        const int tile = A.kopt.rhs_tile > 0 ? std::min(A.kopt.rhs_tile, 16) : 16;
+        const int cols = std::min(a.k, tile);
+        KT = 2;
+        while (KT < cols) KT <<= 1;
+    }
+    for (int c0 = 0; c0 < a.k; c0 += KT) {
+        a.c0 = c0;
+        if (KT > 1 || A.unroll <= 1) launch_psell_U<VM, 1>(a, KT, s);
+        else if (A.unroll <= 2) launch_psell_U<VM, 2>(a, KT, s);
+        else launch_psell_U<VM, 4>(a, KT, s);
+    }
+}
+
 template <int VM>
 static void launch_sell(const Mat &A, JdsArgs a, cudaStream_t s) {
     int KT = 1;
@@ -421,6 +541,10 @@ static gbsp_status launch_family(const Mat &A, JdsArgs a, cudaStream_t s) {
     const int fmt = A.format;
     if (fmt == GBSP_SELL) {
         launch_sell<VM>(A, a, s);
+        return GBSP_OK;
+    }
+    if (fmt == GBSP_PSELL) {
+        launch_psell<VM>(A, a, s);
         return GBSP_OK;
     }
     if (a.k > 1 || fmt == GBSP_NBJDS || fmt == GBSP_RBJDS || fmt == GBSP_SOJDS) {

@@ -172,8 +172,8 @@ extern "C" gbsp_status gbsp_warp_sectors(gbsp_handle h, int32_t lanes, int32_t e
     if (A.kind == KIND_CRS) {
         if (lanes < 1 || lanes > 32 || (lanes & (lanes - 1)))
             return arg_error("gbsp_warp_sectors: CRS lanes must be 1, 2, 4, 8, 16 or 32");
-    } else if (A.format == GBSP_RBJDS || A.format == GBSP_SOJDS) {
-        set_error("gbsp_warp_sectors: RBJDS / SOJDS warp patterns are not modelled");
+    } else if (A.format == GBSP_RBJDS || A.format == GBSP_SOJDS || A.format == GBSP_PSELL) {
+        set_error("gbsp_warp_sectors: RBJDS / SOJDS / PSELL warp patterns are not modelled");
         return GBSP_ERR_UNSUPPORTED;
     }
     GBSP_CUDA(cudaMemsetAsync(d_hist, 0, S_BINS * sizeof(int64_t), s));

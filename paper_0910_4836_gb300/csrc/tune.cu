@@ -93,7 +93,7 @@ static std::vector<Cand> candidates(const Mat &A, int k) {
             }
         }
     } else if (A.built_block > 0) {
-        if (k == 1 && A.format == GBSP_SELL) {
+        if (k == 1 && (A.format == GBSP_SELL || A.format == GBSP_PSELL)) {
             for (int u : {1, 2, 4}) {
                 Cand c = base;
                 c.unroll = u;

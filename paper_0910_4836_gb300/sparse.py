@@ -271,8 +271,9 @@ class JDSMatrix(_Product):
         self.perm = torch.empty(A.n_rows, dtype=torch.int32, device=dev)
         self.iperm = torch.empty(A.n_rows, dtype=torch.int32, device=dev)
         self.blk_ptr = (torch.empty(sizes.n_blocks + 1, dtype=torch.int32, device=dev)
-                        if fmt in ("RBJDS", "SOJDS", "SELL") else None)
-        self.rlen = torch.empty(A.n_rows, dtype=torch.int32, device=dev) if fmt == "SELL" else None
+                        if fmt in ("RBJDS", "SOJDS", "SELL", "PSELL") else None)
+        self.rlen = (torch.empty(A.n_rows, dtype=torch.int32, device=dev) if fmt in ("SELL", "PSELL")
+                     else None)
         work = torch.empty(max(sizes.workspace_bytes, 1), dtype=torch.uint8, device=dev)
         self.vmap = torch.empty(A.nnz, dtype=torch.int32, device=dev) if value_map else None
         bufs = L.JdsBuffers(_vp(self.jd_ptr).value, _vp(self.col).value, _vp(self.val).value,
@@ -283,7 +284,7 @@ class JDSMatrix(_Product):
                 "gbsp_jds_build")
         del work  # the build synchronised the stream
         self.fmt, self.perm_mode, self.block, self.unroll = fmt, perm, block, unroll
-        self.window = window if fmt == "SELL" else None
+        self.window = window if fmt in ("SELL", "PSELL") else None
         self.symmetric = perm == "symmetric"
 
     def refresh_values(self, crs_val: torch.Tensor, stream=None) -> None:

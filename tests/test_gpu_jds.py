@@ -252,3 +252,62 @@ def test_adversarial(idx):
         J = M.to_jds(fmt, perm, block=b or 256)
         check_arrays(J, Oj, fmt, b or 256)
         assert_close64(host(J.spmv_original(dev(x))), ref, s, f"{A.name} {fmt}")
+
+
+PSELL_MATS = MATS + [lambda: S.small_random(65, 65, 24, density=0.1),
+                     lambda: S.small_random(127, 127, 25, density=0.05, empty_rows=0.5),
+                     lambda: S.from_coo(3, 3, [1], [2], [1.5])]
+
+
+@pytest.mark.parametrize("mi", range(len(PSELL_MATS)))
+@pytest.mark.parametrize("perm", ["symmetric", "row_only"])
+def test_psell_conversion_and_products(mi, perm):
+    """Paired SELL: arrays bit-exact against the oracle's builder, products
+    within tolerance for every unroll, in both bases, with accumulate."""
+    A = PSELL_MATS[mi]()
+    M = crs(A)
+    x = S.vector(A.n_cols, 71 + mi)
+    ref, s = O.crs_spmv_exact(A, x)
+    for window in (64, 128, 1024):
+        Op = O.psell_build(A, window, symmetric=perm == "symmetric")
+        G = M.to_jds("PSELL", perm, window=window, value_map=True)
+        assert G.n_blocks == (A.n_rows + 63) // 64
+        assert np.array_equal(host(G.perm), Op.perm)
+        assert np.array_equal(host(G.iperm), Op.iperm)
+        assert np.array_equal(host(G.rlen), Op.rlen)
+        assert np.array_equal(host(G.blk_ptr), Op.blk_ptr)
+        assert np.array_equal(host(G.col), Op.col)
+        assert np.array_equal(host(G.val).view(np.int64), Op.val.view(np.int64))
+        xp = O.permute(Op.perm, x) if perm == "symmetric" else x
+        for u in (1, 2, 4):
+            G.set_format("PSELL", unroll=u)
+            yp = host(G.spmv(dev(xp)))
+            assert_close64(yp, O.permute(Op.perm, ref), O.permute(Op.perm, s), f"PSELL w={window} u={u}")
+            yo = host(G.spmv_original(dev(x)))
+            assert_close64(yo, ref, s, f"PSELL w={window} u={u} original")
+            # y += A x on top of a known y
+            y0 = S.vector(A.n_rows, 5)
+            out = dev(O.permute(Op.perm, y0))
+            G.spmv(dev(xp), out=out, accumulate=True)
+            assert_close64(host(out) - O.permute(Op.perm, y0), O.permute(Op.perm, ref),
+                           O.permute(Op.perm, s) + np.abs(O.permute(Op.perm, y0)), f"PSELL accumulate u={u}")
+        # the oracle's own paired loop, in the permuted basis
+        assert_close64(O.psell_spmv(Op, xp), O.permute(Op.perm, ref), O.permute(Op.perm, s), "oracle PSELL")
+        G.refresh_values(dev(A.val * 2.0))
+        assert_close64(host(G.spmv_original(dev(x))) / 2.0, ref, s, "PSELL refreshed values")
+
+
+def test_psell_spmm_integer_and_rejections():
+    A = S.integer_values(S.hh_like(50_000, 54), 54, 512)
+    X = np.stack([S.int_vector(A.n_cols, 80 + c, 512) for c in range(16)], axis=1)
+    ref = O.crs_spmm(A, X)
+    M = crs(A)
+    G = M.to_jds("PSELL", "row_only", window=128)
+    for k in (1, 3, 4, 16):
+        Y = host(G.spmm(dev(X[:, :k].copy()), basis=1))
+        assert np.array_equal(Y, ref[:, :k]), k
+    from paper_0910_4836_gb300 import GbspError
+    with pytest.raises(GbspError):
+        M.to_jds("PSELL", "row_only", window=96)  # not a multiple of 64
+    with pytest.raises(GbspError):
+        G.set_format("SELL")  # different storage
