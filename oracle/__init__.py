@@ -69,6 +69,9 @@ def lib():
             "orc_psell_build": [_I64, _I64, _I32, _I32, _F64, _INT, _I64, _I32, _I32, _I32, _I32, _I32,
                                 _F64],
             "orc_psell_spmv": [_I64, _I32, _I32, _I32, _F64, _F64, _F64],
+            "orc_upper_count": [_I64, _I32, _I32],
+            "orc_upper_extract": [_I64, _I32, _I32, _F64, _I32, _I32, _F64],
+            "orc_sym_spmv": [_I64, _I32, _I32, _F64, _F64, _F64],
             "orc_stride_hist": [_I64, _I32, _I64P],
             "orc_warp_sectors_crs": [_I64, _I32, _I32, _INT, _INT, _I64P],
             "orc_warp_sectors_jds": [_I64, _I64, _I32, _I32, _INT, _I64P],
@@ -78,7 +81,7 @@ def lib():
         for name, args in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args
-            fn.restype = _I64 if name in ("orc_max_row_len", "orc_jds_build") else (
+            fn.restype = _I64 if name in ("orc_max_row_len", "orc_jds_build", "orc_upper_count") else (
                 _INT if name in ("orc_num_threads", "orc_sell_build", "orc_psell_build") else (
                     ctypes.c_double if name == "orc_gather_sum" else None))
         _lib = L
@@ -421,4 +424,27 @@ def psell_build(A, window, symmetric=True):
 def psell_spmv(P, x_p):
     out = np.zeros(P.n_rows)
     lib().orc_psell_spmv(P.n_rows, _i32(P.rlen), _i32(P.blk_ptr), _i32(P.col), _f64(P.val), _f64(x_p), out)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Symmetric SpMVM from the upper triangle
+# ---------------------------------------------------------------------------
+
+def upper(A):
+    """CRS of the entries with col >= row, in their CRS order."""
+    from types import SimpleNamespace
+    rp, c = _i32(A.row_ptr), _i32(A.col)
+    nu = int(lib().orc_upper_count(A.n_rows, rp, c))
+    rpu = np.zeros(A.n_rows + 1, np.int32)
+    cu = np.zeros(nu, np.int32)
+    vu = np.zeros(nu)
+    lib().orc_upper_extract(A.n_rows, rp, c, _f64(A.val), rpu, cu, vu)
+    return SimpleNamespace(n_rows=A.n_rows, n_cols=A.n_cols, row_ptr=rpu, col=cu, val=vu, nnz=nu)
+
+
+def sym_spmv(U, x):
+    """y = (U + U^T - diag U) x from the upper triangle U."""
+    out = np.zeros(U.n_rows)
+    lib().orc_sym_spmv(U.n_rows, _i32(U.row_ptr), _i32(U.col), _f64(U.val), _f64(x), out)
     return out

@@ -750,3 +750,48 @@ void orc_psell_spmv(int64_t n_rows, const int32_t *rlen, const int32_t *blk_ptr,
             }
     }
 }
+
+/* ------------------------------------------------------------------------
+ * Symmetric SpMVM from the upper triangle (Sect. 3.2 names the option of
+ * using the symmetry of the Hamiltonian to save data transfer and does not
+ * pursue it).  U holds the entries with col >= row of a symmetric A, so
+ * A = U + U^T - diag(U):
+ *     y_i = sum_{j>=i} u_ij x_j + sum_{k<i} u_ki x_k.
+ * The loop walks U row by row; every off-diagonal u_ij adds u_ij x_j to
+ * y_i and u_ij x_i to y_j.
+ * ---------------------------------------------------------------------- */
+int64_t orc_upper_count(int64_t n_rows, const int32_t *row_ptr, const int32_t *col_idx)
+{
+    int64_t c = 0;
+    for (int64_t i = 0; i < n_rows; ++i)
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) c += col_idx[e] >= i;
+    return c;
+}
+
+void orc_upper_extract(int64_t n_rows, const int32_t *row_ptr, const int32_t *col_idx, const double *val,
+                       int32_t *row_ptr_u, int32_t *col_u, double *val_u)
+{
+    int64_t pos = 0;
+    row_ptr_u[0] = 0;
+    for (int64_t i = 0; i < n_rows; ++i) {
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            if (col_idx[e] >= i) {
+                col_u[pos] = col_idx[e];
+                val_u[pos] = val[e];
+                ++pos;
+            }
+        row_ptr_u[i + 1] = (int32_t)pos;
+    }
+}
+
+void orc_sym_spmv(int64_t n_rows, const int32_t *row_ptr_u, const int32_t *col_u, const double *val_u,
+                  const double *invec, double *resvec)
+{
+    for (int64_t i = 0; i < n_rows; ++i) resvec[i] = 0.0;
+    for (int64_t i = 0; i < n_rows; ++i)
+        for (int64_t e = row_ptr_u[i]; e < row_ptr_u[i + 1]; ++e) {
+            int64_t j = col_u[e];
+            resvec[i] = resvec[i] + val_u[e] * invec[j];
+            if (j != i) resvec[j] = resvec[j] + val_u[e] * invec[i];
+        }
+}

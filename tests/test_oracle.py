@@ -748,3 +748,53 @@ def test_psell_pairs_long_with_short():
     assert np.all(a >= b)
     tot = a + b
     assert tot.std(axis=1).mean() < 0.5 * P.rlen[:len(P.rlen) // 64 * 64].reshape(-1, 64).std(axis=1).mean()
+
+
+# --------------------------------------------------------------------------
+# Symmetric SpMVM from the upper triangle (Sect. 3.2's unused symmetry)
+# --------------------------------------------------------------------------
+
+def symmetric_random(n, seed, density):
+    B = S.small_random(n, n, seed, density=density)
+    D = B.to_dense()
+    D = D + D.T  # symmetric values
+    r, c = np.nonzero(D)
+    return S.from_coo(n, n, r, c, D[r, c])
+
+
+def test_upper_extract_is_triu():
+    A = symmetric_random(300, 5, 0.03)
+    U = O.upper(A)
+    Ud = np.zeros((300, 300))
+    rows = np.repeat(np.arange(300), np.diff(U.row_ptr))
+    Ud[rows, U.col] = U.val
+    assert np.array_equal(Ud, np.triu(A.to_dense()))
+    assert U.nnz == np.count_nonzero(np.triu(A.to_dense()))
+
+
+@pytest.mark.parametrize("n", [1, 2, 57, 300])
+def test_sym_spmv_equals_full_product(n):
+    A = symmetric_random(n, 6 + n, min(0.5, 8.0 / n))
+    x = S.vector(n, 7)
+    U = O.upper(A)
+    y = O.sym_spmv(U, x)
+    D = A.to_dense()
+    assert np.all(np.abs(y - D @ x) <= 1e-14 * (np.abs(D) @ np.abs(x)) + 1e-300)
+    Ai = S.integer_values(A, 8, 1000)
+    Di = Ai.to_dense()
+    Di = np.triu(Di) + np.triu(Di, 1).T  # integer symmetric values
+    r, c = np.nonzero(Di)
+    Ai = S.from_coo(n, n, r, c, Di[r, c])
+    xi = S.int_vector(n, 9, 1000)
+    assert np.array_equal(O.sym_spmv(O.upper(Ai), xi), (Di.astype(np.int64) @ xi.astype(np.int64)).astype(float))
+
+
+def test_sym_spmv_hh_like_matches_crs():
+    """The HH-like stand-in is symmetric by construction (mirrored pattern,
+    equal values): the upper-triangle product equals the full CRS product."""
+    A = S.hh_like(20_000, 1)
+    x = S.vector(A.n_rows, 3)
+    ref, s = O.crs_spmv_exact(A, x)
+    U = O.upper(A)
+    assert 2 * U.nnz - A.n_rows == A.nnz  # every off-diagonal entry has its mirror
+    assert np.all(np.abs(O.sym_spmv(U, x) - ref) <= 1e-14 * s)
