@@ -354,6 +354,8 @@ def run_ours(args):
         }
         if not args.no_extras:
             result["fp32"] = fp32_numbers(M, A, x, y, dev, time_launches, table[kname]["ms"])
+            torch.cuda.empty_cache()
+            result["symmetric"] = symmetric_numbers(M, A, x, dev, time_launches, table[kname]["ms"])
             del table
             torch.cuda.empty_cache()
             result["batched"] = batched_speedups(dev, time_launches)
@@ -417,6 +419,22 @@ def fp32_numbers(M, A, x, y64, dev, time_launches, ms64):
             "max_err_over_sum_abs_compensated": float(((yc - ref).abs() / den).max()),
             "max_err_over_sum_abs_plain": float(((yp - ref).abs() / den).max()),
             "note": "error of FP32 data and FP32 vector against the FP64 product of the FP64 data"}
+
+
+def symmetric_numbers(M, A, x, dev, time_launches, ms_full):
+    """The product from the upper triangle only (FP64 atomic scatter of the
+    transposed half) on the same matrix: its time against the full-storage
+    step, and the entries it reads."""
+    import torch
+    U = M.upper()
+    y = torch.zeros(A.n_rows, dtype=torch.float64, device=dev)
+    out = {"nnz_upper": U.nnz, "nnz_full": A.nnz, "full_step_ms": ms_full}
+    for name, H in (("CRS upper", U), ("SELL upper row_only w=128 u=4", U.to_jds("SELL", "row_only", window=128,
+                                                                                 unroll=4))):
+        t = statistics.median(time_launches(lambda: H.spmv_symmetric(x, out=y), 10))
+        out[name] = {"ms": round(t, 4), "gflops": round(2.0 * A.nnz / (t * 1e-3) / 1e9, 1),
+                     "speedup_vs_full": round(ms_full / t, 3)}
+    return out
 
 
 def small_numbers(dev, time_launches):

@@ -24,7 +24,9 @@
  *     on `stream`.  Device-side checks (validation, bounded waits) report
  *     into a caller-provided int32 status word in device memory.
  *   - All kernels are deterministic: the same inputs give bit-identical
- *     outputs on every run (no floating-point atomics).
+ *     outputs on every run (no floating-point atomics) -- except
+ *     gbsp_spmv_symmetric, whose FP64 atomic adds make it reproducible only
+ *     within rounding.
  */
 #ifndef GBSPMV_H
 #define GBSPMV_H
@@ -456,6 +458,42 @@ gbsp_status gbsp_gather_sum(int32_t op, int32_t access, int64_t n, int64_t strid
                             const double *d_a, const double *d_b, int64_t len_b,
                             const int32_t *d_ind, double *d_partials, int32_t n_partials,
                             double *d_out, int32_t *d_status, void *stream);
+
+/* --------------------------------------------- symmetric SpMVM (one triangle) -- */
+
+/* The Hamiltonian of Sect. 3.2 is symmetric, which the paper notes would
+ * allow a further saving of data transfer and does not pursue.  These calls
+ * store only the upper triangle U (col >= row) of a square CRS matrix and
+ * apply it as A = U + U^T - diag(U), reading half of the off-diagonal
+ * entries.
+ *
+ * gbsp_upper_workspace: device scratch bytes gbsp_upper_plan needs.
+ * gbsp_upper_plan: counts the upper entries of each row into d_row_ptr_u
+ *   (int32 [n_rows+1], caller memory) and scans them, so d_row_ptr_u is U's
+ *   row_ptr; *nnz_upper = its last entry.  Synchronises `stream`.
+ * gbsp_upper_build: fills d_col_u [nnz_upper] and d_val_u [nnz_upper] (the
+ *   CRS dtype) with the upper entries in their CRS order and returns a CRS
+ *   handle over (d_row_ptr_u, d_col_u, d_val_u), borrowed as usual.
+ * Errors: GBSP_ERR_UNSUPPORTED for a non-square matrix, GBSP_ERR_ARG for
+ * NULL or undersized buffers. */
+gbsp_status gbsp_upper_workspace(int64_t n_rows, int64_t *bytes);
+gbsp_status gbsp_upper_plan(gbsp_handle crs, int32_t *d_row_ptr_u, void *d_ws, int64_t ws_bytes, void *stream,
+                            int64_t *nnz_upper);
+gbsp_status gbsp_upper_build(gbsp_handle crs, const int32_t *d_row_ptr_u, int32_t *d_col_u, void *d_val_u,
+                             int64_t nnz_upper, void *stream, gbsp_handle *out);
+
+/* y = (S + S^T - diag S) x for the stored entries S of handle `S` -- A x
+ * when S holds the upper triangle of a symmetric A.  S: a CRS handle
+ * (thread per row) or a SELL handle with the row-only permutation (warp per
+ * 32-row block; vectors in the original basis either way).  FP64 only.
+ * Each stored off-diagonal s_ij adds s_ij x_j to y_i and s_ij x_i to y_j;
+ * updates of y are FP64 atomic adds, so y is first zeroed (accumulate = 0)
+ * or added to (accumulate = 1), and the summation order -- hence the last
+ * bits -- may differ between runs; exact when all partial sums are.
+ * Asynchronous on `stream` (a memset and one kernel).
+ * Errors: GBSP_ERR_UNSUPPORTED for FP32 or other formats, GBSP_ERR_ARG for
+ * NULL vectors or a non-square handle. */
+gbsp_status gbsp_spmv_symmetric(gbsp_handle S, const void *d_x, void *d_y, int32_t accumulate, void *stream);
 
 /* -------------------------------------------------- access-pattern analysis -- */
 

@@ -104,6 +104,10 @@ SIGNATURES = {
                                       c_vp]),
     "gbsp_gather_partials": (c_i32, [c_i64, ctypes.POINTER(c_i32)]),
     "gbsp_stride_hist": (c_i32, [c_vp, c_i64, c_vp, c_vp]),
+    "gbsp_upper_workspace": (c_i32, [c_i64, ctypes.POINTER(c_i64)]),
+    "gbsp_upper_plan": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(c_i64)]),
+    "gbsp_upper_build": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(c_vp)]),
+    "gbsp_spmv_symmetric": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_vp]),
     "gbsp_warp_sectors": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_vp]),
     "gbsp_gather_sum": (c_i32, [c_i32, c_i32, c_i64, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_i32, c_vp,
                                 c_vp, c_vp]),

@@ -97,11 +97,11 @@ __global__ void scan_apply(const int32_t *in, int64_t n, const int32_t *__restri
     if (total_out && base < n && base + kScanPer >= n) *total_out = run;
 }
 
-static int64_t scan_ws_bytes(int64_t n) { return (ceil_div(std::max<int64_t>(n, 1), kScanTile) + 1) * 4; }
+int64_t scan_ws_bytes(int64_t n) { return (ceil_div(std::max<int64_t>(n, 1), kScanTile) + 1) * 4; }
 
 // out[0..n) = exclusive scan of in[0..n); out[n] = total if total_out given
 // (total_out may point at out + n).  in and out may alias.
-static gbsp_status scan_exclusive(const int32_t *in, int64_t n, int32_t *out, int32_t *total_out,
+gbsp_status scan_exclusive(const int32_t *in, int64_t n, int32_t *out, int32_t *total_out,
                                   int32_t *ws, cudaStream_t s) {
     if (n == 0) {
         if (total_out) GBSP_CUDA(cudaMemsetAsync(total_out, 0, 4, s));

@@ -98,6 +98,12 @@ inline int num_sms() {
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// device exclusive scan of int32 (convert.cu): out[0..n) = exclusive scan of
+// in, *total_out = the total when given; ws holds scan_ws_bytes(n) bytes
+int64_t scan_ws_bytes(int64_t n);
+gbsp_status scan_exclusive(const int32_t *in, int64_t n, int32_t *out, int32_t *total_out, int32_t *ws,
+                           cudaStream_t s);
+
 // launchers implemented in crs.cu -----------------------------------------
 struct VecArgs {
     const void *x;

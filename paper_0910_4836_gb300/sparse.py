@@ -94,6 +94,17 @@ class _Product(_Handle):
             raise ValueError("spmv takes a 1-D vector; use spmm for several")
         return self.spmm(x, out, accumulate, transpose, basis, stream)
 
+    def spmv_symmetric(self, x: torch.Tensor, out: torch.Tensor | None = None, accumulate: bool = False,
+                       stream=None) -> torch.Tensor:
+        """y = (S + S^T - diag S) x for the stored triangle S (FP64 atomics:
+        reproducible within rounding only).  CRS or row-only SELL handles."""
+        x = _need_cuda(x, "x", self.dtype)
+        if out is None:
+            out = torch.zeros(self.n_rows, dtype=self.dtype, device=x.device)
+        L.check(L.load().gbsp_spmv_symmetric(self._h, _vp(x), _vp(out), int(accumulate), _stream(stream)),
+                "gbsp_spmv_symmetric")
+        return out
+
     def set_kernel(self, kernel: str = "vector", lanes: int = 0, rows_per_warp: int = 0,
                    tile: int = 0, rhs_tile: int = 0, compensated: bool | None = None) -> None:
         o = L.KernelOpts()
@@ -209,6 +220,29 @@ class CRSMatrix(_Product):
         T._source = self
         self._transpose = T
         return T
+
+    def upper(self, stream=None) -> "CRSMatrix":
+        """CRS of the upper triangle (col >= row, CRS order kept) of this
+        square matrix, for ``spmv_symmetric``."""
+        lib = L.load()
+        dev = self._device
+        ws = ctypes.c_int64()
+        L.check(lib.gbsp_upper_workspace(self.n_rows, ctypes.byref(ws)), "gbsp_upper_workspace")
+        row_ptr_u = torch.empty(self.n_rows + 1, dtype=torch.int32, device=dev)
+        work = torch.empty(max(ws.value, 1), dtype=torch.uint8, device=dev)
+        nnz_u = ctypes.c_int64()
+        L.check(lib.gbsp_upper_plan(self._h, _vp(row_ptr_u), _vp(work), ws.value, _stream(stream),
+                                    ctypes.byref(nnz_u)), "gbsp_upper_plan")
+        col_u = torch.empty(nnz_u.value, dtype=torch.int32, device=dev)
+        val_u = torch.empty(nnz_u.value, dtype=self.dtype, device=dev)
+        U = CRSMatrix.__new__(CRSMatrix)
+        _Handle.__init__(U)
+        L.check(lib.gbsp_upper_build(self._h, _vp(row_ptr_u), _vp(col_u), _vp(val_u), nnz_u.value,
+                                     _stream(stream), ctypes.byref(U._h)), "gbsp_upper_build")
+        U.row_ptr, U.col, U.val = row_ptr_u, col_u, val_u
+        U.dtype, U.n_rows, U.n_cols, U.nnz = self.dtype, self.n_rows, self.n_cols, nnz_u.value
+        U._device, U._tile_table, U._transpose = dev, None, None
+        return U
 
     def attach_transpose(self, at: "_Product") -> None:
         L.check(L.load().gbsp_attach_transpose(self._h, at.handle), "gbsp_attach_transpose")
