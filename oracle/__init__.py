@@ -72,6 +72,9 @@ def lib():
             "orc_upper_count": [_I64, _I32, _I32],
             "orc_upper_extract": [_I64, _I32, _I32, _F64, _I32, _I32, _F64],
             "orc_sym_spmv": [_I64, _I32, _I32, _F64, _F64, _F64],
+            "orc_dia_select": [_I64, _I64, _I32, _I32, _I64, ctypes.c_double, _I32],
+            "orc_dia_build": [_I64, _I32, _I32, _F64, _I64, _I32, _F64, _I32, _I32, _F64],
+            "orc_dia_spmv": [_I64, _I64, _I64, _I32, _F64, _I32, _I32, _F64, _F64, _F64],
             "orc_stride_hist": [_I64, _I32, _I64P],
             "orc_warp_sectors_crs": [_I64, _I32, _I32, _INT, _INT, _I64P],
             "orc_warp_sectors_jds": [_I64, _I64, _I32, _I32, _INT, _I64P],
@@ -81,7 +84,8 @@ def lib():
         for name, args in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args
-            fn.restype = _I64 if name in ("orc_max_row_len", "orc_jds_build", "orc_upper_count") else (
+            fn.restype = _I64 if name in ("orc_max_row_len", "orc_jds_build", "orc_upper_count",
+                                          "orc_dia_select", "orc_dia_build") else (
                 _INT if name in ("orc_num_threads", "orc_sell_build", "orc_psell_build") else (
                     ctypes.c_double if name == "orc_gather_sum" else None))
         _lib = L
@@ -447,4 +451,39 @@ def sym_spmv(U, x):
     """y = (U + U^T - diag U) x from the upper triangle U."""
     out = np.zeros(U.n_rows)
     lib().orc_sym_spmv(U.n_rows, _i32(U.row_ptr), _i32(U.col), _f64(U.val), _f64(x), out)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Hybrid storage: dense secondary diagonals in DIA form + remainder CRS
+# ---------------------------------------------------------------------------
+
+def dia_select(A, max_diags=16, min_fill=2.0 / 3.0):
+    offs = np.zeros(max(max_diags, 1), np.int32)
+    m = int(lib().orc_dia_select(A.n_rows, A.n_cols, _i32(A.row_ptr), _i32(A.col), max_diags, min_fill, offs))
+    return offs[:m].copy()
+
+
+def dia_build(A, offs):
+    """(dia [len(offs), n_rows], remainder CRS as a SimpleNamespace)."""
+    from types import SimpleNamespace
+    offs = _i32(offs)
+    nd = len(offs)
+    dia = np.zeros(nd * A.n_rows)
+    rp = np.zeros(A.n_rows + 1, np.int32)
+    col = np.zeros(max(A.nnz, 1), np.int32)
+    val = np.zeros(max(A.nnz, 1))
+    m = int(lib().orc_dia_build(A.n_rows, _i32(A.row_ptr), _i32(A.col), _f64(A.val), nd,
+                                offs if nd else np.zeros(1, np.int32), dia if nd else np.zeros(1), rp, col, val))
+    rem = SimpleNamespace(n_rows=A.n_rows, n_cols=A.n_cols, row_ptr=rp, col=col[:m].copy(), val=val[:m].copy(),
+                          nnz=m)
+    return dia.reshape(nd, A.n_rows), rem
+
+
+def dia_spmv(offs, dia, rem, x):
+    out = np.zeros(rem.n_rows)
+    nd = len(offs)
+    lib().orc_dia_spmv(rem.n_rows, rem.n_cols, nd, _i32(offs) if nd else np.zeros(1, np.int32),
+                       _f64(dia.ravel()) if nd else np.zeros(1), _i32(rem.row_ptr), _i32(rem.col) if rem.nnz else
+                       np.zeros(1, np.int32), _f64(rem.val) if rem.nnz else np.zeros(1), _f64(x), out)
     return out

@@ -795,3 +795,99 @@ void orc_sym_spmv(int64_t n_rows, const int32_t *row_ptr_u, const int32_t *col_u
             if (j != i) resvec[j] = resvec[j] + val_u[e] * invec[i];
         }
 }
+
+/* ------------------------------------------------------------------------
+ * Hybrid storage (Sect. 3.2: most entries of the Hamiltonian sit in a few
+ * dense outer secondary diagonals, "candidates for special treatment by a
+ * dense storage scheme"): selected diagonals in DIA form, the rest in CRS.
+ *
+ * Diagonal of offset o = col - row; its length is the number of in-matrix
+ * positions (i, i+o).  fill(o) = entries with offset o / length.  The
+ * offsets with fill >= min_fill are ranked by entry count (descending),
+ * then |o|, then o, and the first max_diags are kept.  DIA values:
+ * dia[k*n_rows + i] = the first entry (CRS order) of row i with offset o_k,
+ * 0 where none.  Every other entry stays in the remainder CRS, in CRS order.
+ * Product: y_i = (sum over k ascending of dia[k][i] x[i+o_k], in-range
+ * columns only) + (the remainder row's sum in CRS order).
+ * ---------------------------------------------------------------------- */
+static int64_t diag_length(int64_t n_rows, int64_t n_cols, int64_t o)
+{
+    int64_t lo = o < 0 ? -o : 0;                              /* first row */
+    int64_t hi = n_rows < n_cols - o ? n_rows : n_cols - o;   /* one past the last row */
+    return hi > lo ? hi - lo : 0;
+}
+
+/* Selected offsets into offs_out (at most max_diags); returns their number. */
+int64_t orc_dia_select(int64_t n_rows, int64_t n_cols, const int32_t *row_ptr, const int32_t *col_idx,
+                       int64_t max_diags, double min_fill, int32_t *offs_out)
+{
+    int64_t span = n_rows + n_cols;  /* offsets -(n_rows-1) .. n_cols-1 */
+    int64_t *cnt = (int64_t *)calloc((size_t)(span > 0 ? span : 1), sizeof(int64_t));
+    for (int64_t i = 0; i < n_rows; ++i)
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) cnt[(int64_t)col_idx[e] - i + n_rows] += 1;
+    int64_t m = 0;
+    for (int64_t k = 0; k < max_diags; ++k) {
+        /* the best remaining offset by (count desc, |o| asc, o asc) */
+        int64_t best = -1;
+        for (int64_t b = 0; b < span; ++b) {
+            if (cnt[b] <= 0) continue;
+            int64_t o = b - n_rows;
+            if ((double)cnt[b] < min_fill * (double)diag_length(n_rows, n_cols, o)) continue;
+            if (best < 0) { best = b; continue; }
+            int64_t ob = best - n_rows;
+            int64_t ao = o < 0 ? -o : o, aob = ob < 0 ? -ob : ob;
+            if (cnt[b] > cnt[best] || (cnt[b] == cnt[best] && (ao < aob || (ao == aob && o < ob)))) best = b;
+        }
+        if (best < 0) break;
+        offs_out[m++] = (int32_t)(best - n_rows);
+        cnt[best] = 0;
+    }
+    free(cnt);
+    return m;
+}
+
+/* DIA values [n_diags][n_rows] and the remainder CRS (row_ptr_rem [n_rows+1],
+ * col_rem / val_rem sized for nnz); returns the remainder's entry count. */
+int64_t orc_dia_build(int64_t n_rows, const int32_t *row_ptr, const int32_t *col_idx, const double *val,
+                      int64_t n_diags, const int32_t *offs, double *dia, int32_t *row_ptr_rem,
+                      int32_t *col_rem, double *val_rem)
+{
+    for (int64_t q = 0; q < n_diags * n_rows; ++q) dia[q] = 0.0;
+    char *taken = (char *)calloc((size_t)(n_diags > 0 ? n_diags : 1), 1);
+    int64_t pos = 0;
+    row_ptr_rem[0] = 0;
+    for (int64_t i = 0; i < n_rows; ++i) {
+        for (int64_t k = 0; k < n_diags; ++k) taken[k] = 0;
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            int64_t o = (int64_t)col_idx[e] - i, k = 0;
+            while (k < n_diags && (offs[k] != o || taken[k])) ++k;
+            if (k < n_diags) {
+                dia[k * n_rows + i] = val[e];
+                taken[k] = 1;
+            } else {
+                col_rem[pos] = col_idx[e];
+                val_rem[pos] = val[e];
+                ++pos;
+            }
+        }
+        row_ptr_rem[i + 1] = (int32_t)pos;
+    }
+    free(taken);
+    return pos;
+}
+
+void orc_dia_spmv(int64_t n_rows, int64_t n_cols, int64_t n_diags, const int32_t *offs, const double *dia,
+                  const int32_t *row_ptr_rem, const int32_t *col_rem, const double *val_rem,
+                  const double *invec, double *resvec)
+{
+    for (int64_t i = 0; i < n_rows; ++i) {
+        double d = 0.0;
+        for (int64_t k = 0; k < n_diags; ++k) {
+            int64_t j = i + offs[k];
+            if (j >= 0 && j < n_cols) d = d + dia[k * n_rows + i] * invec[j];
+        }
+        double r = 0.0;
+        for (int64_t e = row_ptr_rem[i]; e < row_ptr_rem[i + 1]; ++e) r = r + val_rem[e] * invec[col_rem[e]];
+        resvec[i] = d + r;
+    }
+}

@@ -270,6 +270,53 @@ def hh_like(n: int = 6_000_000, seed: int = 1) -> CRS:
     return CRS(n, n, row_ptr.astype(np.int32), c.astype(np.int32), val, f"hh_like_{n}")
 
 
+HH_OUTER_OFFSETS = tuple(65536 * k for k in range(1, 7))
+
+
+def hh_diagonals(n: int = 6_000_000, seed: int = 5, fill: float = 0.8, band: int = 400) -> CRS:
+    """Symmetric stand-in that follows Sect. 3.2's description of the
+    Holstein-Hubbard matrix literally: about 60% of the entries in the twelve
+    outermost secondary diagonals, the rest scattered evenly over a band of
+    several hundred diagonals.
+
+    Six upper offsets 65536k (k = 1..6) each hold an entry in row i with
+    probability `fill`; row i also draws U{1..4} upper entries at offsets
+    uniform in [1, band].  Columns >= n are dropped, duplicates removed, the
+    pattern mirrored with equal values normal(0,1), and a normal(0,1)
+    diagonal added: at n = 6e6 about 15 entries a row, 60% of them on the
+    twelve outer diagonals."""
+    i_all = np.arange(n, dtype=np.int64)
+    parts_i, parts_j = [], []
+    for k, o in enumerate(HH_OUTER_OFFSETS):
+        keep = (uniform01(seed, 20 + k, i_all) < fill) & (i_all + o < n)
+        parts_i.append(i_all[keep])
+        parts_j.append(i_all[keep] + o)
+    m = randint(seed, 30, i_all, 1, 4)
+    i = np.repeat(i_all, m)
+    t = np.arange(i.size, dtype=np.int64)
+    j = i + randint(seed, 31, t, 1, band)
+    keep = j < n
+    parts_i.append(i[keep])
+    parts_j.append(j[keep])
+    i = np.concatenate(parts_i)
+    j = np.concatenate(parts_j)
+    upper = _sorted_unique(i * n + j)
+    del i, j, keep, t, parts_i, parts_j
+    ui, uj = upper // n, upper % n
+    key = np.concatenate([upper, uj * n + ui, i_all * n + i_all])
+    del ui, uj
+    key.sort()
+    r = key // n
+    c = key - r * n
+    lo = np.minimum(r, c)
+    hi = np.maximum(r, c)
+    val = np.where(r == c, normal(seed, 33, r), normal(seed, 32, lo * n + hi))
+    counts = np.bincount(r, minlength=n)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    return CRS(n, n, row_ptr.astype(np.int32), c.astype(np.int32), val, f"hh_diagonals_{n}")
+
+
 def zipf_lengths(n: int, seed: int, s: float = 2.0, lmin: int = 1, lmax: int = 5000,
                  stream: int = 11) -> np.ndarray:
     """Row lengths from Zipf(s) truncated (renormalised) to [lmin, lmax]."""

@@ -798,3 +798,90 @@ def test_sym_spmv_hh_like_matches_crs():
     U = O.upper(A)
     assert 2 * U.nnz - A.n_rows == A.nnz  # every off-diagonal entry has its mirror
     assert np.all(np.abs(O.sym_spmv(U, x) - ref) <= 1e-14 * s)
+
+
+# --------------------------------------------------------------------------
+# Hybrid storage: dense secondary diagonals in DIA form + remainder CRS
+# (Sect. 3.2's "special treatment by a dense storage scheme")
+# --------------------------------------------------------------------------
+
+def dense_of(offs, dia, rem, n_cols):
+    n = rem.n_rows
+    D = np.zeros((n, n_cols))
+    for k, o in enumerate(offs):
+        for i in range(n):
+            if 0 <= i + o < n_cols:
+                D[i, i + o] += dia[k, i]
+    rows = np.repeat(np.arange(n), np.diff(rem.row_ptr))
+    np.add.at(D, (rows, rem.col), rem.val)
+    return D
+
+
+def test_dia_laplacian_closed_form():
+    """nx x ny Laplacian: diagonal n entries, offsets +-1 hold (nx-1) ny,
+    offsets +-nx hold n - nx; all five are full enough, nothing remains,
+    and on integer data the product is exact."""
+    nx, ny = 12, 9
+    A = S.laplace2d(nx, ny)
+    n = nx * ny
+    offs = O.dia_select(A, 8, 0.5)
+    assert list(offs) == [0, -1, 1, -nx, nx]  # counts n, (nx-1)ny twice, n-nx twice
+    dia, rem = O.dia_build(A, offs)
+    assert rem.nnz == 0
+    assert np.array_equal(dense_of(offs, dia, rem, n), A.to_dense())
+    assert np.count_nonzero(dia[1]) == (nx - 1) * ny and np.count_nonzero(dia[3]) == n - nx
+    x = S.int_vector(n, 3, 1000)
+    assert np.array_equal(O.dia_spmv(offs, dia, rem, x), A.to_dense() @ x)
+
+
+def test_dia_none_selected_is_crs():
+    A = S.small_random(200, 150, 4, density=0.05, empty_rows=0.2)
+    offs = O.dia_select(A, 8, 1.01)  # no diagonal can be fuller than 1
+    assert len(offs) == 0
+    dia, rem = O.dia_build(A, offs)
+    assert np.array_equal(rem.row_ptr, A.row_ptr) and np.array_equal(rem.col, A.col)
+    x = S.vector(150, 5)
+    assert np.array_equal(O.dia_spmv(offs, dia, rem, x), O.crs_spmv(A, x))
+
+
+def test_dia_planted_diagonals_and_duplicates():
+    """Planted diagonals of fill 0.9 are found (and a sparse band is not);
+    DIA + remainder reproduce A, including a duplicated entry whose second
+    copy stays in the remainder."""
+    n = 400
+    rng_rows, rng_cols, vals = [], [], []
+    for k, o in enumerate((-50, 7, 123)):
+        i = np.arange(max(0, -o), min(n, n - o))
+        keep = S.uniform01(6, 40 + k, i) < 0.9
+        rng_rows += list(i[keep]); rng_cols += list(i[keep] + o)
+    i = np.arange(n)
+    j = S.randint(6, 50, i, 0, n - 1)
+    rng_rows += list(i); rng_cols += list(j)
+    vals = S.uniform(6, 51, np.arange(len(rng_rows)), -1, 1)
+    A = S.from_coo(n, n, rng_rows, rng_cols, vals, dedupe=False)
+    offs = O.dia_select(A, 8, 0.7)
+    assert sorted(offs) == [-50, 7, 123]
+    dia, rem = O.dia_build(A, offs)
+    assert np.allclose(dense_of(offs, dia, rem, n), _dense_sum(A), rtol=0, atol=1e-15)
+    x = S.vector(n, 7)
+    ref, s = O.crs_spmv_exact(A, x)
+    assert np.all(np.abs(O.dia_spmv(offs, dia, rem, x) - ref) <= 1e-14 * s)
+
+
+def _dense_sum(A):
+    D = np.zeros((A.n_rows, A.n_cols))
+    np.add.at(D, (A.row_ids(), A.col), A.val)
+    return D
+
+
+def test_dia_hh_diagonals_selects_the_outer_diagonals():
+    A = S.hh_diagonals(200_000, 5)
+    offs = O.dia_select(A, 16, 2.0 / 3.0)
+    inside = [o for o in S.HH_OUTER_OFFSETS if o < A.n_rows]  # 65536, 131072, 196608
+    assert sorted(np.abs(offs[1:]).tolist()) == sorted(2 * inside)
+    assert offs[0] == 0
+    dia, rem = O.dia_build(A, offs)
+    assert rem.nnz + np.count_nonzero(dia) == A.nnz
+    x = S.vector(A.n_rows, 8)
+    ref, s = O.crs_spmv_exact(A, x)
+    assert np.all(np.abs(O.dia_spmv(offs, dia, rem, x) - ref) <= 1e-14 * s)
