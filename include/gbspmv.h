@@ -459,6 +459,52 @@ gbsp_status gbsp_gather_sum(int32_t op, int32_t access, int64_t n, int64_t strid
                             const int32_t *d_ind, double *d_partials, int32_t n_partials,
                             double *d_out, int32_t *d_status, void *stream);
 
+/* ------------------------------------- hybrid storage: DIA + remainder -- */
+
+/* Sect. 3.2 observes that most entries of the Holstein-Hubbard matrix sit
+ * in a few dense outer secondary diagonals, each "a potential candidate for
+ * special treatment by a dense storage scheme", and leaves such a hybrid
+ * unbuilt.  Here the selected diagonals go to DIA storage (one value per
+ * row, zeros where the diagonal has no entry, no column index) and every
+ * other entry to a remainder CRS matrix, which may then be converted to any
+ * format of this library.  The product is y = DIA x followed by the
+ * remainder's product with accumulate = 1, so y_i = (DIA sum) + (remainder
+ * sum).
+ *
+ * Diagonal of offset o = col - row; its length is the number of in-matrix
+ * positions (i, i+o); fill = its entries / its length.  gbsp_dia_plan keeps
+ * the offsets with fill >= min_fill (2/3 is the FP64 break-even: 8 bytes a
+ * DIA slot against 12 an entry), ranked by entry count (descending), then
+ * |o|, then o, at most max_diags (<= GBSP_DIA_MAX).  In each row, the first
+ * entry (CRS order) on a selected diagonal goes to DIA; the rest stay.
+ *
+ * gbsp_dia_plan_workspace: device scratch bytes of gbsp_dia_plan.
+ * gbsp_dia_plan: an exact offset histogram on the device, read back
+ *   (4 (n_rows + n_cols) bytes) for the selection; fills d_row_ptr_rem
+ *   (int32 [n_rows+1], caller memory) with the remainder's row_ptr and *out
+ *   with the chosen offsets and counts.  Synchronises `stream`.
+ * gbsp_dia_build: d_dia [n_diags * n_rows] (dtype of the CRS; diagonal k
+ *   at d_dia + k*n_rows, entry i = row i), d_offsets int32 [n_diags], and the
+ *   remainder's d_col_rem [nnz_rem], d_val_rem [nnz_rem].  Returns a DIA
+ *   handle (gbsp_spmv / gbsp_spmm with k = 1, OP_N; it borrows d_dia and
+ *   d_offsets) and a CRS handle of the remainder.  Synchronises `stream`.
+ * Errors: GBSP_ERR_ARG for bad sizes or NULL buffers. */
+#define GBSP_DIA_MAX 64
+typedef struct {
+    int64_t n_rows, n_cols;
+    int32_t n_diags;                   /* diagonals selected */
+    int32_t offsets[GBSP_DIA_MAX];     /* their offsets, in rank order */
+    int64_t nnz_dia;                   /* entries moved to DIA */
+    int64_t nnz_rem;                   /* entries left in the remainder */
+} gbsp_dia_sizes;
+
+gbsp_status gbsp_dia_plan_workspace(gbsp_handle crs, int64_t *bytes);
+gbsp_status gbsp_dia_plan(gbsp_handle crs, int32_t max_diags, double min_fill, int32_t *d_row_ptr_rem,
+                          void *d_ws, int64_t ws_bytes, void *stream, gbsp_dia_sizes *out);
+gbsp_status gbsp_dia_build(gbsp_handle crs, const gbsp_dia_sizes *sizes, void *d_dia, int32_t *d_offsets,
+                           const int32_t *d_row_ptr_rem, int32_t *d_col_rem, void *d_val_rem, void *stream,
+                           gbsp_handle *dia_out, gbsp_handle *rem_out);
+
 /* --------------------------------------------- symmetric SpMVM (one triangle) -- */
 
 /* The Hamiltonian of Sect. 3.2 is symmetric, which the paper notes would

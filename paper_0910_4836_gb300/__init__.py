@@ -13,12 +13,12 @@ from __future__ import annotations
 import importlib
 
 __all__ = ["CRSMatrix", "JDSMatrix", "GbspError", "SpMVFunction", "power_apply", "Batch",
-           "gather_sum", "build", "synth"]
+           "gather_sum", "HybridMatrix", "build", "synth"]
 
 _LAZY = {
     "CRSMatrix": "sparse", "JDSMatrix": "sparse", "GbspError": "_lib",
     "SpMVFunction": "autograd", "power_apply": "autograd", "Batch": "batch",
-    "gather_sum": "gather",
+    "gather_sum": "gather", "HybridMatrix": "sparse",
 }
 
 

@@ -51,6 +51,14 @@ class JdsBuffers(ctypes.Structure):
                 ("blk_ptr", c_vp), ("workspace", c_vp), ("vmap", c_vp), ("rlen", c_vp)]
 
 
+DIA_MAX = 64
+
+
+class DiaSizes(ctypes.Structure):
+    _fields_ = [("n_rows", c_i64), ("n_cols", c_i64), ("n_diags", c_i32), ("offsets", c_i32 * DIA_MAX),
+                ("nnz_dia", c_i64), ("nnz_rem", c_i64)]
+
+
 class TransposeBuffers(ctypes.Structure):
     _fields_ = [("t_row_ptr", c_vp), ("t_col", c_vp), ("t_val", c_vp), ("tmap", c_vp),
                 ("workspace", c_vp)]
@@ -104,6 +112,10 @@ SIGNATURES = {
                                       c_vp]),
     "gbsp_gather_partials": (c_i32, [c_i64, ctypes.POINTER(c_i32)]),
     "gbsp_stride_hist": (c_i32, [c_vp, c_i64, c_vp, c_vp]),
+    "gbsp_dia_plan_workspace": (c_i32, [c_vp, ctypes.POINTER(c_i64)]),
+    "gbsp_dia_plan": (c_i32, [c_vp, c_i32, ctypes.c_double, c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(DiaSizes)]),
+    "gbsp_dia_build": (c_i32, [c_vp, ctypes.POINTER(DiaSizes), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
+                               ctypes.POINTER(c_vp), ctypes.POINTER(c_vp)]),
     "gbsp_upper_workspace": (c_i32, [c_i64, ctypes.POINTER(c_i64)]),
     "gbsp_upper_plan": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(c_i64)]),
     "gbsp_upper_build": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(c_vp)]),

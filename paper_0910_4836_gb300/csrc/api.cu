@@ -376,6 +376,7 @@ gbsp_status gbsp_spmm(gbsp_handle A, int32_t op, int32_t basis, int32_t k, const
     v.k = k;
     v.accumulate = accumulate ? 1 : 0;
     if (A->kind == KIND_CRS) return crs_launch(*A, v, s);
+    if (A->kind == KIND_DIA) return dia_launch(*A, v, s);
     if (basis == GBSP_BASIS_ORIGINAL) {
         v.y_perm = A->perm;
         v.x_perm = A->perm_mode == GBSP_PERM_SYMMETRIC ? A->perm : nullptr;

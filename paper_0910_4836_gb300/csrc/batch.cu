@@ -299,6 +299,10 @@ gbsp_status make_work(int32_t n, const gbsp_batch_item *items, int32_t chunk, cu
         const gbsp_batch_item &it = items[b];
         if (!it.A) return arg_error("gbsp_batch: NULL handle in item");
         const Mat &A = *it.A;
+        if (A.kind == KIND_DIA) {
+            set_error("gbsp_batch: DIA handles are not batched");
+            return GBSP_ERR_UNSUPPORTED;
+        }
         if (A.kind == KIND_JDS && A.format == GBSP_PSELL) {
             set_error("gbsp_batch: PSELL handles are not batched; use SELL");
             return GBSP_ERR_UNSUPPORTED;

@@ -12,7 +12,7 @@
 
 namespace gbsp {
 
-enum HandleKind { KIND_CRS = 0, KIND_JDS = 1 };
+enum HandleKind { KIND_CRS = 0, KIND_JDS = 1, KIND_DIA = 2 };
 
 struct Mat {
     int kind = KIND_CRS;
@@ -114,6 +114,10 @@ struct VecArgs {
     const int32_t *x_perm;   // optional: x index = x_perm[col]
     const int32_t *y_perm;   // optional: y row = y_perm[row]
 };
+
+// DIA part of the hybrid storage (dia.cu): y (+)= sum_k dia[k][i] x[i+o_k]
+gbsp_status dia_launch(const Mat &A, const VecArgs &v, cudaStream_t s);
+
 
 gbsp_status crs_launch(const Mat &A, const VecArgs &v, cudaStream_t s);
 gbsp_status crs_prepare_tiles(Mat &A, int32_t tile, int32_t *table, cudaStream_t s);

@@ -169,6 +169,10 @@ extern "C" gbsp_status gbsp_warp_sectors(gbsp_handle h, int32_t lanes, int32_t e
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned long long *hist = reinterpret_cast<unsigned long long *>(d_hist);
     const Mat &A = *h;
+    if (A.kind == KIND_DIA) {
+        set_error("gbsp_warp_sectors: a DIA handle reads x contiguously");
+        return GBSP_ERR_UNSUPPORTED;
+    }
     if (A.kind == KIND_CRS) {
         if (lanes < 1 || lanes > 32 || (lanes & (lanes - 1)))
             return arg_error("gbsp_warp_sectors: CRS lanes must be 1, 2, 4, 8, 16 or 32");

@@ -149,6 +149,10 @@ using namespace gbsp;
 extern "C" gbsp_status gbsp_autotune(gbsp_handle h, int32_t k, const void *d_X, void *d_Y, void *stream,
                                      gbsp_kernel_opts *best, float *best_ms) {
     if (!h || k < 1) return arg_error("gbsp_autotune: bad arguments");
+    if (h->kind == KIND_DIA) {
+        set_error("gbsp_autotune: a DIA handle has one kernel");
+        return GBSP_ERR_UNSUPPORTED;
+    }
     if (h->n_rows > 0 && (!d_X || !d_Y)) return arg_error("gbsp_autotune: NULL scratch vectors");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const TuneKey key = key_of(*h, k);

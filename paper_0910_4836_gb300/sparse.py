@@ -358,3 +358,62 @@ class JDSMatrix(_Product):
 
     def spmv_original(self, x: torch.Tensor, out=None, accumulate=False, stream=None):
         return self.spmv(x, out, accumulate, basis=L.BASIS_ORIGINAL, stream=stream)
+
+
+class DIAMatrix(_Product):
+    """The DIA part of a hybrid matrix: selected secondary diagonals, one
+    value per row (built by :class:`HybridMatrix`)."""
+
+
+class HybridMatrix:
+    """Dense secondary diagonals in DIA form plus the remainder (Sect. 3.2's
+    suggested hybrid): ``y = DIA x`` then the remainder's product added to
+    it.  The remainder is kept in CRS or converted to SELL-32-sigma with the
+    row-only permutation (vectors stay in the original basis)."""
+
+    def __init__(self, A: CRSMatrix, max_diags: int = 16, min_fill: float = 2.0 / 3.0,
+                 remainder: str = "SELL", window: int = 128, unroll: int = 4, stream=None):
+        lib = L.load()
+        dev = A._device
+        ws = ctypes.c_int64()
+        L.check(lib.gbsp_dia_plan_workspace(A.handle, ctypes.byref(ws)), "gbsp_dia_plan_workspace")
+        work = torch.empty(max(ws.value, 1), dtype=torch.uint8, device=dev)
+        row_ptr_rem = torch.empty(A.n_rows + 1, dtype=torch.int32, device=dev)
+        sz = L.DiaSizes()
+        L.check(lib.gbsp_dia_plan(A.handle, max_diags, float(min_fill), _vp(row_ptr_rem), _vp(work), ws.value,
+                                  _stream(stream), ctypes.byref(sz)), "gbsp_dia_plan")
+        del work
+        nd = sz.n_diags
+        self.offsets_host = [int(sz.offsets[k]) for k in range(nd)]
+        self.nnz_dia, self.nnz_rem = int(sz.nnz_dia), int(sz.nnz_rem)
+        self.dia = torch.empty((nd, A.n_rows), dtype=A.dtype, device=dev)
+        self.offsets = torch.empty(max(nd, 1), dtype=torch.int32, device=dev)
+        col_rem = torch.empty(self.nnz_rem, dtype=torch.int32, device=dev)
+        val_rem = torch.empty(self.nnz_rem, dtype=A.dtype, device=dev)
+        D = DIAMatrix.__new__(DIAMatrix)
+        _Handle.__init__(D)
+        R = CRSMatrix.__new__(CRSMatrix)
+        _Handle.__init__(R)
+        L.check(lib.gbsp_dia_build(A.handle, ctypes.byref(sz), _vp(self.dia), _vp(self.offsets), _vp(row_ptr_rem),
+                                   _vp(col_rem), _vp(val_rem), _stream(stream), ctypes.byref(D._h),
+                                   ctypes.byref(R._h)), "gbsp_dia_build")
+        D.n_rows, D.n_cols, D.dtype, D._device = A.n_rows, A.n_cols, A.dtype, dev
+        D._dia, D._offsets = self.dia, self.offsets
+        R.row_ptr, R.col, R.val = row_ptr_rem, col_rem, val_rem
+        R.dtype, R.n_rows, R.n_cols, R.nnz = A.dtype, A.n_rows, A.n_cols, self.nnz_rem
+        R._device, R._tile_table, R._transpose = dev, None, None
+        self.dia_part, self.remainder = D, R
+        self.n_rows, self.n_cols, self.dtype = A.n_rows, A.n_cols, A.dtype
+        self.rem_op = None
+        if self.nnz_rem > 0:
+            self.rem_op = R.to_jds("SELL", "row_only", window=window, unroll=unroll) if remainder == "SELL" else R
+
+    def spmv(self, x: torch.Tensor, out: torch.Tensor | None = None, accumulate: bool = False,
+             stream=None) -> torch.Tensor:
+        out = self.dia_part.spmv(x, out=out, accumulate=accumulate, stream=stream)
+        if self.rem_op is not None:
+            if isinstance(self.rem_op, JDSMatrix):
+                self.rem_op.spmv_original(x, out=out, accumulate=True, stream=stream)
+            else:
+                self.rem_op.spmv(x, out=out, accumulate=True, stream=stream)
+        return out
