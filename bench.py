@@ -162,20 +162,25 @@ def job_throughput(units_per_rank: float, world: int, max_ms: float) -> float:
     return world * units_per_rank / (max_ms * 1e-3)
 
 
+KERNEL_SOURCES = ("jds.cu", "accum.cuh")  # the JDS-family / SELL kernels, their loads and sums
+
+
 def kernel_source_hash():
+    """Hash of the files the step kernels and their launch setup are
+    compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0910_4836_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:12]
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
-# capture, keyed by the hash of the CRS kernel sources it was taken on; a
-# different hash means the kernel changed since and traffic is reported null.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the step kernel on the full
+# workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
+# a one-pass metric set), keyed by (config, kernel, source hash); a different
+# hash means the kernel changed since and traffic is reported null.
+NCU_TRAFFIC = {(1, "SELL row_only w=128 u=4", "aed63f5047e4"): 1144022016 + 40434688}
 
 
 # --------------------------------------------------------------- ours ------
@@ -210,14 +215,14 @@ def candidates(M, A, x, only=None):
     for t in (1024, 2048):
         out.append((f"CRS tiled {t}", M, x, crs_b, ("tiled", t)))
     for perm, w, u in (("row_only", 128, 2), ("row_only", 128, 4), ("row_only", 512, 4),
-                       ("row_only", 4096, 4), ("symmetric", 128, 4)):
+                       ("row_only", 4096, 4)):
         name = f"SELL {perm} w={w} u={u}"
         if want(name):
             G = M.to_jds("SELL", perm, window=w, unroll=u)
             xs = G.permute(x) if perm == "symmetric" else x
             gb = 12 * A.nnz + 4 * (G.n_blocks + 1) + 4 * A.n_rows + 8 * A.n_cols + 8 * A.n_rows
             out.append((name, G, xs, gb, ("fixed",)))
-    for perm, w, u in (("row_only", 64, 2), ("row_only", 64, 4), ("row_only", 128, 4), ("symmetric", 64, 4)):
+    for perm, w, u in (("row_only", 64, 2), ("row_only", 64, 4), ("row_only", 128, 4)):
         name = f"PSELL {perm} w={w} u={u}"
         if want(name):
             G = M.to_jds("PSELL", perm, window=w, unroll=u)
