@@ -263,6 +263,31 @@ gbsp_status gbsp_jds_set_format(gbsp_handle jds, int32_t format, int32_t block, 
  * Errors: GBSP_ERR_UNSUPPORTED if the handle was built without vmap. */
 gbsp_status gbsp_jds_values(gbsp_handle jds, const void *d_src_val, void *stream);
 
+/* Shared-memory staging of x for a SELL handle (GB300 addition; the paper
+ * has none).  A warp-wide gather costs the L1TEX stage about one clock per
+ * distinct cache line it touches, so scattered gathers, not bytes, bound
+ * the SELL product on banded matrices.  Staging: for every group of 32
+ * blocks (1024 permuted rows) the product kernel first copies up to
+ * `pages_per_group` pages of x (1024 consecutive entries each; the pages
+ * the group's entries reference most, each referenced at least `min_refs`
+ * times, ties to the smaller page) into shared memory with coalesced loads,
+ * then reads those entries' x values from there.  The arithmetic is
+ * unchanged: staged and unstaged products are bit-identical.
+ * gbsp_sell_stage_bytes: sizes of d_col_staged (int32, nnz entries), d_pages
+ *   (int32, one row of pages_per_group per group) and the device workspace.
+ * gbsp_sell_stage: builds both arrays (borrowed by the handle until destroy
+ *   or the next call) and switches SpMVs with k = 1 whose x is not
+ *   gathered through the permutation (row-only permutation, or the permuted
+ *   basis) to the staged kernel.  pages_per_group: 1..14 (FP64) or 1..16
+ *   (FP32) -- each page takes 8 or 4 KB of shared memory per CTA, two CTAs
+ *   per SM; 0 removes the staging.  Synchronises `stream`.
+ * Errors: GBSP_ERR_ARG (not SELL, bad counts, undersized buffers),
+ * GBSP_ERR_UNSUPPORTED when (group, page) keys exceed 32 bits. */
+gbsp_status gbsp_sell_stage_bytes(gbsp_handle sell, int32_t pages_per_group, int64_t *col_bytes,
+                                  int64_t *pages_bytes, int64_t *ws_bytes);
+gbsp_status gbsp_sell_stage(gbsp_handle sell, int32_t pages_per_group, int32_t min_refs, int32_t *d_col_staged,
+                            int32_t *d_pages, void *d_ws, int64_t ws_bytes, void *stream);
+
 /* Deep-diagonal split for the JDS and NUJDS walks (GB300 addition; the
  * paper has none).  The thread of a permuted row walks its jagged diagonals
  * one after another, so a few very long rows (heavy-tailed row lengths)
@@ -270,9 +295,15 @@ gbsp_status gbsp_jds_values(gbsp_handle jds, const void *d_src_val, void *stream
  * summed by a separate kernel in chunks of `chunk` diagonals -- one thread
  * per (row, chunk), so the long rows are spread over many threads -- into
  * partial sums in caller workspace, and the row walk stops at `depth` and
- * adds the row's partial sums in chunk order (deterministic; the grouping
- * of the sum differs from the unsplit walk).  Two launches per product;
- * k = 1 only (SpMM ignores the split).  depth = 0 removes the split.
+ * adds the row's partial sums (deterministic; the grouping of the sum
+ * differs from the unsplit walk): rows with at most 8 chunks add them in
+ * chunk order, longer rows in a fixed lane-strided tree.  Three launches per
+ * product: the deep kernel runs on a stream of the handle (created here),
+ * forked from `stream` and joined back with events, so it overlaps the walk;
+ * the merge kernel follows on `stream` (capturable in a CUDA graph).  Calls
+ * on one split handle must not overlap (they share the workspace and the
+ * side stream).  k = 1 only (SpMM ignores the split).  depth = 0 removes the
+ * split.
  * Workspace bytes from gbsp_jds_split_bytes; 256-byte aligned; borrowed
  * until destroy or the next gbsp_jds_split.  Synchronises `stream`. */
 gbsp_status gbsp_jds_split_bytes(gbsp_handle jds, int32_t depth, int32_t chunk, int64_t *bytes);

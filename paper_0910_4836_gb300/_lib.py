@@ -112,6 +112,9 @@ SIGNATURES = {
                                       c_vp]),
     "gbsp_gather_partials": (c_i32, [c_i64, ctypes.POINTER(c_i32)]),
     "gbsp_stride_hist": (c_i32, [c_vp, c_i64, c_vp, c_vp]),
+    "gbsp_sell_stage_bytes": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64),
+                                      ctypes.POINTER(c_i64)]),
+    "gbsp_sell_stage": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_i64, c_vp]),
     "gbsp_dia_plan_workspace": (c_i32, [c_vp, ctypes.POINTER(c_i64)]),
     "gbsp_dia_plan": (c_i32, [c_vp, c_i32, ctypes.c_double, c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(DiaSizes)]),
     "gbsp_dia_build": (c_i32, [c_vp, ctypes.POINTER(DiaSizes), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,

@@ -80,6 +80,12 @@ int32_t gbsp_version(void) { return 10000; }
 
 gbsp_status gbsp_destroy(gbsp_handle h) {
     if (!h) return GBSP_OK;
+    if (h->split_side) {
+        cudaStreamSynchronize(h->split_side);
+        cudaStreamDestroy(h->split_side);
+        cudaEventDestroy(h->split_fork);
+        cudaEventDestroy(h->split_join);
+    }
     if (h->owns_transpose && h->transpose) delete static_cast<gbsp_mat *>(h->transpose);
     delete h;
     return GBSP_OK;

@@ -245,6 +245,18 @@ static gbsp_status radix_sort_index(uint32_t *keys, int64_t n, int bits, SortWs 
     return GBSP_OK;
 }
 
+// Sort of bare keys (the values, the original positions, are not needed):
+// workspace of sort_keys_ws_bytes(n); *sorted points into keys or the
+// workspace.  `keys` is overwritten.
+int64_t sort_keys_ws_bytes(int64_t n) { return sort_ws_bytes(n); }
+
+gbsp_status sort_keys(uint32_t *keys, int64_t n, int bits, void *ws, cudaStream_t s, uint32_t **sorted) {
+    char *p = static_cast<char *>(ws);
+    SortWs w = carve_sort_ws(p, n);
+    int32_t *vs = nullptr;
+    return radix_sort_index(keys, n, bits, w, s, sorted, &vs);
+}
+
 // ------------------------------------------------------------ JDS build --
 
 __global__ void row_len_kernel(int64_t n, const int32_t *__restrict__ row_ptr, int32_t *len,

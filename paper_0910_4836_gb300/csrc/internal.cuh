@@ -55,6 +55,19 @@ struct Mat {
     const int4 *split_table = nullptr;  // per chunk {d_begin, d_end, rows, partial offset}
     const int32_t *split_items = nullptr;  // per chunk: first CTA item (k+1 entries)
     void *split_part = nullptr;
+    void *split_shallow = nullptr;  // walk sums of the rows deeper than split_depth
+    int64_t split_rows = 0;         // those rows: [0, split_rows)
+    int64_t split_wide_rows = 0;    // rows with more than 8 chunks: [0, split_wide_rows)
+    // SELL with x staged in shared memory: per 1024-row group (32 blocks)
+    // up to stage_pages_per_group pages of 1024 x entries, and the columns
+    // re-encoded (staged entries as ~(slot*1024 + col % 1024))
+    const int32_t *stage_col = nullptr;
+    const int32_t *stage_pages = nullptr;
+    int32_t stage_pages_per_group = 0;
+    // the deep kernel runs on a side stream of the handle, forked from and
+    // joined back to the caller's stream with these events
+    cudaStream_t split_side = nullptr;
+    cudaEvent_t split_fork = nullptr, split_join = nullptr;
     std::vector<int32_t> h_jd_ptr;  // host copy, read back once at build (literal launches)
 
     // transposed structure (CRS handle built by gbsp_transpose_build)
@@ -101,6 +114,9 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // device exclusive scan of int32 (convert.cu): out[0..n) = exclusive scan of
 // in, *total_out = the total when given; ws holds scan_ws_bytes(n) bytes
 int64_t scan_ws_bytes(int64_t n);
+// stable LSD radix sort of bare uint32 keys (convert.cu)
+int64_t sort_keys_ws_bytes(int64_t n);
+gbsp_status sort_keys(uint32_t *keys, int64_t n, int bits, void *ws, cudaStream_t s, uint32_t **sorted);
 gbsp_status scan_exclusive(const int32_t *in, int64_t n, int32_t *out, int32_t *total_out, int32_t *ws,
                            cudaStream_t s);
 

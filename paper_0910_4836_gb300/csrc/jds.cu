@@ -20,6 +20,7 @@
 //                consecutively (diagonal-major inside the block), so a CTA
 //                streams one contiguous chunk.
 #include <algorithm>
+#include <climits>
 #include <vector>
 
 #include "accum.cuh"
@@ -47,6 +48,9 @@ struct JdsArgs {
     const int4 *split_table;
     const int32_t *split_items;
     const void *split_part;
+    void *split_shallow;   // walk sums of the rows that go deeper than d_limit
+    int64_t split_rows;    // those rows: [0, split_rows)
+    int64_t n_cols;
 };
 
 __device__ __forceinline__ int64_t xidx(const int32_t *x_perm, int32_t c) {
@@ -126,20 +130,14 @@ __global__ void __launch_bounds__(256) jds_row_kernel(JdsArgs a) {
 #pragma unroll
             for (int j = 0; j <= U; ++j) e[j] = en[j];
         }
-        // deeper diagonals: the chunk partial sums, in chunk order
-        if (a.split_k > 0) {
-            const Acc<VM> *part = static_cast<const Acc<VM> *>(a.split_part);
-            for (int32_t k = 0; k < a.split_k; ++k) {
-                const int4 t = __ldg(a.split_table + k);
-                if (rr[0] >= t.z) break;  // rows of chunk k are [0, t.z)
+        // rows that go deeper than the split depth: their walk sum waits in
+        // the workspace for the merge with the chunk partial sums
 #pragma unroll
-                for (int i = 0; i < R; ++i)
-                    if (rr[i] < t.z) acc[i].merge(part[(int64_t)t.w + rr[i]]);
-            }
+        for (int i = 0; i < R; ++i) {
+            if (rr[i] >= a.n_rows) continue;
+            if (rr[i] < a.split_rows) static_cast<Acc<VM> *>(a.split_shallow)[rr[i]] = acc[i];
+            else store_row<VM>(a, rr[i], 0, acc[i]);
         }
-#pragma unroll
-        for (int i = 0; i < R; ++i)
-            if (rr[i] < a.n_rows) store_row<VM>(a, rr[i], 0, acc[i]);
     }
 }
 
@@ -149,33 +147,107 @@ __global__ void __launch_bounds__(256) jds_row_kernel(JdsArgs a) {
 template <int VM>
 __global__ void __launch_bounds__(256) jds_deep_kernel(JdsArgs a, int64_t n_items) {
     typedef typename ValT<VM>::T T;
+    constexpr int W = 256;  // diagonals of jd_ptr staged in shared memory at a time
+    constexpr int G = 8;    // diagonals whose loads are issued together
+    __shared__ int32_t sj[W + 1];
     const T *__restrict__ val = static_cast<const T *>(a.val);
     const T *__restrict__ x = static_cast<const T *>(a.x);
     Acc<VM> *part = static_cast<Acc<VM> *>(const_cast<void *>(a.split_part));
+    // a CTA works on one item at a time, so its threads share the chunk and
+    // its diagonal offsets; its items come in increasing order, so the chunk
+    // index only moves forward
+    int32_t k = 0;
     for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-        int32_t k = 0;
         while (k + 1 < a.split_k && __ldg(a.split_items + k + 1) <= it) ++k;
         const int4 t = __ldg(a.split_table + k);
         const int64_t r = (it - __ldg(a.split_items + k)) * 256 + threadIdx.x;
-        if (r >= t.z) continue;
+        const bool live = r < t.z;
         Acc<VM> acc;
         acc.init();
-        int32_t st = __ldg(a.jd_ptr + t.x);
-        for (int32_t d = t.x; d < t.y; d += 2) {
-            const int32_t e1 = __ldg(a.jd_ptr + d + 1);
-            const int32_t e2 = d + 1 < t.y ? __ldg(a.jd_ptr + d + 2) : e1;
-            const bool ok0 = e1 - st > r, ok1 = d + 1 < t.y && e2 - e1 > r;
-            if (!ok0) break;
-            const int c0 = ld_stream(a.col + st + r);
-            const T v0 = ld_stream(val + st + r);
-            const int c1 = ok1 ? ld_stream(a.col + e1 + r) : 0;
-            const T v1 = ok1 ? ld_stream(val + e1 + r) : T(0);
-            acc.add(v0, ld_vec(x + xidx(a.x_perm, c0) * a.ldx));
-            if (ok1) acc.add(v1, ld_vec(x + xidx(a.x_perm, c1) * a.ldx));
-            if (!ok1) break;
-            st = e2;
+        bool done = !live;
+        for (int32_t w0 = t.x; w0 < t.y; w0 += W) {
+            const int32_t wn = min(W, t.y - w0);
+            __syncthreads();
+            for (int i = threadIdx.x; i <= wn; i += blockDim.x) sj[i] = __ldg(a.jd_ptr + w0 + i);
+            __syncthreads();
+            if (done) continue;
+            for (int32_t d = 0; d < wn; d += G) {
+                int c[G];
+                T v[G];
+#pragma unroll
+                for (int j = 0; j < G; ++j) {
+                    // diagonal lengths fall with d: once row r is past one, it is past the rest
+                    const bool ok = d + j < wn && sj[d + j + 1] - sj[d + j] > r;
+                    c[j] = ok ? ld_stream(a.col + sj[d + j] + r) : -1;
+                    v[j] = ok ? ld_stream(val + sj[d + j] + r) : T(0);
+                }
+#pragma unroll
+                for (int j = 0; j < G; ++j)
+                    if (c[j] >= 0) acc.add(v[j], ld_vec(x + xidx(a.x_perm, c[j]) * a.ldx));
+                if (c[G - 1] < 0) {
+                    done = true;
+                    break;
+                }
+            }
         }
-        part[(int64_t)t.w + r] = acc;
+        if (live) part[(int64_t)t.w + r] = acc;
+    }
+}
+
+// Last step of a split walk: row r (a row deeper than the split depth)
+// takes its walk sum and adds its chunk partial sums.  Rows with more than
+// 8 chunks ([0, wide_rows)) get a warp: lane l sums chunks l, l+32, ... in
+// order and a fixed shuffle tree combines the lanes.  The others get a
+// thread that adds its (at most 8) chunks in chunk order, loads issued
+// together.
+template <int VM>
+__global__ void __launch_bounds__(256) jds_split_merge_kernel(JdsArgs a, int64_t wide_rows) {
+    const Acc<VM> *part = static_cast<const Acc<VM> *>(a.split_part);
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < wide_rows; r += nwarps) {
+        Acc<VM> s;
+        s.init();
+        for (int32_t k0 = lane; k0 < a.split_k; k0 += 32 * 4) {
+            Acc<VM> p[4];
+            bool ok[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int32_t k = k0 + 32 * j;
+                const int4 t = k < a.split_k ? __ldg(a.split_table + k) : make_int4(0, 0, 0, 0);
+                ok[j] = k < a.split_k && r < t.z;
+                if (ok[j]) p[j] = part[(int64_t)t.w + r];
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (ok[j]) s.merge(p[j]);
+            if (!ok[3]) break;
+        }
+        group_reduce<32>(s);
+        if (lane == 0) {
+            Acc<VM> acc = static_cast<const Acc<VM> *>(a.split_shallow)[r];
+            acc.merge(s);
+            store_row<VM>(a, r, 0, acc);
+        }
+    }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = wide_rows + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.split_rows; r += stride) {
+        Acc<VM> acc = static_cast<const Acc<VM> *>(a.split_shallow)[r];
+        for (int32_t k0 = 0; k0 < a.split_k; k0 += 8) {
+            Acc<VM> p[8];
+            bool ok[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int4 t = k0 + j < a.split_k ? __ldg(a.split_table + k0 + j) : make_int4(0, 0, 0, 0);
+                ok[j] = k0 + j < a.split_k && r < t.z;  // rows of chunk k are [0, t.z)
+                if (ok[j]) p[j] = part[(int64_t)t.w + r];
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (ok[j]) acc.merge(p[j]);
+            if (!ok[7]) break;
+        }
+        store_row<VM>(a, r, 0, acc);
     }
 }
 
@@ -309,6 +381,81 @@ __global__ void __launch_bounds__(1024) sell_kernel(JdsArgs a) {
             for (int q = 0; q < KT; ++q)
                 if (KT == 1 || a.c0 + q < a.k) store_row<VM>(a, r, a.c0 + q, acc[q]);
         }
+    }
+}
+
+// SELL with the banded part of x staged in shared memory.  A CTA of 32 warps
+// takes a group of 32 consecutive blocks (1024 rows) at a time, as the SELL
+// kernel does; before walking them it copies the group's chosen x pages
+// (1024 entries each, the pages its rows reference most) into shared memory
+// with coalesced loads.  A staged entry's column is stored as
+// ~(slot * 1024 + col % 1024) and read from shared memory; the rest are
+// gathered from global memory as before.  The arithmetic is the SELL
+// kernel's, entry for entry, so the results are bit-identical; only where
+// each x value is read from changes.  Two CTAs per SM, so one stages while
+// the other walks.
+constexpr int kStagePage = 1024;
+
+template <int VM, int U>
+__global__ void __launch_bounds__(1024, 2) sell_staged_kernel(JdsArgs a, const int32_t *__restrict__ col_st,
+                                                               const int32_t *__restrict__ pages, int P) {
+    typedef typename ValT<VM>::T T;
+    extern __shared__ __align__(16) unsigned char stage_smem[];
+    T *xs = reinterpret_cast<T *>(stage_smem);
+    const T *__restrict__ val = static_cast<const T *>(a.val);
+    const T *__restrict__ x = static_cast<const T *>(a.x);
+    const int lane = threadIdx.x & 31;
+    const int64_t nb = ceil_div_dev(a.n_rows, 32);
+    const int wpc = blockDim.x >> 5;
+    const int wid = threadIdx.x >> 5;
+    const int64_t ngroups = ceil_div_dev(nb, wpc);
+    int64_t it = 0;
+    for (int64_t g0 = 0; g0 < ngroups; g0 += gridDim.x, ++it) {
+        const int64_t g = g0 + (int64_t)((blockIdx.x + it) % gridDim.x);
+        __syncthreads();  // the previous group's staged x is no longer read
+        if (g < ngroups) {
+            for (int q = threadIdx.x; q < P * kStagePage; q += blockDim.x) {
+                const int32_t pg = __ldg(pages + g * P + q / kStagePage);
+                const int64_t idx = (int64_t)pg * kStagePage + (q % kStagePage);
+                xs[q] = (pg >= 0 && idx < a.n_cols) ? ld_vec(x + idx) : T(0);
+            }
+        }
+        __syncthreads();
+        if (g >= ngroups) continue;
+        const int64_t b = g * wpc + (int64_t)((wid + it * 7) % wpc);
+        if (b >= nb) continue;
+        const int64_t r = b * 32 + lane;
+        const int32_t len = r < a.n_rows ? __ldg(a.rlen + r) : 0;
+        const int32_t width = __shfl_sync(0xffffffffu, len, 0);
+        int64_t off = __ldg(a.blk_ptr + b);
+        Acc<VM> acc;
+        acc.init();
+        constexpr int NONE = INT_MIN;
+        int c[U];
+        T v[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const bool ok = len > j;
+            c[j] = ok ? ld_stream(col_st + off + lane) : NONE;
+            v[j] = ok ? ld_stream(val + off + lane) : T(0);
+            off += __popc(__ballot_sync(0xffffffffu, len > j));
+        }
+        for (int32_t d0 = 0; d0 < width; d0 += U) {
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                if (c[j] == NONE) continue;
+                acc.add(v[j], c[j] >= 0 ? ld_vec(x + c[j]) : xs[~c[j]]);
+            }
+            if (d0 + U >= width) break;
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const bool ok = len > d0 + U + j;
+                c[j] = ok ? ld_stream(col_st + off + lane) : NONE;
+                v[j] = ok ? ld_stream(val + off + lane) : T(0);
+                off += __popc(__ballot_sync(0xffffffffu, len > d0 + U + j));
+            }
+        }
+        if (r < a.n_rows) store_row<VM>(a, r, 0, acc);
     }
 }
 
@@ -518,6 +665,24 @@ static void launch_psell(const Mat &A, JdsArgs a, cudaStream_t s) {
     }
 }
 
+template <int VM, int U>
+static gbsp_status launch_sell_staged_U(const Mat &A, JdsArgs a, cudaStream_t s) {
+    typedef typename ValT<VM>::T T;
+    const int P = A.stage_pages_per_group;
+    const int smem = P * kStagePage * (int)sizeof(T);
+    static int configured = 0;  // largest dynamic shared memory set so far for this kernel
+    if (smem > configured) {
+        GBSP_CUDA(cudaFuncSetAttribute(sell_staged_kernel<VM, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        GBSP_CUDA(cudaFuncSetAttribute(sell_staged_kernel<VM, U>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       100));
+        configured = smem;
+    }
+    const int64_t ngroups = ceil_div(ceil_div(a.n_rows, 32), 32);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ngroups, (int64_t)num_sms() * 2));
+    sell_staged_kernel<VM, U><<<(unsigned)grid, 1024, smem, s>>>(a, A.stage_col, A.stage_pages, P);
+    return GBSP_OK;
+}
+
 template <int VM>
 static void launch_sell(const Mat &A, JdsArgs a, cudaStream_t s) {
     int KT = 1;
@@ -539,6 +704,11 @@ template <int VM>
 static gbsp_status launch_family(const Mat &A, JdsArgs a, cudaStream_t s) {
     typedef typename ValT<VM>::T T;
     const int fmt = A.format;
+    if (fmt == GBSP_SELL && A.stage_col && a.k == 1 && !a.x_perm) {
+        if (A.unroll <= 1) return launch_sell_staged_U<VM, 1>(A, a, s);
+        if (A.unroll <= 2) return launch_sell_staged_U<VM, 2>(A, a, s);
+        return launch_sell_staged_U<VM, 4>(A, a, s);
+    }
     if (fmt == GBSP_SELL) {
         launch_sell<VM>(A, a, s);
         return GBSP_OK;
@@ -584,21 +754,33 @@ static gbsp_status launch_family(const Mat &A, JdsArgs a, cudaStream_t s) {
     const int u = fmt == GBSP_NUJDS ? A.unroll : 1;
     const int R = A.kopt.rows_per_warp > 1 ? A.kopt.rows_per_warp : 1;  // rows per thread
     if (A.split_k > 0) {
-        // deep diagonals first (chunk partial sums), then the walk that stops
-        // at the split depth and merges them
+        // deep diagonals (chunk partial sums), the walk that stops at the
+        // split depth, then the merge of the two for the deep rows
         a.d_limit = A.split_depth;
         a.split_k = A.split_k;
         a.split_table = A.split_table;
         a.split_items = A.split_items;
         a.split_part = A.split_part;
+        a.split_shallow = A.split_shallow;
+        a.split_rows = A.split_rows;
+        // fork: the deep kernel on the side stream, overlapping the walk
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(A.split_items_total, (int64_t)num_sms() * 16));
-        jds_deep_kernel<VM><<<(unsigned)grid, 256, 0, s>>>(a, A.split_items_total);
+        GBSP_CUDA(cudaEventRecord(A.split_fork, s));
+        GBSP_CUDA(cudaStreamWaitEvent(A.split_side, A.split_fork, 0));
+        jds_deep_kernel<VM><<<(unsigned)grid, 256, 0, A.split_side>>>(a, A.split_items_total);
+        GBSP_CUDA(cudaEventRecord(A.split_join, A.split_side));
     }
     if (u <= 1) launch_row<VM, 1>(a, R, s);
     else if (u <= 2) launch_row<VM, 2>(a, R, s);
     else if (u <= 4) launch_row<VM, 4>(a, R, s);
     else if (u <= 8) launch_row<VM, 8>(a, std::min(R, 2), s);
     else launch_row<VM, 16>(a, 1, s);
+    if (A.split_k > 0) {
+        GBSP_CUDA(cudaStreamWaitEvent(s, A.split_join, 0));  // join
+        const int64_t work = std::max<int64_t>(A.split_wide_rows * 32, A.split_rows - A.split_wide_rows);
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), (int64_t)num_sms() * 8));
+        jds_split_merge_kernel<VM><<<(unsigned)grid, 256, 0, s>>>(a, A.split_wide_rows);
+    }
     return GBSP_OK;
 }
 
@@ -625,6 +807,9 @@ gbsp_status jds_launch(const Mat &A, const VecArgs &v, cudaStream_t s) {
     a.rlen = A.rlen;
     a.d_limit = A.n_diag;
     a.split_k = 0;
+    a.split_rows = 0;
+    a.split_shallow = nullptr;
+    a.n_cols = A.n_cols;
     gbsp_status st;
     if (A.dtype == GBSP_F64) st = launch_family<VM_F64>(A, a, s);
     else if (A.kopt.accum == GBSP_ACC_COMPENSATED) st = launch_family<VM_F32C>(A, a, s);
@@ -637,7 +822,7 @@ gbsp_status jds_launch(const Mat &A, const VecArgs &v, cudaStream_t s) {
 // Split set-up: chunks of `chunk` diagonals from `depth` on; chunk k holds
 // the rows [0, diagLen(d_begin)).  Workspace: the chunk table, the per-chunk
 // first CTA item, then the ragged partial sums (one accumulator per row and
-// chunk).
+// chunk), then the walk sums of the rows of chunk 0.
 static int64_t acc_bytes(int dtype, int accum) {
     return dtype == GBSP_F64 ? 8 : (accum == GBSP_ACC_COMPENSATED ? 8 : 4);
 }
@@ -665,7 +850,9 @@ gbsp_status jds_split_bytes_impl(const Mat &A, int32_t depth, int32_t chunk, int
     std::vector<int32_t> it;
     int64_t parts = 0;
     split_plan(A, depth, chunk, &t, &it, &parts);
-    *bytes = 256 + 16 * (int64_t)t.size() + 4 * (int64_t)it.size() + 16 + parts * acc_bytes(A.dtype, GBSP_ACC_COMPENSATED);
+    const int64_t rows = t.empty() ? 0 : t[0].z;  // rows deeper than the split depth
+    *bytes = 256 + 16 * (int64_t)t.size() + 4 * (int64_t)it.size() + 16 +
+             (parts + rows) * acc_bytes(A.dtype, GBSP_ACC_COMPENSATED);
     return GBSP_OK;
 }
 
@@ -689,6 +876,11 @@ gbsp_status jds_split_impl(Mat &A, int32_t depth, int32_t chunk, void *ws, int64
     int4 *dt = reinterpret_cast<int4 *>(p);
     int32_t *di = reinterpret_cast<int32_t *>(p + 16 * t.size());
     const int64_t po = ((16 * (int64_t)t.size() + 4 * (int64_t)it.size()) + 255) & ~int64_t(255);
+    if (!A.split_side) {
+        GBSP_CUDA(cudaStreamCreateWithFlags(&A.split_side, cudaStreamNonBlocking));
+        GBSP_CUDA(cudaEventCreateWithFlags(&A.split_fork, cudaEventDisableTiming));
+        GBSP_CUDA(cudaEventCreateWithFlags(&A.split_join, cudaEventDisableTiming));
+    }
     GBSP_CUDA(cudaMemcpyAsync(dt, t.data(), 16 * t.size(), cudaMemcpyHostToDevice, s));
     GBSP_CUDA(cudaMemcpyAsync(di, it.data(), 4 * it.size(), cudaMemcpyHostToDevice, s));
     GBSP_CUDA(cudaStreamSynchronize(s));
@@ -699,6 +891,9 @@ gbsp_status jds_split_impl(Mat &A, int32_t depth, int32_t chunk, void *ws, int64
     A.split_items = di;
     A.split_items_total = it.back();
     A.split_part = p + po;
+    A.split_rows = t.empty() ? 0 : t[0].z;
+    A.split_wide_rows = t.size() > 8 ? t[8].z : 0;  // rows with more than 8 chunks
+    A.split_shallow = p + po + parts * acc_bytes(A.dtype, GBSP_ACC_COMPENSATED);
     return GBSP_OK;
 }
 

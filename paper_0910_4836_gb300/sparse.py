@@ -356,6 +356,24 @@ class JDSMatrix(_Product):
                                           _stream(stream)), "gbsp_permute_vec")
         return out
 
+    def stage_x(self, pages_per_group: int = 12, min_refs: int = 32, stream=None) -> None:
+        """SELL only: stage the most referenced pages of x per 1024-row group
+        in shared memory (0 removes it).  Products stay bit-identical."""
+        lib = L.load()
+        if pages_per_group == 0:
+            L.check(lib.gbsp_sell_stage(self._h, 0, 1, None, None, None, 0, _stream(stream)), "gbsp_sell_stage")
+            self._stage = None
+            return
+        cb, pb, wb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        L.check(lib.gbsp_sell_stage_bytes(self._h, pages_per_group, ctypes.byref(cb), ctypes.byref(pb),
+                                          ctypes.byref(wb)), "gbsp_sell_stage_bytes")
+        col_st = torch.empty(cb.value // 4, dtype=torch.int32, device=self._device)
+        pages = torch.empty(max(pb.value // 4, 1), dtype=torch.int32, device=self._device)
+        work = torch.empty(max(wb.value, 1), dtype=torch.uint8, device=self._device)
+        L.check(lib.gbsp_sell_stage(self._h, pages_per_group, min_refs, _vp(col_st), _vp(pages), _vp(work),
+                                    wb.value, _stream(stream)), "gbsp_sell_stage")
+        self._stage = (col_st, pages)
+
     def spmv_original(self, x: torch.Tensor, out=None, accumulate=False, stream=None):
         return self.spmv(x, out, accumulate, basis=L.BASIS_ORIGINAL, stream=stream)
 

@@ -100,6 +100,24 @@ def test_deep_split(perm):
         for fmt, b, u, r in (("JDS", 0, 0, 1), ("NUJDS", 0, 2, 2), ("NUJDS", 0, 4, 1)):
             set_variant(J, fmt, b, u, r)
             assert_close64(host(J.spmv_original(dev(x))), ref, s, f"split {depth}/{chunk} {fmt} u{u} r{r}")
+    # the split product forks its deep kernel onto a side stream: it must
+    # still capture into a CUDA graph and replay to the same result
+    J.split(16, 32)
+    set_variant(J, "NUJDS", 0, 2, 1)
+    xd = dev(x)
+    yd = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+    ref_split = host(J.spmv_original(xd, out=yd)).copy()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        J.spmv_original(xd, out=yd)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        J.spmv_original(xd, out=yd)
+    yd.zero_()
+    g.replay()
+    assert np.array_equal(host(yd), ref_split)
     J.split(0)
     Ai = S.integer_values(A, 58, 1000)
     xi = S.int_vector(A.n_cols, 58, 1000)
@@ -311,3 +329,39 @@ def test_psell_spmm_integer_and_rejections():
         M.to_jds("PSELL", "row_only", window=96)  # not a multiple of 64
     with pytest.raises(GbspError):
         G.set_format("SELL")  # different storage
+
+
+STAGE_MATS = [lambda: S.laplace2d(), lambda: S.hh_like(100_000, 21), lambda: S.zipf_rows(60_000, 22, lmax=3000),
+              lambda: S.small_random(500, 700, 23, density=0.02, empty_rows=0.3),
+              lambda: S.from_coo(3, 3, [1], [2], [1.5])]
+
+
+@pytest.mark.parametrize("mi", range(len(STAGE_MATS)))
+@pytest.mark.parametrize("perm", ["symmetric", "row_only"])
+def test_sell_staged_x_is_bit_identical(mi, perm):
+    """Staging pages of x in shared memory changes where x values are read,
+    not the arithmetic: the staged SELL product equals the unstaged one bit
+    for bit, in FP64 and compensated FP32, and matches the oracle."""
+    A = STAGE_MATS[mi]()
+    if perm == "symmetric" and A.n_rows != A.n_cols:
+        pytest.skip("symmetric permutation needs a square matrix")
+    x = S.vector(A.n_cols, 91 + mi)
+    ref, s = O.crs_spmv_exact(A, x)
+    for dtype in (torch.float64, torch.float32):
+        M = crs(A, dtype)
+        if dtype == torch.float32:
+            M.set_kernel("vector", compensated=True)
+        for w, u in ((128, 1), (128, 2), (1024, 4)):
+            G = M.to_jds("SELL", perm, window=w, unroll=u)
+            xd = dev(x).to(dtype)
+            xp = G.permute(xd)  if perm == "symmetric" else xd
+            plain = G.spmv(xp).clone()
+            plain_o = G.spmv_original(xd).clone()
+            for pages, refs in ((12, 32), (1, 1), (4, 10 ** 9)):
+                G.stage_x(pages, refs)
+                assert torch.equal(G.spmv(xp), plain), (mi, perm, dtype, w, u, pages, refs)
+                assert torch.equal(G.spmv_original(xd), plain_o)
+            G.stage_x(0)
+            assert torch.equal(G.spmv(xp), plain)
+            if dtype == torch.float64:
+                assert_close64(host(plain_o), ref, s, f"staged SELL w={w} u={u}")
