@@ -643,9 +643,27 @@ def fwd_bwd_speedup(dev, time_launches):
 
 # ------------------------------------------------------------ CPU side -----
 
+def host_copy_gbs(nbytes=1 << 30, reps=5):
+    """STREAM-style copy bandwidth of the host (torch CPU copy, all its
+    threads), read + write bytes per second: the CPU side's own roofline."""
+    import torch
+    src = torch.ones(nbytes // 8, dtype=torch.float64)
+    dst = torch.empty_like(src)
+    dst.copy_(src)
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        dst.copy_(src)
+        el = time.perf_counter() - t0
+        best = el if best is None else min(best, el)
+    return round(2 * nbytes / best / 1e9, 1)
+
+
 def cpu_baseline(A, x, seconds):
-    """The oracle's OpenMP static-schedule CRS loop on the host cores, on
-    the full matrix, repeated for about `seconds`."""
+    """The oracle on the host cores: its OpenMP static-schedule CRS loop (the
+    paper's best parallel setting) on the full matrix, repeated for about
+    `seconds`; the serial literal CRS and JDS loops on one core, once each;
+    and the host copy bandwidth."""
     import oracle as O
     y = np.zeros(A.n_rows)
     O.crs_spmv_omp(A, x, y)  # first touch
@@ -658,9 +676,20 @@ def cpu_baseline(A, x, seconds):
         if el >= seconds or reps >= 200:
             break
     per = el / reps
-    return {"value": round(2.0 * A.nnz / per / 1e9, 3), "unit": "GFlop/s",
-            "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"full matrix, {reps} SpMVMs with the OpenMP static CRS loop ({el:.1f} s)"}
+    out = {"value": round(2.0 * A.nnz / per / 1e9, 3), "unit": "GFlop/s",
+           "cores": O.num_threads(), "kind": "oracle",
+           "sample": f"full matrix, {reps} SpMVMs with the OpenMP static CRS loop ({el:.1f} s)"}
+    t0 = time.perf_counter()
+    O.crs_spmv(A, x)
+    out["serial_crs_gflops"] = round(2.0 * A.nnz / (time.perf_counter() - t0) / 1e9, 3)
+    J = O.jds_build(A, symmetric=True)
+    xp = O.permute(J.perm, x)
+    t0 = time.perf_counter()
+    O.jds_spmv(J, xp)
+    out["serial_jds_gflops"] = round(2.0 * A.nnz / (time.perf_counter() - t0) / 1e9, 3)
+    out["serial_cores"] = 1
+    out["host_copy_gbs"] = host_copy_gbs()
+    return out
 
 
 def run_reference(args):
