@@ -315,7 +315,9 @@ def run_ours(args):
         table[name] = {"gflops": round(2.0 * A.nnz / (t * 1e-3) / 1e9, 1),
                        "gbs": round(nbytes / (t * 1e-3) / 1e9, 1), "ms": round(t, 4),
                        "frac": round(nbytes / (t * 1e-3) / 1e9 / peak, 3)}
-        if best is None or t < best[0]:
+        # a later scheme replaces the choice only when more than 1% faster,
+        # so near-ties keep the earlier (listed first) scheme from run to run
+        if best is None or t < 0.99 * best[0]:
             best = (t, name, H, xin, nbytes, how)
     _, kname, H, xin, alg, how = best
     configure(H, how)
@@ -447,10 +449,12 @@ def fp32_numbers(M, A, x, y64, dev, time_launches, ms64):
     y32 = torch.empty(A.n_rows, dtype=torch.float32, device=dev)
     J32 = M32.to_jds("NUJDS", "symmetric", unroll=4)
     xp32 = J32.permute(x32)
+    G32 = M32.to_jds("SELL", "row_only", window=128, unroll=4)
     res = {}
     opts = [("CRS vector l4 r4", M32, x32, lambda: M32.set_kernel("vector", lanes=4, rows_per_warp=4)),
             ("CRS tiled 1024", M32, x32, lambda: M32.prepare_tiled(1024)),
-            ("NUJDS symmetric u=4", J32, xp32, lambda: None)]
+            ("NUJDS symmetric u=4", J32, xp32, lambda: None),
+            ("SELL row_only w=128 u=4", G32, x32, lambda: None)]
     best = None
     for name, H, xin, conf in opts:
         conf()
