@@ -70,13 +70,15 @@ class Batch:
             pass
 
     @staticmethod
-    def autotuned(mats, ks, dtype=torch.float64, device="cuda", formats=("CRS", "JDS"),
-                  compensated: bool = True, chunk: int = 4096):
+    def autotuned(mats, ks, dtype=torch.float64, device="cuda", formats=("CRS", "JDS", "SELL"),
+                  compensated: bool = True, chunk: int = 4096, window: int = 128):
         """Build a batch over host CRS matrices `mats` with k_b right-hand
         sides: for every matrix, tune the CRS kernel and (if asked) the JDS
-        walks, and keep the faster scheme.  Returns (batch, handles, X, Y)
-        with X, Y in the basis of the chosen handle (the JDS permuted basis
-        for JDS items) and filled with zeros."""
+        walks and SELL-32-sigma (row-only permutation, `window` rows), and
+        keep the fastest scheme.  Returns (batch, handles, X, Y) with X, Y in
+        the basis of the chosen handle (the JDS permuted basis for JDS items;
+        for SELL items x in the original basis and y in the window-permuted
+        one) and filled with zeros."""
         handles, Xs, Ys = [], [], []
         for A, k in zip(mats, ks):
             M = CRSMatrix.from_host(A, device=device, dtype=dtype)
@@ -90,7 +92,14 @@ class Batch:
                     J.set_kernel("vector", compensated=compensated)
                 _, jms = J.autotune(k)
                 if jms < best_ms:
-                    choice = J
+                    choice, best_ms = J, jms
+            if "SELL" in formats:
+                G = M.to_jds("SELL", "row_only", window=window, unroll=4)
+                if dtype == torch.float32:
+                    G.set_kernel("vector", compensated=compensated)
+                _, gms = G.autotune(k)
+                if gms < best_ms:
+                    choice, best_ms = G, gms
             handles.append(choice)
             shape_x = (A.n_cols,) if k == 1 else (A.n_cols, k)
             shape_y = (A.n_rows,) if k == 1 else (A.n_rows, k)

@@ -32,6 +32,8 @@ def test_batch_matches_single_launches(dtype):
         M.set_kernel("vector", lanes=(4, 8, 16)[b % 3], rows_per_warp=2, rhs_tile=(4, 8, 16)[b % 3])
         if b % 4 == 1 and A.n_rows == A.n_cols:
             M = M.to_jds(("JDS", "NUJDS", "RBJDS", "SOJDS")[(b // 4) % 4], "symmetric", block=256)
+        elif b % 4 == 3:
+            M = M.to_jds("SELL", "row_only", window=(32, 128, 1024)[(b // 4) % 3], unroll=(1, 2, 4)[b % 3])
         shape = (A.n_cols,) if k == 1 else (A.n_cols, k)
         X = torch.as_tensor(np.stack([S.vector(A.n_cols, 10 * b + c) for c in range(k)], axis=1)
                             .reshape(shape)).to(dtype).cuda()
@@ -129,3 +131,21 @@ def test_autotuned_batch_builder():
     torch.cuda.synchronize()
     for H, X, Y in zip(handles, Xs, Ys):
         assert torch.equal(Y, H.spmm(X))
+
+
+def test_autotuned_batch_with_sell_items():
+    """The autotuner may pick SELL per matrix; the batch still reproduces
+    each chosen handle's own product bit for bit."""
+    from paper_0910_4836_gb300 import Batch, JDSMatrix
+    mats = small_batch(16, 7)
+    ks = S.batch_k(len(mats), "mixed")
+    bt, handles, Xs, Ys = Batch.autotuned(mats, ks, torch.float64, device="cuda")
+    for b, X in enumerate(Xs):
+        X.copy_(torch.as_tensor(np.stack([S.vector(X.shape[0], 100 * b + c) for c in range(ks[b])], axis=1)
+                                .reshape(X.shape)))
+    refs = [H.spmm(X) for H, X in zip(handles, Xs)]
+    bt.run()
+    torch.cuda.synchronize()
+    for Y, ref in zip(Ys, refs):
+        assert torch.equal(Y, ref)
+    assert all(isinstance(h, JDSMatrix) or h.__class__.__name__ == "CRSMatrix" for h in handles)
