@@ -171,22 +171,30 @@ __device__ void batch_sell_rows(const BatchMat &m, int64_t rb, int64_t re, int c
     }
 }
 
-template <int VM>
+// Right-hand-side tiles are clamped to KTMAX, the widest tile the kernel
+// instance carries (a batch whose matrices all have k = 1 runs an instance
+// without the wide-tile code and its registers; k = 16 runs as two 8-wide
+// tiles at twice the occupancy of a 16-wide one).  The tile width never
+// changes a result: every right-hand side is summed on its own, in the same
+// entry order.
+template <int KTMAX>
+__device__ __forceinline__ int clamp_tile(int kt) { return kt < KTMAX ? kt : KTMAX; }
+
+template <int VM, int KTMAX>
 __device__ void batch_item(const BatchMat &m, int64_t rb, int64_t re) {
     if (m.kind == KIND_JDS && m.format == GBSP_SELL) {
         int KT = 1;
         if (m.k > 1) {
             KT = 2;
             while (KT < min(m.k, m.rhs_tile > 0 ? min(m.rhs_tile, 16) : 16)) KT <<= 1;
+            KT = clamp_tile<KTMAX>(KT);
         }
         for (int c0 = 0; c0 < m.k; c0 += KT) {
-            switch (KT) {
-                case 1: batch_sell_rows<VM, 1>(m, rb, re, c0); break;
-                case 2: batch_sell_rows<VM, 2>(m, rb, re, c0); break;
-                case 4: batch_sell_rows<VM, 4>(m, rb, re, c0); break;
-                case 8: batch_sell_rows<VM, 8>(m, rb, re, c0); break;
-                default: batch_sell_rows<VM, 16>(m, rb, re, c0); break;
-            }
+            if (KT == 1) batch_sell_rows<VM, 1>(m, rb, re, c0);
+            if constexpr (KTMAX >= 2) if (KT == 2) batch_sell_rows<VM, 2>(m, rb, re, c0);
+            if constexpr (KTMAX >= 4) if (KT == 4) batch_sell_rows<VM, 4>(m, rb, re, c0);
+            if constexpr (KTMAX >= 8) if (KT == 8) batch_sell_rows<VM, 8>(m, rb, re, c0);
+            if constexpr (KTMAX >= 16) if (KT >= 16) batch_sell_rows<VM, 16>(m, rb, re, c0);
         }
         return;
     }
@@ -200,37 +208,36 @@ __device__ void batch_item(const BatchMat &m, int64_t rb, int64_t re) {
                 case 16: batch_crs_rows<VM, 16>(m, rb, re); break;
                 default: batch_crs_rows<VM, 32>(m, rb, re); break;
             }
-        } else {
+        } else if constexpr (KTMAX >= 2) {
             int KT = 2;
             while (KT < min(m.k, m.rhs_tile > 0 ? min(m.rhs_tile, 32) : 16)) KT <<= 1;
+            KT = clamp_tile<KTMAX>(KT);
             for (int c0 = 0; c0 < m.k; c0 += KT) {
-                switch (KT) {
-                    case 2: batch_crs_spmm_rows<VM, 2>(m, rb, re, c0); break;
-                    case 4: batch_crs_spmm_rows<VM, 4>(m, rb, re, c0); break;
-                    case 8: batch_crs_spmm_rows<VM, 8>(m, rb, re, c0); break;
-                    case 16: batch_crs_spmm_rows<VM, 16>(m, rb, re, c0); break;
-                    default: batch_crs_spmm_rows<VM, 32>(m, rb, re, c0); break;
-                }
+                if (KT == 2) batch_crs_spmm_rows<VM, 2>(m, rb, re, c0);
+                if constexpr (KTMAX >= 4) if (KT == 4) batch_crs_spmm_rows<VM, 4>(m, rb, re, c0);
+                if constexpr (KTMAX >= 8) if (KT == 8) batch_crs_spmm_rows<VM, 8>(m, rb, re, c0);
+                if constexpr (KTMAX >= 16) if (KT == 16) batch_crs_spmm_rows<VM, 16>(m, rb, re, c0);
+                if constexpr (KTMAX >= 32) if (KT >= 32) batch_crs_spmm_rows<VM, 32>(m, rb, re, c0);
             }
         }
     } else {
         if (m.k == 1) {
             batch_jds_rows<VM, 1>(m, rb, re, 0);
-        } else {
+        } else if constexpr (KTMAX >= 2) {
             int KT = 2;
             while (KT < min(m.k, m.rhs_tile > 0 ? min(m.rhs_tile, 16) : 16)) KT <<= 1;
+            KT = clamp_tile<KTMAX>(KT);
             for (int c0 = 0; c0 < m.k; c0 += KT) {
-                switch (KT) {
-                    case 2: batch_jds_rows<VM, 2>(m, rb, re, c0); break;
-                    case 4: batch_jds_rows<VM, 4>(m, rb, re, c0); break;
-                    case 8: batch_jds_rows<VM, 8>(m, rb, re, c0); break;
-                    default: batch_jds_rows<VM, 16>(m, rb, re, c0); break;
-                }
+                if (KT == 2) batch_jds_rows<VM, 2>(m, rb, re, c0);
+                if constexpr (KTMAX >= 4) if (KT == 4) batch_jds_rows<VM, 4>(m, rb, re, c0);
+                if constexpr (KTMAX >= 8) if (KT == 8) batch_jds_rows<VM, 8>(m, rb, re, c0);
+                if constexpr (KTMAX >= 16) if (KT >= 16) batch_jds_rows<VM, 16>(m, rb, re, c0);
             }
         }
     }
 }
 
+template <int KTMAX>
 __global__ void __launch_bounds__(kBatchThreads)
 batch_kernel(const BatchMat *__restrict__ mats, const BatchWork *__restrict__ work, int64_t n_work,
              int32_t *counter, const volatile int32_t *ready, int32_t *status) {
@@ -262,9 +269,9 @@ batch_kernel(const BatchMat *__restrict__ mats, const BatchWork *__restrict__ wo
         if (w >= n_work) break;
         const BatchWork wk = work[w];
         const BatchMat m = mats[wk.mat];
-        if (m.vm == VM_F64) batch_item<VM_F64>(m, wk.rb, wk.re);
-        else if (m.vm == VM_F32C) batch_item<VM_F32C>(m, wk.rb, wk.re);
-        else batch_item<VM_F32>(m, wk.rb, wk.re);
+        if (m.vm == VM_F64) batch_item<VM_F64, KTMAX>(m, wk.rb, wk.re);
+        else if (m.vm == VM_F32C) batch_item<VM_F32C, KTMAX>(m, wk.rb, wk.re);
+        else batch_item<VM_F32, KTMAX>(m, wk.rb, wk.re);
     }
 }
 
@@ -280,6 +287,7 @@ struct gbsp_batch_s {
     const BatchWork *work = nullptr;
     const int32_t *ready = nullptr;
     int grid = 0;
+    int ktmax = 1;  // widest right-hand-side tile of the kernel instance: 1, 4 or 8
 };
 
 namespace {
@@ -445,8 +453,19 @@ gbsp_status gbsp_batch_create(int32_t n, const gbsp_batch_item *items, int32_t c
         GBSP_CUDA(cudaMemcpyAsync(const_cast<BatchWork *>(b->work), work.data(), sizeof(BatchWork) * work.size(),
                                   cudaMemcpyHostToDevice, s));
     GBSP_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
+    int kmax = 1;
+    for (int32_t i = 0; i < n; ++i) kmax = std::max(kmax, (int)items[i].k);
+    // the widest tile decides the registers, hence the CTAs per SM: 48
+    // registers for 1 (5 CTAs of 256 threads), 64 for 4 and 8 (4 CTAs),
+    // about 128 for 16 (2 CTAs); wider k runs as several 8-wide tiles
+    b->ktmax = kmax == 1 ? 1 : (kmax <= 4 ? 4 : 8);
     int per_sm = 0;
-    GBSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBatchThreads, 0));
+    if (b->ktmax == 1)
+        GBSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<1>, kBatchThreads, 0));
+    else if (b->ktmax == 4)
+        GBSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<4>, kBatchThreads, 0));
+    else
+        GBSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<8>, kBatchThreads, 0));
     b->grid = (int)std::max<int64_t>(1, std::min<int64_t>(b->n_work, (int64_t)num_sms() * std::max(per_sm, 1)));
     *out = b;
     return GBSP_OK;
@@ -457,7 +476,12 @@ gbsp_status gbsp_batch_run(gbsp_batch b, int32_t *d_status, void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (b->n_work == 0) return GBSP_OK;
     GBSP_CUDA(cudaMemsetAsync(b->counter, 0, sizeof(int32_t), s));
-    batch_kernel<<<b->grid, kBatchThreads, 0, s>>>(b->mats, b->work, b->n_work, b->counter, b->ready, d_status);
+    if (b->ktmax == 1)
+        batch_kernel<1><<<b->grid, kBatchThreads, 0, s>>>(b->mats, b->work, b->n_work, b->counter, b->ready, d_status);
+    else if (b->ktmax == 4)
+        batch_kernel<4><<<b->grid, kBatchThreads, 0, s>>>(b->mats, b->work, b->n_work, b->counter, b->ready, d_status);
+    else
+        batch_kernel<8><<<b->grid, kBatchThreads, 0, s>>>(b->mats, b->work, b->n_work, b->counter, b->ready, d_status);
     GBSP_LAUNCH_CHECK("batch_kernel");
     return GBSP_OK;
 }
