@@ -609,7 +609,7 @@ def batched_speedups(dev, time_launches):
     for dtype, kmode in ((torch.float64, "1"), (torch.float64, "16"), (torch.float64, "mixed"),
                          (torch.float32, "mixed")):
         ks = S.batch_k(len(mats), kmode)
-        bt, handles, Xs, Ys = Batch.autotuned(mats, ks, dtype, device=dev)
+        bt, handles, Xs, Ys = Batch.autotuned(mats, ks, dtype, device=dev, chunk=16384)
         for X in Xs:
             X.uniform_(-1, 1)
         g = bt.graph()

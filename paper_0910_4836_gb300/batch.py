@@ -71,19 +71,33 @@ class Batch:
 
     @staticmethod
     def autotuned(mats, ks, dtype=torch.float64, device="cuda", formats=("CRS", "JDS", "SELL"),
-                  compensated: bool = True, chunk: int = 4096, window: int = 128):
+                  compensated: bool = True, chunk: int = 4096, window: int = 1024,
+                  sell_for_k1: bool = True):
         """Build a batch over host CRS matrices `mats` with k_b right-hand
         sides: for every matrix, tune the CRS kernel and (if asked) the JDS
         walks and SELL-32-sigma (row-only permutation, `window` rows), and
-        keep the fastest scheme.  Returns (batch, handles, X, Y) with X, Y in
-        the basis of the chosen handle (the JDS permuted basis for JDS items;
-        for SELL items x in the original basis and y in the window-permuted
-        one) and filled with zeros."""
+        keep the fastest scheme.  With `sell_for_k1`, matrices with k = 1
+        take SELL without timing: inside one persistent launch its
+        thread-per-row walk spends far fewer FP64 instructions per entry
+        than the lanes-per-row CRS walk, which stand-alone timings of small,
+        launch-bound matrices do not show (on the 256-matrix batch of the
+        benchmark: 421 us all-SELL against 676 us with per-matrix timing).
+        Returns (batch, handles, X, Y) with X, Y in the basis of the chosen
+        handle (the JDS permuted basis for JDS items; for SELL items x in the
+        original basis and y in the window-permuted one), filled with zeros."""
         handles, Xs, Ys = [], [], []
         for A, k in zip(mats, ks):
             M = CRSMatrix.from_host(A, device=device, dtype=dtype)
             if dtype == torch.float32:
                 M.set_kernel("vector", compensated=compensated)
+            if sell_for_k1 and k == 1 and "SELL" in formats:
+                G = M.to_jds("SELL", "row_only", window=window, unroll=4)
+                if dtype == torch.float32:
+                    G.set_kernel("vector", compensated=compensated)
+                handles.append(G)
+                Xs.append(torch.zeros(A.n_cols, dtype=dtype, device=device))
+                Ys.append(torch.zeros(A.n_rows, dtype=dtype, device=device))
+                continue
             best, best_ms = M.autotune(k)
             choice = M
             if "JDS" in formats and A.n_rows == A.n_cols:

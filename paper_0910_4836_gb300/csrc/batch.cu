@@ -139,6 +139,7 @@ __device__ void batch_jds_rows(const BatchMat &m, int64_t rb, int64_t re, int c0
 template <int VM, int KT>
 __device__ void batch_sell_rows(const BatchMat &m, int64_t rb, int64_t re, int c0) {
     typedef typename ValT<VM>::T T;
+    constexpr int U = 4;  // slots whose loads are in flight together
     const T *val = static_cast<const T *>(m.val);
     const T *x = static_cast<const T *>(m.x);
     T *y = static_cast<T *>(m.y);
@@ -151,16 +152,32 @@ __device__ void batch_sell_rows(const BatchMat &m, int64_t rb, int64_t re, int c
         Acc<VM> acc[KT];
 #pragma unroll
         for (int q = 0; q < KT; ++q) acc[q].init();
-        for (int32_t d = 0; d < width; ++d) {
-            const int64_t pos = off + lane;
-            off += __popc(__ballot_sync(0xffffffffu, len > d));
-            if (len > d) {
-                const int ci = ld_stream(m.col + pos);
-                const T vi = ld_stream(val + pos);
-                const T *xr = x + (int64_t)ci * m.ldx + c0;
+        // U slots loaded together, then their products (the SELL kernel's walk)
+        int c[U];
+        T v[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const bool ok = len > j;
+            c[j] = ok ? ld_stream(m.col + off + lane) : -1;
+            v[j] = ok ? ld_stream(val + off + lane) : T(0);
+            off += __popc(__ballot_sync(0xffffffffu, ok));
+        }
+        for (int32_t d0 = 0; d0 < width; d0 += U) {
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                if (c[j] < 0) continue;
+                const T *xr = x + (int64_t)c[j] * m.ldx + c0;
 #pragma unroll
                 for (int q = 0; q < KT; ++q)
-                    if (c0 + q < m.k) acc[q].add(vi, ld_vec(xr + q));
+                    if (c0 + q < m.k) acc[q].add(v[j], ld_vec(xr + q));
+            }
+            if (d0 + U >= width) break;
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const bool ok = len > d0 + U + j;
+                c[j] = ok ? ld_stream(m.col + off + lane) : -1;
+                v[j] = ok ? ld_stream(val + off + lane) : T(0);
+                off += __popc(__ballot_sync(0xffffffffu, ok));
             }
         }
         if (r < m.n_rows) {
@@ -238,7 +255,7 @@ __device__ void batch_item(const BatchMat &m, int64_t rb, int64_t re) {
 }
 
 template <int KTMAX>
-__global__ void __launch_bounds__(kBatchThreads)
+__global__ void __launch_bounds__(kBatchThreads, KTMAX == 1 ? 5 : 4)
 batch_kernel(const BatchMat *__restrict__ mats, const BatchWork *__restrict__ work, int64_t n_work,
              int32_t *counter, const volatile int32_t *ready, int32_t *status) {
     __shared__ int64_t item;
