@@ -689,7 +689,7 @@ def fwd_bwd_speedup(dev, time_launches):
         key = "f64" if dtype == torch.float64 else "f32"
         res[key] = {"plain_ms": round(tp, 3), "tuned_ms": round(tt, 3), "speedup": round(tp / tt, 3),
                     "vectors_stored_plain": m + 1, "vectors_stored_tuned": m // 5 + 5,
-                    "tuned_forward": type(pt.F).__name__, "tuned_adjoint": type(pt._adj).__name__}
+                    "tuned_forward": getattr(pt.F, "fmt", "CRS"), "tuned_adjoint": getattr(pt._adj, "fmt", "CRS")}
     return res
 
 

@@ -28,9 +28,12 @@ class Pattern:
     order).  The products can run elsewhere:
       forward: "crs" -- the CRS handle; "jds" -- a JDS of A (row-only
                permutation, NUJDS walk) whose values are re-gathered when they
-               change; "auto" -- whichever the autotuner times faster.
-      adjoint: "crs" -- the CRS of A^T (transposed structure); "jds" -- a JDS
-               of A^T (the transposed-JDS form); "auto" -- the faster one.
+               change; "sell" -- SELL-32-sigma of A (row-only, window 128),
+               likewise; "auto" -- whichever of the three the autotuner times
+               fastest.
+      adjoint: "crs" -- the CRS of A^T (transposed structure); "jds" / "sell"
+               -- a JDS / SELL of A^T (the transposed-JDS form); "auto" -- the
+               fastest of the three.
     """
 
     def __init__(self, row_ptr: torch.Tensor, col: torch.Tensor, n_cols: int, dtype=torch.float64,
@@ -49,6 +52,7 @@ class Pattern:
             self.A.prepare_tiled(1024)
         self.F = None
         self._fkey = None
+        self.ST = None
         self.AT = None
         self.JT = None
         self._adj = None
@@ -71,14 +75,18 @@ class Pattern:
         if self.forward == "crs":
             return A
         if self.F is None:
-            J = A.to_jds("NUJDS", "row_only", unroll=4, value_map=True)
-            J.refresh_values(val.detach())
+            cands = []
+            if self.forward in ("jds", "auto"):
+                cands.append(A.to_jds("NUJDS", "row_only", unroll=4, value_map=True))
+            if self.forward in ("sell", "auto"):
+                cands.append(A.to_jds("SELL", "row_only", window=128, unroll=4, value_map=True))
+            for J in cands:
+                J.refresh_values(val.detach())
             if self.forward == "auto":
-                _, ms_a = A.autotune(1)
-                _, ms_j = J.autotune(1)
-                self.F = J if ms_j < ms_a else A
+                timed = [(A.autotune(1)[1], 0, A)] + [(J.autotune(1)[1], i + 1, J) for i, J in enumerate(cands)]
+                self.F = min(timed, key=lambda t: (t[0], t[1]))[2]
             else:
-                self.F = J
+                self.F = cands[0]
             self._fkey = None
         if self.F is not A:
             key = (val.data_ptr(), val._version)
@@ -100,17 +108,19 @@ class Pattern:
             if self.adjoint in ("jds", "auto"):
                 self.JT = self.AT.to_jds("NUJDS", "row_only", unroll=4, value_map=True)
                 self.JT.refresh_values(self.AT.val)
-            self._adj = self.JT if self.adjoint == "jds" else self.AT
+            if self.adjoint in ("sell", "auto"):
+                self.ST = self.AT.to_jds("SELL", "row_only", window=128, unroll=4, value_map=True)
+                self.ST.refresh_values(self.AT.val)
+            self._adj = {"jds": self.JT, "sell": self.ST}.get(self.adjoint, self.AT)
             if self.adjoint == "auto":
-                _, ms_c = self.AT.autotune(1)
-                _, ms_j = self.JT.autotune(1)
-                self._adj = self.JT if ms_j < ms_c else self.AT
+                timed = [(H.autotune(1)[1], i, H) for i, H in enumerate((self.AT, self.JT, self.ST))]
+                self._adj = min(timed, key=lambda t: (t[0], t[1]))[2]
             self._akey = None
         key = (val.data_ptr(), val._version)
         if self._akey != key:
             self.A.refresh_transpose_values()
-            if self._adj is self.JT:
-                self.JT.refresh_values(self.AT.val)
+            if self._adj is not self.AT:
+                self._adj.refresh_values(self.AT.val)
             self._akey = key
         return self._adj
 

@@ -105,7 +105,7 @@ def _pattern(A, **kw):
     return Pattern.from_host(A, **kw)
 
 
-@pytest.mark.parametrize("adjoint", ["crs", "jds"])
+@pytest.mark.parametrize("adjoint", ["crs", "jds", "sell"])
 def test_spmv_function_gradcheck(adjoint):
     from paper_0910_4836_gb300.autograd import spmv
     A = S.small_random(30, 25, 84, density=0.2)
@@ -115,7 +115,7 @@ def test_spmv_function_gradcheck(adjoint):
     assert torch.autograd.gradcheck(lambda v, xx: spmv(p, v, xx), (val, x), eps=1e-6, atol=1e-9)
 
 
-@pytest.mark.parametrize("adjoint,forward", [("crs", "crs"), ("jds", "jds"), ("auto", "auto")])
+@pytest.mark.parametrize("adjoint,forward", [("crs", "crs"), ("jds", "jds"), ("sell", "sell"), ("auto", "auto")])
 def test_power_gradients_against_oracle(adjoint, forward):
     from paper_0910_4836_gb300.autograd import power_apply
     A = S.stencil27(8, 4)
