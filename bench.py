@@ -923,10 +923,24 @@ def run_analysis(args):
 
 def run_ncu_case(args):
     """A few launches of one kernel on a 2e6-row HH-like matrix (~350 MB,
-    above the 129 MB L2) for an ncu capture; prints nothing to time."""
+    above the 129 MB L2) for an ncu capture; prints nothing to time.  With
+    --config 2: the Zipf-rows matrix (345 MB) and its NUJDS walk split at
+    depth 16 in chunks of 64."""
     import torch
     from paper_0910_4836_gb300 import CRSMatrix, build, synth as S
     build()
+    if args.config == 2:
+        A = S.config(2)
+        M = CRSMatrix.from_host(A)
+        x = torch.as_tensor(S.vector(A.n_cols, 2)).cuda()
+        y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+        J = M.to_jds("NUJDS", "row_only", unroll=2)
+        J.split(16, 64)
+        for _ in range(3):
+            J.spmv(x, out=y)
+        torch.cuda.synchronize()
+        print("ran NUJDS row_only u=2 split 16/64 on the Zipf rows")
+        return
     A = S.hh_like(2_000_000, 1)
     M = CRSMatrix.from_host(A)
     x = torch.as_tensor(S.vector(A.n_cols, 1)).cuda()
