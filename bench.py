@@ -477,7 +477,34 @@ def fp32_numbers(M, A, x, y64, dev, time_launches, ms64):
     return {"best": best[1], "speedup_vs_fp64": round(ms64 / best[0], 3), "kernels": res,
             "max_err_over_sum_abs_compensated": float(((yc - ref).abs() / den).max()),
             "max_err_over_sum_abs_plain": float(((yp - ref).abs() / den).max()),
+            "per_config": fp32_errors(dev),
             "note": "error of FP32 data and FP32 vector against the FP64 product of the FP64 data"}
+
+
+def fp32_errors(dev):
+    """Max |y32 - y64| / sum|a||x| per workload (FP32 values and vector,
+    compensated and plain row sums, against the FP64 GPU product of the
+    FP64 data): the Laplacian, the HH-like matrix, the Zipf rows and the
+    27-point stencil."""
+    import torch
+    from paper_0910_4836_gb300 import CRSMatrix, synth as S
+    out = {}
+    for i, name in ((0, "laplace_64x64"), (1, "hh_like_6M"), (2, "zipf_rows_4M"), (4, "stencil27_100^3")):
+        A = S.config(i)
+        M = CRSMatrix.from_host(A, device=dev)
+        x = torch.as_tensor(S.vector(A.n_cols, i)).to(dev)
+        ref = M.spmv(x)
+        sabs = CRSMatrix(M.row_ptr, M.col, M.val.abs(), A.n_cols).spmv(x.abs()).clamp_min(1e-300)
+        M32 = CRSMatrix(M.row_ptr, M.col, M.val.float(), A.n_cols)
+        row = {}
+        for comp in (True, False):
+            M32.set_kernel("vector", lanes=4, rows_per_warp=4, compensated=comp)
+            y = M32.spmv(x.float()).double()
+            row["compensated" if comp else "plain"] = float(((y - ref).abs() / sabs).max())
+        out[name] = row
+        del M, M32, ref, sabs
+        torch.cuda.empty_cache()
+    return out
 
 
 def symmetric_numbers(M, A, x, dev, time_launches, ms_full):
