@@ -365,3 +365,30 @@ def test_sell_staged_x_is_bit_identical(mi, perm):
             assert torch.equal(G.spmv(xp), plain)
             if dtype == torch.float64:
                 assert_close64(host(plain_o), ref, s, f"staged SELL w={w} u={u}")
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("cfg", [1, 2, 4])
+def test_full_size_step_kernels(cfg):
+    """The schemes the benchmark times, at full size and in its launch
+    configuration: every output entry against the accurate oracle (SELL-32-σ
+    σ=128 u=4 and NUJDS on the HH-like matrix and the stencil; NUJDS split
+    16/64 on the Zipf rows), and the staged-x SELL bit-identical to SELL."""
+    from gpu_util import full_config
+    A = full_config(cfg)
+    x = S.vector(A.n_cols, cfg)
+    ref, s = O.crs_spmv_exact(A, x)
+    M = crs(A)
+    xd = dev(x)
+    if cfg == 2:
+        J = M.to_jds("NUJDS", "row_only", unroll=2)
+        J.split(16, 64)
+        assert_close64(host(J.spmv_original(xd)), ref, s, "Zipf NUJDS split 16/64")
+        return
+    G = M.to_jds("SELL", "row_only", window=128, unroll=4)
+    y = host(G.spmv_original(xd))
+    assert_close64(y, ref, s, f"config {cfg} SELL w=128 u=4")
+    G.stage_x(12, 32)
+    assert np.array_equal(host(G.spmv_original(xd)), y)
+    J = M.to_jds("NUJDS", "symmetric", unroll=2)
+    assert_close64(host(J.spmv_original(xd)), ref, s, f"config {cfg} NUJDS u=2")
