@@ -20,6 +20,7 @@
 //                consecutively (diagonal-major inside the block), so a CTA
 //                streams one contiguous chunk.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <vector>
 
@@ -395,6 +396,7 @@ __global__ void __launch_bounds__(1024) sell_kernel(JdsArgs a) {
 // each x value is read from changes.  Two CTAs per SM, so one stages while
 // the other walks.
 constexpr int kStagePage = 1024;
+constexpr int kMaxDevices = 64;
 
 template <int VM, int U>
 __global__ void __launch_bounds__(1024, 2) sell_staged_kernel(JdsArgs a, const int32_t *__restrict__ col_st,
@@ -670,12 +672,19 @@ static gbsp_status launch_sell_staged_U(const Mat &A, JdsArgs a, cudaStream_t s)
     typedef typename ValT<VM>::T T;
     const int P = A.stage_pages_per_group;
     const int smem = P * kStagePage * (int)sizeof(T);
-    static int configured = 0;  // largest dynamic shared memory set so far for this kernel
-    if (smem > configured) {
+    // largest dynamic shared memory set so far for this kernel, per device
+    static std::atomic<int> configured[kMaxDevices];
+    int dev = 0;
+    GBSP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices || smem > configured[dev].load()) {
         GBSP_CUDA(cudaFuncSetAttribute(sell_staged_kernel<VM, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         GBSP_CUDA(cudaFuncSetAttribute(sell_staged_kernel<VM, U>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        100));
-        configured = smem;
+        if (dev >= 0 && dev < kMaxDevices) {
+            int cur = configured[dev].load();
+            while (cur < smem && !configured[dev].compare_exchange_weak(cur, smem)) {
+            }
+        }
     }
     const int64_t ngroups = ceil_div(ceil_div(a.n_rows, 32), 32);
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ngroups, (int64_t)num_sms() * 2));
