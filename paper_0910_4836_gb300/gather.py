@@ -40,6 +40,10 @@ class GatherSum:
         self.n_partials = partials_needed(self.n)
         self.partials = torch.empty(self.n_partials, dtype=torch.float64, device=dev)
         self.out = torch.zeros(1, dtype=torch.float64, device=dev)
+        if status is not None:
+            status = _need_cuda(status, "status", torch.int32)
+            if status.numel() < 1:
+                raise ValueError("status must hold one int32")
         self.status = status
 
     def __call__(self, stream=None) -> torch.Tensor:
