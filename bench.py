@@ -396,6 +396,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(gbs / peak, 4), "traffic": traffic,
+                         "frac_of_8tbs_spec": round(gbs / 8000.0, 4),
                          "algorithmic_bytes": alg, "peak_source": f"{peak_kind} hbm_gbs (burst)",
                          "kernel_source_hash": h},
             "e2e": {"value": round(world * flops / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GFlop/s",
