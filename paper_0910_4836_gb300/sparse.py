@@ -422,6 +422,8 @@ class HybridMatrix:
         R._device, R._tile_table, R._transpose = dev, None, None
         self.dia_part, self.remainder = D, R
         self.n_rows, self.n_cols, self.dtype = A.n_rows, A.n_cols, A.dtype
+        # the remainder sums like the source handle (plain or compensated FP32)
+        R.set_kernel("vector", compensated=A.kernel_opts()["accum"] == L.ACC_COMPENSATED)
         self.rem_op = None
         if self.nnz_rem > 0:
             self.rem_op = R.to_jds("SELL", "row_only", window=window, unroll=unroll) if remainder == "SELL" else R

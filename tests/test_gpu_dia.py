@@ -88,3 +88,23 @@ def test_hybrid_rejections():
         H.dia_part.spmm(dev(np.ones((256, 2))))
     with pytest.raises(GbspError):
         H.dia_part.spmv(dev(np.ones(256)), transpose=True)
+
+
+def test_hybrid_fp32_compensated_within_dot2_bound():
+    """FP32 values with compensated row sums through DIA + remainder: within
+    the Dot2 bound of the exact product of the FP32-rounded data."""
+    from gpu_util import dot2_bound
+    from paper_0910_4836_gb300 import HybridMatrix
+    A = S.hh_diagonals(200_000, 12)
+    A32 = A.astype(np.float32)
+    x32 = S.vector(A.n_cols, 13).astype(np.float32)
+    ref, s = O.crs_spmv_exact(A32.astype(np.float64), x32.astype(np.float64))
+    M = crs(A, torch.float32)
+    M.set_kernel("vector", compensated=True)
+    for remainder in ("CRS", "SELL"):
+        H = HybridMatrix(M, 16, 2.0 / 3.0, remainder=remainder)
+        y = host(H.spmv(dev(x32))).astype(np.float64)
+        lens = np.diff(A.row_ptr.astype(np.int64))
+        # the DIA sum is rounded to FP32 once before the remainder is added
+        bound = dot2_bound(ref, s, lens) + 2.0 ** -24 * s
+        assert np.all(np.abs(y - ref) <= bound), remainder

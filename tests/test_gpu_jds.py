@@ -392,3 +392,21 @@ def test_full_size_step_kernels(cfg):
     assert np.array_equal(host(G.spmv_original(xd)), y)
     J = M.to_jds("NUJDS", "symmetric", unroll=2)
     assert_close64(host(J.spmv_original(xd)), ref, s, f"config {cfg} NUJDS u=2")
+
+
+def test_psell_fp32_compensated_and_spmm():
+    """Paired SELL in FP32 with compensated sums: within the Dot2 bound of
+    the exact product of the FP32-rounded data, for one and several RHS."""
+    from gpu_util import dot2_bound
+    A = S.hh_like(50_000, 61)
+    A32 = A.astype(np.float32)
+    M = crs(A, torch.float32)
+    M.set_kernel("vector", compensated=True)
+    G = M.to_jds("PSELL", "row_only", window=128, unroll=4)
+    G.set_kernel("vector", compensated=True)
+    lens = np.diff(A.row_ptr.astype(np.int64))
+    X = np.stack([S.vector(A.n_cols, 62 + c).astype(np.float32) for c in range(4)], axis=1)
+    Y = host(G.spmm(dev(X), basis=1)).astype(np.float64)
+    for c in range(4):
+        ref, s = O.crs_spmv_exact(A32.astype(np.float64), X[:, c].astype(np.float64))
+        assert np.all(np.abs(Y[:, c] - ref) <= dot2_bound(ref, s, lens)), c
