@@ -908,6 +908,31 @@ def run_analysis(args):
         t = statistics.median(time_launches(lambda: H.spmv(xin, out=y), 10))
         out["sweep"][name] = {"us": round(t * 1e3, 1), "gflops": round(2.0 * A.nnz / (t * 1e-3) / 1e9, 1)}
 
+    # throughput against the number of CTAs in use (the GPU counterpart of
+    # the paper's performance against threads per socket, Sect. 5)
+    out["cta_scaling"] = {}
+    alg = 12 * A.nnz + 20 * A.n_rows
+
+    def scaling(name, H, xin, limits):
+        row = {}
+        for lim in limits:
+            H.set_grid_limit(lim)
+            t = statistics.median(time_launches(lambda: H.spmv(xin, out=y), 10))
+            row[str(lim or "all")] = {"us": round(t * 1e3, 1), "gbs": round(alg / (t * 1e-3) / 1e9, 1)}
+        H.set_grid_limit(0)
+        out["cta_scaling"][name] = row
+
+    G = M.to_jds("SELL", "row_only", window=128, unroll=4)
+    scaling("SELL w=128 u=4 (1024-thread CTAs, at most 2 per SM)", G, x,
+            (8, 16, 32, 48, 64, 76, 96, 128, 152, 228, 304, 0))
+    del G
+    J = M.to_jds("NUJDS", "row_only", unroll=2)
+    scaling("NUJDS u=2 (256-thread CTAs)", J, x, (38, 76, 152, 304, 608, 1216, 2432, 0))
+    del J
+    M.set_kernel("vector", lanes=4, rows_per_warp=4)
+    scaling("CRS vector l4 r4 (256-thread CTAs)", M, x, (38, 76, 152, 304, 608, 1216, 2432, 0))
+    torch.cuda.empty_cache()
+
     strides("CRS", M.col)
     for l, r in ((1, 1), (2, 2), (4, 4), (8, 2), (16, 2), (32, 1)):
         if r == 1 or l in (2, 4):

@@ -251,6 +251,14 @@ gbsp_status gbsp_jds_build(gbsp_handle crs, const gbsp_jds_opts *opts,
                            const gbsp_jds_buffers *bufs, const gbsp_jds_sizes *sizes,
                            void *stream, gbsp_handle *out);
 
+/* Cap the grid (number of CTAs) of the handle's SELL, JDS / NUJDS walk and
+ * CRS VECTOR product kernels at max_ctas (0 removes the cap).  A measurement
+ * knob, the GPU counterpart of running the paper's OpenMP kernels on fewer
+ * threads (Sect. 5, intra-socket scaling): the SELL kernel places at most
+ * two 1024-thread CTAs per SM, the others up to eight 256-thread CTAs.
+ * Host-side only.  Errors: GBSP_ERR_ARG for a negative cap. */
+gbsp_status gbsp_set_grid_limit(gbsp_handle h, int32_t max_ctas);
+
 /* Switch a built JDS-family handle between the formats that share its
  * storage pattern (JDS <-> NBJDS <-> NUJDS <-> JDS_LITERAL) and set block
  * or unroll.  RBJDS / SOJDS handles accept only a block size equal to the

@@ -112,6 +112,7 @@ SIGNATURES = {
                                       c_vp]),
     "gbsp_gather_partials": (c_i32, [c_i64, ctypes.POINTER(c_i32)]),
     "gbsp_stride_hist": (c_i32, [c_vp, c_i64, c_vp, c_vp]),
+    "gbsp_set_grid_limit": (c_i32, [c_vp, c_i32]),
     "gbsp_sell_stage_bytes": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64),
                                       ctypes.POINTER(c_i64)]),
     "gbsp_sell_stage": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_i64, c_vp]),

@@ -275,6 +275,12 @@ gbsp_status gbsp_jds_build(gbsp_handle crs, const gbsp_jds_opts *opts, const gbs
     return GBSP_OK;
 }
 
+gbsp_status gbsp_set_grid_limit(gbsp_handle h, int32_t max_ctas) {
+    if (!h || max_ctas < 0) return arg_error("gbsp_set_grid_limit: bad arguments");
+    h->grid_limit = max_ctas;
+    return GBSP_OK;
+}
+
 gbsp_status gbsp_jds_set_format(gbsp_handle h, int32_t format, int32_t block, int32_t unroll) {
     if (!h) return arg_error("gbsp_jds_set_format: NULL handle");
     if (h->kind != KIND_JDS || !is_jds_family(format))

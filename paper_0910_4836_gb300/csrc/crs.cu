@@ -180,7 +180,7 @@ template <int VM, int L>
 static void launch_vector_R(const Mat &A, const VecArgs &v, int R, cudaStream_t s) {
     typedef typename ValT<VM>::T T;
     const int64_t rw = (32 / L) * R;
-    const int grid = grid_for(ceil_div(A.n_rows, rw));
+    const int grid = (int)limit_grid(grid_for(ceil_div(A.n_rows, rw)), A.grid_limit);
     auto *val = static_cast<const T *>(A.val);
     auto *x = static_cast<const T *>(v.x);
     auto *y = static_cast<T *>(v.y);

@@ -37,6 +37,11 @@ struct Mat {
     // optional device status word for bounded-wait timeouts
     int32_t *status = nullptr;
 
+    // largest grid (CTAs) of the SELL, JDS-walk and CRS-vector product
+    // kernels; 0 = no limit (a measurement knob: throughput against the
+    // number of CTAs in use)
+    int32_t grid_limit = 0;
+
     // JDS family
     int format = GBSP_CRS;
     int perm_mode = GBSP_PERM_SYMMETRIC;
@@ -110,6 +115,9 @@ inline int num_sms() {
 }
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// a launcher's grid under a handle's grid limit (0 = none)
+inline int64_t limit_grid(int64_t grid, int32_t limit) { return limit > 0 && grid > limit ? limit : grid; }
 
 // device exclusive scan of int32 (convert.cu): out[0..n) = exclusive scan of
 // in, *total_out = the total when given; ws holds scan_ws_bytes(n) bytes

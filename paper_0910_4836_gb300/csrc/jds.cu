@@ -52,6 +52,7 @@ struct JdsArgs {
     void *split_shallow;   // walk sums of the rows that go deeper than d_limit
     int64_t split_rows;    // those rows: [0, split_rows)
     int64_t n_cols;
+    int32_t grid_limit;    // 0 = none
 };
 
 __device__ __forceinline__ int64_t xidx(const int32_t *x_perm, int32_t c) {
@@ -595,9 +596,12 @@ static int row_grid(int64_t rows) {
 
 template <int VM, int U>
 static void launch_row(const JdsArgs &a, int R, cudaStream_t s) {
-    if (R >= 4) jds_row_kernel<VM, U, 4><<<row_grid(ceil_div(a.n_rows, 4)), 256, 0, s>>>(a);
-    else if (R >= 2) jds_row_kernel<VM, U, 2><<<row_grid(ceil_div(a.n_rows, 2)), 256, 0, s>>>(a);
-    else jds_row_kernel<VM, U, 1><<<row_grid(a.n_rows), 256, 0, s>>>(a);
+    const unsigned g4 = (unsigned)limit_grid(row_grid(ceil_div(a.n_rows, 4)), a.grid_limit);
+    const unsigned g2 = (unsigned)limit_grid(row_grid(ceil_div(a.n_rows, 2)), a.grid_limit);
+    const unsigned g1 = (unsigned)limit_grid(row_grid(a.n_rows), a.grid_limit);
+    if (R >= 4) jds_row_kernel<VM, U, 4><<<g4, 256, 0, s>>>(a);
+    else if (R >= 2) jds_row_kernel<VM, U, 2><<<g2, 256, 0, s>>>(a);
+    else jds_row_kernel<VM, U, 1><<<g1, 256, 0, s>>>(a);
 }
 
 template <int VM, bool CONTIG>
@@ -626,7 +630,8 @@ template <int VM, int U>
 static void launch_sell_U(JdsArgs a, int KT, cudaStream_t s) {
     const int64_t nb = ceil_div(a.n_rows, 32);
     const int threads = 1024;
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(nb * 32, threads), (int64_t)num_sms() * 2));
+    const int64_t grid = limit_grid(
+        std::max<int64_t>(1, std::min<int64_t>(ceil_div(nb * 32, threads), (int64_t)num_sms() * 2)), a.grid_limit);
     switch (KT) {
         case 1: sell_kernel<VM, U, 1><<<(unsigned)grid, threads, 0, s>>>(a); break;
         case 2: sell_kernel<VM, U, 2><<<(unsigned)grid, threads, 0, s>>>(a); break;
@@ -819,6 +824,7 @@ gbsp_status jds_launch(const Mat &A, const VecArgs &v, cudaStream_t s) {
     a.split_rows = 0;
     a.split_shallow = nullptr;
     a.n_cols = A.n_cols;
+    a.grid_limit = A.grid_limit;
     gbsp_status st;
     if (A.dtype == GBSP_F64) st = launch_family<VM_F64>(A, a, s);
     else if (A.kopt.accum == GBSP_ACC_COMPENSATED) st = launch_family<VM_F32C>(A, a, s);

@@ -105,6 +105,11 @@ class _Product(_Handle):
                 "gbsp_spmv_symmetric")
         return out
 
+    def set_grid_limit(self, max_ctas: int = 0) -> None:
+        """Cap the product kernel's grid at max_ctas CTAs (0: no cap); for
+        throughput-against-CTAs measurements."""
+        L.check(L.load().gbsp_set_grid_limit(self._h, int(max_ctas)), "gbsp_set_grid_limit")
+
     def set_kernel(self, kernel: str = "vector", lanes: int = 0, rows_per_warp: int = 0,
                    tile: int = 0, rhs_tile: int = 0, compensated: bool | None = None) -> None:
         o = L.KernelOpts()
