@@ -9,7 +9,7 @@ import torch
 import oracle as O
 from paper_0910_4836_gb300 import synth as S
 
-# FP64 acceptance per entry (spec tolerance): |y - y_ref| <= 1e-14 * sum_j |a_ij||x_j|
+# FP64 acceptance per entry: |y - y_ref| <= 1e-14 * sum_j |a_ij||x_j|
 TOL64 = 1e-14
 U32 = 2.0 ** -24
 
