@@ -451,11 +451,13 @@ def fp32_numbers(M, A, x, y64, dev, time_launches, ms64):
     J32 = M32.to_jds("NUJDS", "symmetric", unroll=4)
     xp32 = J32.permute(x32)
     G32 = M32.to_jds("SELL", "row_only", window=128, unroll=4)
+    G32w = M32.to_jds("SELL", "row_only", window=1024, unroll=4)
     res = {}
     opts = [("CRS vector l4 r4", M32, x32, lambda: M32.set_kernel("vector", lanes=4, rows_per_warp=4)),
             ("CRS tiled 1024", M32, x32, lambda: M32.prepare_tiled(1024)),
             ("NUJDS symmetric u=4", J32, xp32, lambda: None),
-            ("SELL row_only w=128 u=4", G32, x32, lambda: None)]
+            ("SELL row_only w=128 u=4", G32, x32, lambda: None),
+            ("SELL row_only w=1024 u=4", G32w, x32, lambda: None)]
     best = None
     for name, H, xin, conf in opts:
         conf()
