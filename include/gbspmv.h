@@ -156,12 +156,14 @@ gbsp_status gbsp_set_status_word(gbsp_handle h, int32_t *d_status);
 
 /* Create a CRS handle (Sect. 2, "compressed row storage": val, col_idx and
  * row_ptr, row i owning entries row_ptr[i] .. row_ptr[i+1]-1).
- *   n_rows, n_cols >= 0, nnz >= 0 (nnz < 2^31).
+ *   0 <= n_rows, n_cols < 2^31 - 1 and 0 <= nnz <= 2^31 - 2^16 - 1: the
+ *   int32 index arrays, with 2^16 entries of headroom for padded layouts.
  *   d_row_ptr: int32[n_rows+1], d_col: int32[nnz], d_val: double[nnz]
  *   (GBSP_F64) or float[nnz] (GBSP_F32).  d_col and d_val may be NULL only
  *   when nnz == 0.  Entries inside a row may be in any column order.
  * Borrowed pointers; nothing is read here (no device work).  Errors:
- * GBSP_ERR_ARG on negative sizes, NULL pointers or a bad dtype. */
+ * GBSP_ERR_ARG on sizes outside those ranges, NULL pointers, misaligned
+ * arrays or a bad dtype. */
 gbsp_status gbsp_crs_create(int64_t n_rows, int64_t n_cols, int64_t nnz,
                             const int32_t *d_row_ptr, const int32_t *d_col,
                             const void *d_val, gbsp_dtype dtype, gbsp_handle *out);
@@ -245,8 +247,11 @@ gbsp_status gbsp_jds_plan(gbsp_handle crs, const gbsp_jds_opts *opts, int32_t *d
  * columns read x with stride one where possible (nearest-column greedy:
  * slot d of row r takes the unplaced entry whose column is closest to
  * 1 + the column in slot d of row r-1, ties to the smaller column; the first
- * row of a block keeps its order).  Output arrays are bit-exact functions of
- * the input.  `bufs` sizes must match gbsp_jds_plan. */
+ * row of a block keeps its order).  SELL / PSELL sort only inside windows of
+ * `window` rows (stable, decreasing length); when the (window, length) pair
+ * does not fit one 32-bit radix key, the sort runs as two stable passes,
+ * length first, then window.  Output arrays are bit-exact functions of the
+ * input.  `bufs` sizes must match gbsp_jds_plan. */
 gbsp_status gbsp_jds_build(gbsp_handle crs, const gbsp_jds_opts *opts,
                            const gbsp_jds_buffers *bufs, const gbsp_jds_sizes *sizes,
                            void *stream, gbsp_handle *out);

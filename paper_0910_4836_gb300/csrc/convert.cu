@@ -218,14 +218,18 @@ static SortWs carve_sort_ws(char *&p, int64_t n) {
     return w;
 }
 
-// Sorts keys[0..n) (bits significant bits) with values = original index.
+// Sorts keys[0..n) (bits significant bits) carrying values vals0[0..n)
+// (the original index when vals0 is NULL; vals0 is only read, and must not
+// be one of the workspace's value buffers).
 // Result: *keys_out / *vals_out point at the buffer holding the sorted pairs.
-static gbsp_status radix_sort_index(uint32_t *keys, int64_t n, int bits, SortWs &w,
+static gbsp_status radix_sort_pairs(uint32_t *keys, const int32_t *vals0, int64_t n, int bits, SortWs &w,
                                     cudaStream_t s, uint32_t **keys_out, int32_t **vals_out) {
     const int64_t tiles = ceil_div(std::max<int64_t>(n, 1), kSortTile);
     uint32_t *ka = keys, *kb = w.keys_b;
-    int32_t *va = nullptr, *vb = w.vals_a;
+    const int32_t *va = vals0;
+    int32_t *vb = w.vals_a;
     int32_t *vspare = w.vals_b;
+    bool va_in_ws = false;
     if (bits <= 0) bits = 1;
     for (int shift = 0; shift < bits; shift += 8) {
         radix_hist_kernel<<<(unsigned)tiles, kSortThreads, 0, s>>>(ka, n, shift, tiles, w.hist);
@@ -235,14 +239,21 @@ static gbsp_status radix_sort_index(uint32_t *keys, int64_t n, int bits, SortWs 
                                                                       w.hist, kb, vb);
         GBSP_LAUNCH_CHECK("radix_scatter_kernel");
         std::swap(ka, kb);
-        // values: the buffer just written becomes the input; pick a free one
+        // values: the buffer just written becomes the input; the next output
+        // is the workspace buffer not being read
         int32_t *written = vb;
-        vb = (va == nullptr) ? vspare : va;
+        vb = va_in_ws ? const_cast<int32_t *>(va) : vspare;
         va = written;
+        va_in_ws = true;
     }
     *keys_out = ka;
-    *vals_out = va;
+    *vals_out = const_cast<int32_t *>(va);
     return GBSP_OK;
+}
+
+static gbsp_status radix_sort_index(uint32_t *keys, int64_t n, int bits, SortWs &w,
+                                    cudaStream_t s, uint32_t **keys_out, int32_t **vals_out) {
+    return radix_sort_pairs(keys, nullptr, n, bits, w, s, keys_out, vals_out);
 }
 
 // Sort of bare keys (the values, the original positions, are not needed):
@@ -457,6 +468,13 @@ __global__ void sell_key_kernel(int64_t n, const int32_t *__restrict__ len, int3
     if (i < n) keys[i] = ((uint32_t)(i / window) << lbits) | (uint32_t)(max_len - len[i]);
 }
 
+// Second key of the two-stage SELL sort: the window of the row now at r.
+__global__ void window_key_kernel(int64_t n, const int32_t *__restrict__ rows, int64_t window,
+                                  uint32_t *keys) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) keys[r] = (uint32_t)(rows[r] / window);
+}
+
 __global__ void sell_rlen_kernel(int64_t n, const int32_t *__restrict__ perm,
                                  const int32_t *__restrict__ len, int32_t *rlen) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -618,10 +636,6 @@ gbsp_status jds_plan_impl(const Mat &A, const gbsp_jds_opts &o, int32_t *d_scrat
                       o.format == GBSP_PSELL ? "PSELL" : "SELL", (int)rows_per_block);
             return GBSP_ERR_ARG;
         }
-        if (bits_for((uint64_t)std::max<int64_t>(A.n_rows - 1, 0) / window) + bits_for((uint64_t)max_len) > 32) {
-            set_error("gbsp_jds_plan: SELL sort key exceeds 32 bits; use a larger window");
-            return GBSP_ERR_UNSUPPORTED;
-        }
         out->n_blocks = ceil_div(A.n_rows, rows_per_block);
         out->workspace_bytes = align256(4 * A.n_rows) * 2 + sort_ws_bytes(A.n_rows) +
                                align256(4 * (out->n_blocks + 1)) + align256(scan_ws_bytes(out->n_blocks + 1)) + 256;
@@ -706,11 +720,26 @@ static gbsp_status sell_build_impl(const Mat &A, const gbsp_jds_opts &o, const g
         row_len_kernel<<<gr, 256, 0, s>>>(n, A.row_ptr, len, max_len_d);
         const int lbits = bits_for((uint64_t)sz.n_diag);
         const int wbits = bits_for((uint64_t)(n - 1) / window);
-        sell_key_kernel<<<gr, 256, 0, s>>>(n, len, (int32_t)sz.n_diag, window, lbits, keys);
-        GBSP_LAUNCH_CHECK("sell keys");
         uint32_t *ks = nullptr;
         int32_t *vs = nullptr;
-        gbsp_status st = radix_sort_index(keys, n, lbits + wbits, sw, s, &ks, &vs);
+        gbsp_status st;
+        if (lbits + wbits <= 32) {
+            // one sort on (window, max_len - len)
+            sell_key_kernel<<<gr, 256, 0, s>>>(n, len, (int32_t)sz.n_diag, window, lbits, keys);
+            GBSP_LAUNCH_CHECK("sell keys");
+            st = radix_sort_index(keys, n, lbits + wbits, sw, s, &ks, &vs);
+        } else {
+            // the pair does not fit 32 bits: stable sort by length, then a
+            // stable sort of that order by window (least significant first)
+            len_key_kernel<<<gr, 256, 0, s>>>(n, len, (int32_t)sz.n_diag, keys);
+            GBSP_LAUNCH_CHECK("sell length keys");
+            st = radix_sort_index(keys, n, lbits, sw, s, &ks, &vs);
+            if (st != GBSP_OK) return st;
+            GBSP_CUDA(cudaMemcpyAsync(b.perm, vs, 4 * n, cudaMemcpyDeviceToDevice, s));
+            window_key_kernel<<<gr, 256, 0, s>>>(n, b.perm, window, keys);
+            GBSP_LAUNCH_CHECK("sell window keys");
+            st = radix_sort_pairs(keys, b.perm, n, wbits, sw, s, &ks, &vs);
+        }
         if (st != GBSP_OK) return st;
         if (paired)
             psell_pair_kernel<<<gr, 256, 0, s>>>(n, window, vs, b.perm);

@@ -462,6 +462,74 @@ def small_random(n_rows: int, n_cols: int, seed: int, density: float = 0.05,
     return from_coo(n_rows, n_cols, r[keep], c[keep], vals[keep], name=f"small_{n_rows}x{n_cols}")
 
 
+def long_rows(n: int, long_lengths, seed: int, short_max: int = 6) -> CRS:
+    """``n`` rows of U{0..short_max} entries plus, at rows spread through the
+    matrix, rows of the given (long) lengths; uniform random columns.  Rows
+    longer than 2^17 entries with more than 2^15 windows push the windowed
+    length sort of SELL past a 32-bit key."""
+    lens = randint(seed, 71, np.arange(n), 0, short_max).astype(np.int64)
+    at = [(k + 1) * n // (len(long_lengths) + 1) for k in range(len(long_lengths))]
+    for r, l in zip(at, long_lengths):
+        lens[r] = min(int(l), n)
+    rows = np.repeat(np.arange(n, dtype=np.int64), lens)
+    t = np.arange(rows.size)
+    cols = randint(seed, 72, t, 0, n - 1).astype(np.int64)
+    for r, l in zip(at, long_lengths):  # the long rows: distinct columns
+        sel = rows == r
+        cols[sel] = (r + np.arange(sel.sum(), dtype=np.int64) * 7) % n
+    vals = uniform(seed, 73, t, -1.0, 1.0)
+    return from_coo(n, n, rows, cols, vals, name=f"long_rows_{n}")
+
+
+# ----------------------------------------------------- index-limit matrix --
+# The largest matrix whose CRS fits the int32 index arrays the library takes:
+# nnz = 2^31 - 2^16 - 1 (the library keeps 2^16 entries of headroom), on
+# 2^24 rows of ragged length 7..248.  Entries are closed-form functions of
+# (row, position in row), so any row can be regenerated on the host, and the
+# whole matrix on the device, from the same expressions.  The functions take
+# int64 numpy arrays or int64 torch tensors alike.
+LIMIT_NNZ = 2 ** 31 - 2 ** 16 - 1
+LIMIT_ROWS = 2 ** 24
+
+
+def limit_lengths(i):
+    """Row lengths: pairs (2p, 2p+1) get 128 +/- h(p), h in [-120, 120], so
+    each pair holds 256 entries; the first 2^16 + 1 rows lose one entry."""
+    h = ((i // 2) * 2654435761) % 241 - 120
+    return 128 + (1 - 2 * (i % 2)) * h - (i < 2 ** 16 + 1) * 1
+
+
+def limit_cols(i, j):
+    """Column of entry j of row i: distinct within a row (131 is odd); rows
+    whose columns wrap past the last column are not sorted, which CRS
+    allows."""
+    return (i * 7 + j * 131 + 1000) % LIMIT_ROWS
+
+
+def limit_vals(i, j):
+    """Integer values in [-3, 3]."""
+    return (i + 3 * j) % 7 - 3
+
+
+def limit_x(c):
+    """Integer x in [-5, 5]; with the values above every row sum is an
+    integer below 2^12, exact in any summation order."""
+    return c % 11 - 5
+
+
+def limit_rows_crs(rows) -> CRS:
+    """Only the given rows of the index-limit matrix, as a CRS with one row
+    per requested row and the full column range (host side)."""
+    rows = np.asarray(rows, dtype=np.int64)
+    lens = limit_lengths(rows)
+    rp = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum(lens, out=rp[1:])
+    r = np.repeat(rows, lens)
+    j = np.arange(rp[-1], dtype=np.int64) - np.repeat(rp[:-1], lens)
+    return CRS(len(rows), LIMIT_ROWS, rp.astype(np.int32), limit_cols(r, j).astype(np.int32),
+               limit_vals(r, j).astype(np.float64), "limit_rows")
+
+
 def config(i: int) -> CRS:
     """The five workload matrices by index (0: Laplacian 64x64, 1: HH-like
     N=6e6, 2: Zipf rows N=4e6, 4: 27-point stencil 100^3).  Index 3 is the

@@ -56,6 +56,11 @@ def test_host_side_checks_without_gpu():
     assert L.gbsp_crs_create(4, 4, 0, None, None, None, 0, ctypes.byref(h)) == -1
     assert L.gbsp_crs_create(4, 4, 0, ctypes.c_void_p(256), None, None, 7, ctypes.byref(h)) == -1
     assert b"dtype" in L.gbsp_last_error()
+    # the largest nnz the int32 index arrays admit is 2^31 - 2^16 - 1
+    p = ctypes.c_void_p(256)
+    assert L.gbsp_crs_create(4, 4, 2 ** 31 - 2 ** 16, p, p, p, 0, ctypes.byref(h)) == -1
+    assert b"int32" in L.gbsp_last_error()
+    assert L.gbsp_crs_create(2 ** 31 - 1, 4, 0, p, None, None, 0, ctypes.byref(h)) == -1
     assert L.gbsp_spmv(None, 0, 0, 0, None, None, None) == -1
     assert L.gbsp_destroy(None) == 0
 

@@ -334,6 +334,49 @@ def test_sell_windows(window):
     assert np.array_equal(y, O.crs_spmv(Ai, xi))
 
 
+def test_sell_windows_with_rows_longer_than_2_17():
+    """The matrix the GPU tests use for SELL sort keys wider than 32 bits:
+    the oracle's builder still keeps every row in its window, longest
+    first, ties in row order, and reproduces the exact product."""
+    A = S.long_rows(2 ** 20 + 100, [140_001, 70_001], 5)
+    lens = A.row_lengths()
+    assert lens.max() == 140_001 and A.n_rows // 32 >= 2 ** 15
+    for window in (32, 64):
+        Sl = O.sell_build(A, window, symmetric=False)
+        assert np.all(Sl.perm // window == np.arange(A.n_rows) // window)
+        # along the permuted order: windows ascending, lengths descending
+        # inside a window, equal lengths in ascending row order
+        key = (np.arange(A.n_rows, dtype=np.int64) // window) * 2 ** 20 - lens[Sl.perm]
+        step = np.diff(key)
+        assert np.all(step >= 0)
+        assert np.all(np.diff(Sl.perm)[step == 0] > 0)
+        assert Sl.blk_ptr[-1] == A.nnz
+    Ai = S.integer_values(A, 95, 1000)
+    xi = S.int_vector(A.n_cols, 95, 1000)
+    Si = O.sell_build(Ai, 32, symmetric=False)
+    y = np.zeros(A.n_rows)
+    y[Si.perm] = O.sell_spmv(Si, xi)
+    assert np.array_equal(y, O.crs_spmv(Ai, xi))
+
+
+def test_index_limit_matrix_closed_forms():
+    """The index-limit generator: exactly 2^31 - 2^16 - 1 entries on 2^24
+    rows of length 7..248, distinct columns in a row, and every row sum an
+    integer below 2^12 in magnitude (exact in any order)."""
+    i = np.arange(S.LIMIT_ROWS, dtype=np.int64)
+    L = S.limit_lengths(i)
+    assert int(L.sum()) == S.LIMIT_NNZ == 2 ** 31 - 2 ** 16 - 1
+    assert L.min() == 7 and L.max() == 248
+    assert np.all(L[0::2] + L[1::2] == 256 - (i[0::2] < 2 ** 16 + 1) - (i[1::2] < 2 ** 16 + 1))
+    rows = np.array([0, 5, 2 ** 16, S.LIMIT_ROWS - 1])
+    sub = S.limit_rows_crs(rows)
+    for k, r in enumerate(rows):
+        c = sub.col[sub.row_ptr[k]:sub.row_ptr[k + 1]]
+        assert len(np.unique(c)) == len(c) == L[r]
+    assert np.abs(sub.val).max() <= 3 and np.abs(S.limit_x(i)).max() <= 5
+    assert 248 * 3 * 5 < 2 ** 12
+
+
 # ------------------------------------------------------------ SOJDS -----
 
 def test_sojds_is_row_permutation_and_same_product():
