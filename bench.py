@@ -203,7 +203,7 @@ def kernel_source_hash(kname: str = "SELL") -> str:
 # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
 # a one-pass metric set), keyed by (config, kernel, source hash); a different
 # hash means the kernel changed since and traffic is reported null.
-NCU_TRAFFIC = {(1, "SELL row_only w=128 u=4", "1b12b012ead3"): 1143719168 + 40403200}
+NCU_TRAFFIC = {(1, "SELL row_only w=128 u=4", "57e240a09895"): 1136425472 + 40599552}
 
 
 # --------------------------------------------------------------- ours ------

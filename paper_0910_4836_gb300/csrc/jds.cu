@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(256) jds_block_kernel(JdsArgs a) {
 // 1024-row window at a time and its gathers of x stay local.  U slots per
 // step; KT right-hand sides per thread (SpMM).  Row entries are added in
 // slot order, as in every JDS-family kernel.
-template <int VM, int U, int KT>
+template <int VM, int U, int KT, bool PLAIN>
 __global__ void __launch_bounds__(1024) sell_kernel(JdsArgs a) {
     typedef typename ValT<VM>::T T;
     const T *__restrict__ val = static_cast<const T *>(a.val);
@@ -329,23 +329,29 @@ __global__ void __launch_bounds__(1024) sell_kernel(JdsArgs a) {
     const int64_t nb = ceil_div_dev(a.n_rows, 32);
     const int wpc = blockDim.x >> 5;  // warps per CTA
     const int wid = threadIdx.x >> 5;
-    // A CTA takes wpc consecutive blocks per iteration.  Blocks are sorted by
-    // length inside their window, so the warp's pick among them rotates from
-    // one iteration to the next: otherwise warp 0 would always get the
-    // longest rows and warp wpc-1 the shortest.
+    const int64_t ngroups = ceil_div_dev(nb, wpc);
+    // A CTA takes wpc consecutive blocks (a group) per iteration.  Blocks are
+    // sorted by length inside their window, so the warp's pick among them
+    // rotates by 7 from one iteration to the next: otherwise warp 0 would
+    // always get the longest rows and warp wpc-1 the shortest.
     // The group a CTA takes also rotates (by one per iteration): with a
     // window longer than a group, a fixed stride of gridDim.x groups would
-    // hand every CTA the same position in every window.
-    int64_t it = 0;
-    for (int64_t g0 = 0; g0 * wpc < nb; g0 += gridDim.x, ++it) {
-        const int64_t g = g0 + (int64_t)((blockIdx.x + it) % gridDim.x);
-        if (g * wpc >= nb) continue;
-        const int64_t b = g * wpc + (int64_t)((wid + it * 7) % wpc);
-        if (b >= nb) continue;
+    // hand every CTA the same position in every window.  Both rotations are
+    // kept as running 32-bit counters (no division in the loop).
+    uint32_t rot = blockIdx.x;  // (blockIdx.x + iteration) mod gridDim.x
+    int pick = wid;             // (wid + 7 iteration) mod wpc
+    for (int64_t g0 = 0; g0 < ngroups; g0 += gridDim.x) {
+        const int64_t g = g0 + rot;
+        const int64_t b = g * wpc + pick;
+        rot = rot + 1 == gridDim.x ? 0u : rot + 1;
+        pick += 7;
+        while (pick >= wpc) pick -= wpc;
+        if (g >= ngroups || b >= nb) continue;
         const int64_t r = b * 32 + lane;
         const int32_t len = r < a.n_rows ? __ldg(a.rlen + r) : 0;
         const int32_t width = __shfl_sync(0xffffffffu, len, 0);  // lane 0 holds the longest row
-        int64_t off = __ldg(a.blk_ptr + b);
+        // entry offsets fit int32 (nnz < 2^31)
+        int32_t off = __ldg(a.blk_ptr + b);
         Acc<VM> acc[KT];
 #pragma unroll
         for (int q = 0; q < KT; ++q) acc[q].init();
@@ -356,26 +362,30 @@ __global__ void __launch_bounds__(1024) sell_kernel(JdsArgs a) {
 #pragma unroll
         for (int j = 0; j < U; ++j) {
             const bool ok = len > j;
-            c[j] = ok ? ld_stream(a.col + off + lane) : -1;
-            v[j] = ok ? ld_stream(val + off + lane) : T(0);
-            off += __popc(__ballot_sync(0xffffffffu, len > j));
+            c[j] = ok ? ld_stream(a.col + (off + lane)) : -1;
+            v[j] = ok ? ld_stream(val + (off + lane)) : T(0);
+            off += __popc(__ballot_sync(0xffffffffu, ok));
         }
         for (int32_t d0 = 0; d0 < width; d0 += U) {
 #pragma unroll
             for (int j = 0; j < U; ++j) {
                 if (c[j] < 0) continue;
-                const T *xr = x + xidx(a.x_perm, c[j]) * a.ldx + a.c0;
+                if (PLAIN) {
+                    acc[0].add(v[j], ld_vec(x + c[j]));
+                } else {
+                    const T *xr = x + xidx(a.x_perm, c[j]) * a.ldx + a.c0;
 #pragma unroll
-                for (int q = 0; q < KT; ++q)
-                    if (KT == 1 || a.c0 + q < a.k) acc[q].add(v[j], ld_vec(xr + q));
+                    for (int q = 0; q < KT; ++q)
+                        if (KT == 1 || a.c0 + q < a.k) acc[q].add(v[j], ld_vec(xr + q));
+                }
             }
             if (d0 + U >= width) break;
 #pragma unroll
             for (int j = 0; j < U; ++j) {
                 const bool ok = len > d0 + U + j;
-                c[j] = ok ? ld_stream(a.col + off + lane) : -1;
-                v[j] = ok ? ld_stream(val + off + lane) : T(0);
-                off += __popc(__ballot_sync(0xffffffffu, len > d0 + U + j));
+                c[j] = ok ? ld_stream(a.col + (off + lane)) : -1;
+                v[j] = ok ? ld_stream(val + (off + lane)) : T(0);
+                off += __popc(__ballot_sync(0xffffffffu, ok));
             }
         }
         if (r < a.n_rows) {
@@ -632,12 +642,18 @@ static void launch_sell_U(JdsArgs a, int KT, cudaStream_t s) {
     const int threads = 1024;
     const int64_t grid = limit_grid(
         std::max<int64_t>(1, std::min<int64_t>(ceil_div(nb * 32, threads), (int64_t)num_sms() * 2)), a.grid_limit);
+    // one vector, read directly (no x permutation, unit stride): the plain
+    // walk, without the SpMM index arithmetic
+    const bool plain = KT == 1 && !a.x_perm && a.ldx == 1 && a.c0 == 0;
     switch (KT) {
-        case 1: sell_kernel<VM, U, 1><<<(unsigned)grid, threads, 0, s>>>(a); break;
-        case 2: sell_kernel<VM, U, 2><<<(unsigned)grid, threads, 0, s>>>(a); break;
-        case 4: sell_kernel<VM, U, 4><<<(unsigned)grid, threads, 0, s>>>(a); break;
-        case 8: sell_kernel<VM, U, 8><<<(unsigned)grid, threads, 0, s>>>(a); break;
-        default: sell_kernel<VM, U, 16><<<(unsigned)grid, threads, 0, s>>>(a); break;
+        case 1:
+            if (plain) sell_kernel<VM, U, 1, true><<<(unsigned)grid, threads, 0, s>>>(a);
+            else sell_kernel<VM, U, 1, false><<<(unsigned)grid, threads, 0, s>>>(a);
+            break;
+        case 2: sell_kernel<VM, U, 2, false><<<(unsigned)grid, threads, 0, s>>>(a); break;
+        case 4: sell_kernel<VM, U, 4, false><<<(unsigned)grid, threads, 0, s>>>(a); break;
+        case 8: sell_kernel<VM, U, 8, false><<<(unsigned)grid, threads, 0, s>>>(a); break;
+        default: sell_kernel<VM, U, 16, false><<<(unsigned)grid, threads, 0, s>>>(a); break;
     }
 }
 
