@@ -73,7 +73,8 @@ __device__ __forceinline__ void store_row(const JdsArgs &a, int64_t r, int c, Ac
 // of them (rows base + 32 i + lane): the loads of all R rows and U diagonals
 // are issued together, while each warp-wide load still covers 32
 // consecutive entries of one diagonal.
-template <int VM, int U, int R>
+// PLAIN: one vector read directly (no x permutation, unit stride).
+template <int VM, int U, int R, bool PLAIN>
 __global__ void __launch_bounds__(256) jds_row_kernel(JdsArgs a) {
     typedef typename ValT<VM>::T T;
     const T *__restrict__ val = static_cast<const T *>(a.val);
@@ -119,7 +120,8 @@ __global__ void __launch_bounds__(256) jds_row_kernel(JdsArgs a) {
             for (int i = 0; i < R; ++i)
 #pragma unroll
                 for (int j = 0; j < U; ++j)
-                    if (c[i][j] >= 0) acc[i].add(v[i][j], ld_vec(x + xidx(a.x_perm, c[i][j]) * a.ldx));
+                    if (c[i][j] >= 0)
+                        acc[i].add(v[i][j], ld_vec(PLAIN ? x + c[i][j] : x + xidx(a.x_perm, c[i][j]) * a.ldx));
             if (!more) break;
 #pragma unroll
             for (int i = 0; i < R; ++i)
@@ -422,9 +424,15 @@ __global__ void __launch_bounds__(1024, 2) sell_staged_kernel(JdsArgs a, const i
     const int wpc = blockDim.x >> 5;
     const int wid = threadIdx.x >> 5;
     const int64_t ngroups = ceil_div_dev(nb, wpc);
-    int64_t it = 0;
-    for (int64_t g0 = 0; g0 < ngroups; g0 += gridDim.x, ++it) {
-        const int64_t g = g0 + (int64_t)((blockIdx.x + it) % gridDim.x);
+    // the SELL walk's rotations, as running 32-bit counters
+    uint32_t rot = blockIdx.x;
+    int pick = wid;
+    for (int64_t g0 = 0; g0 < ngroups; g0 += gridDim.x) {
+        const int64_t g = g0 + rot;
+        const int64_t b = g * wpc + pick;
+        rot = rot + 1 == gridDim.x ? 0u : rot + 1;
+        pick += 7;
+        while (pick >= wpc) pick -= wpc;
         __syncthreads();  // the previous group's staged x is no longer read
         if (g < ngroups) {
             for (int q = threadIdx.x; q < P * kStagePage; q += blockDim.x) {
@@ -434,9 +442,7 @@ __global__ void __launch_bounds__(1024, 2) sell_staged_kernel(JdsArgs a, const i
             }
         }
         __syncthreads();
-        if (g >= ngroups) continue;
-        const int64_t b = g * wpc + (int64_t)((wid + it * 7) % wpc);
-        if (b >= nb) continue;
+        if (g >= ngroups || b >= nb) continue;
         const int64_t r = b * 32 + lane;
         const int32_t len = r < a.n_rows ? __ldg(a.rlen + r) : 0;
         const int32_t width = __shfl_sync(0xffffffffu, len, 0);
@@ -490,12 +496,16 @@ __global__ void __launch_bounds__(1024, (KT == 1 ? 2 : 1)) psell_kernel(JdsArgs 
     const int wpc = blockDim.x >> 5;
     const int wid = threadIdx.x >> 5;
     // same rotation of blocks over warps and groups over CTAs as SELL
-    int64_t it = 0;
-    for (int64_t g0 = 0; g0 * wpc < nb; g0 += gridDim.x, ++it) {
-        const int64_t g = g0 + (int64_t)((blockIdx.x + it) % gridDim.x);
-        if (g * wpc >= nb) continue;
-        const int64_t b = g * wpc + (int64_t)((wid + it * 7) % wpc);
-        if (b >= nb) continue;
+    const int64_t ngroups = ceil_div_dev(nb, wpc);
+    uint32_t rot = blockIdx.x;
+    int pick = wid;
+    for (int64_t g0 = 0; g0 < ngroups; g0 += gridDim.x) {
+        const int64_t g = g0 + rot;
+        const int64_t b = g * wpc + pick;
+        rot = rot + 1 == gridDim.x ? 0u : rot + 1;
+        pick += 7;
+        while (pick >= wpc) pick -= wpc;
+        if (g >= ngroups || b >= nb) continue;
         const int R = (int)min((int64_t)64, a.n_rows - 64 * b), L = (R + 1) / 2;
         const bool lane_ok = lane < L, has_b = lane_ok && L + lane < R;
         const int32_t la = lane_ok ? __ldg(a.rlen + 64 * b + lane) : 0;
@@ -609,9 +619,15 @@ static void launch_row(const JdsArgs &a, int R, cudaStream_t s) {
     const unsigned g4 = (unsigned)limit_grid(row_grid(ceil_div(a.n_rows, 4)), a.grid_limit);
     const unsigned g2 = (unsigned)limit_grid(row_grid(ceil_div(a.n_rows, 2)), a.grid_limit);
     const unsigned g1 = (unsigned)limit_grid(row_grid(a.n_rows), a.grid_limit);
-    if (R >= 4) jds_row_kernel<VM, U, 4><<<g4, 256, 0, s>>>(a);
-    else if (R >= 2) jds_row_kernel<VM, U, 2><<<g2, 256, 0, s>>>(a);
-    else jds_row_kernel<VM, U, 1><<<g1, 256, 0, s>>>(a);
+    if (!a.x_perm && a.ldx == 1) {
+        if (R >= 4) jds_row_kernel<VM, U, 4, true><<<g4, 256, 0, s>>>(a);
+        else if (R >= 2) jds_row_kernel<VM, U, 2, true><<<g2, 256, 0, s>>>(a);
+        else jds_row_kernel<VM, U, 1, true><<<g1, 256, 0, s>>>(a);
+    } else {
+        if (R >= 4) jds_row_kernel<VM, U, 4, false><<<g4, 256, 0, s>>>(a);
+        else if (R >= 2) jds_row_kernel<VM, U, 2, false><<<g2, 256, 0, s>>>(a);
+        else jds_row_kernel<VM, U, 1, false><<<g1, 256, 0, s>>>(a);
+    }
 }
 
 template <int VM, bool CONTIG>

@@ -92,12 +92,17 @@ __global__ void __launch_bounds__(1024) sym_sell_kernel(int64_t n, const int32_t
     const int64_t nb = ceil_div_dev(n, 32);
     const int wpc = blockDim.x >> 5;
     const int wid = threadIdx.x >> 5;
-    int64_t it = 0;
-    for (int64_t g0 = 0; g0 * wpc < nb; g0 += gridDim.x, ++it) {
-        const int64_t g = g0 + (int64_t)((blockIdx.x + it) % gridDim.x);
-        if (g * wpc >= nb) continue;
-        const int64_t b = g * wpc + (int64_t)((wid + it * 7) % wpc);
-        if (b >= nb) continue;
+    // the SELL walk's rotations, as running 32-bit counters
+    const int64_t ngroups = ceil_div_dev(nb, wpc);
+    uint32_t rot = blockIdx.x;
+    int pick = wid;
+    for (int64_t g0 = 0; g0 < ngroups; g0 += gridDim.x) {
+        const int64_t g = g0 + rot;
+        const int64_t b = g * wpc + pick;
+        rot = rot + 1 == gridDim.x ? 0u : rot + 1;
+        pick += 7;
+        while (pick >= wpc) pick -= wpc;
+        if (g >= ngroups || b >= nb) continue;
         const int64_t r = b * 32 + lane;
         const int32_t len = r < n ? __ldg(rlen + r) : 0;
         const int32_t width = __shfl_sync(0xffffffffu, len, 0);
