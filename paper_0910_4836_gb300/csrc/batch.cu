@@ -135,8 +135,8 @@ __device__ void batch_jds_rows(const BatchMat &m, int64_t rb, int64_t re, int c0
 }
 
 // SELL rows [rb, re) (whole 32-row blocks): one warp per block, lane = row
-// (same arithmetic as sell_kernel).
-template <int VM, int KT>
+// (same arithmetic as sell_kernel).  PLAIN: one vector read directly.
+template <int VM, int KT, bool PLAIN>
 __device__ void batch_sell_rows(const BatchMat &m, int64_t rb, int64_t re, int c0) {
     typedef typename ValT<VM>::T T;
     constexpr int U = 4;  // slots whose loads are in flight together
@@ -148,7 +148,7 @@ __device__ void batch_sell_rows(const BatchMat &m, int64_t rb, int64_t re, int c
         const int64_t r = b * 32 + lane;
         const int32_t len = r < m.n_rows ? __ldg(m.rlen + r) : 0;
         const int32_t width = __shfl_sync(0xffffffffu, len, 0);
-        int64_t off = __ldg(m.blk_ptr + b);
+        int32_t off = __ldg(m.blk_ptr + b);  // entry offsets fit int32
         Acc<VM> acc[KT];
 #pragma unroll
         for (int q = 0; q < KT; ++q) acc[q].init();
@@ -158,25 +158,29 @@ __device__ void batch_sell_rows(const BatchMat &m, int64_t rb, int64_t re, int c
 #pragma unroll
         for (int j = 0; j < U; ++j) {
             const bool ok = len > j;
-            c[j] = ok ? ld_stream(m.col + off + lane) : -1;
-            v[j] = ok ? ld_stream(val + off + lane) : T(0);
+            c[j] = ok ? ld_stream(m.col + (off + lane)) : -1;
+            v[j] = ok ? ld_stream(val + (off + lane)) : T(0);
             off += __popc(__ballot_sync(0xffffffffu, ok));
         }
         for (int32_t d0 = 0; d0 < width; d0 += U) {
 #pragma unroll
             for (int j = 0; j < U; ++j) {
                 if (c[j] < 0) continue;
-                const T *xr = x + (int64_t)c[j] * m.ldx + c0;
+                if (PLAIN) {
+                    acc[0].add(v[j], ld_vec(x + c[j]));
+                } else {
+                    const T *xr = x + (int64_t)c[j] * m.ldx + c0;
 #pragma unroll
-                for (int q = 0; q < KT; ++q)
-                    if (c0 + q < m.k) acc[q].add(v[j], ld_vec(xr + q));
+                    for (int q = 0; q < KT; ++q)
+                        if (c0 + q < m.k) acc[q].add(v[j], ld_vec(xr + q));
+                }
             }
             if (d0 + U >= width) break;
 #pragma unroll
             for (int j = 0; j < U; ++j) {
                 const bool ok = len > d0 + U + j;
-                c[j] = ok ? ld_stream(m.col + off + lane) : -1;
-                v[j] = ok ? ld_stream(val + off + lane) : T(0);
+                c[j] = ok ? ld_stream(m.col + (off + lane)) : -1;
+                v[j] = ok ? ld_stream(val + (off + lane)) : T(0);
                 off += __popc(__ballot_sync(0xffffffffu, ok));
             }
         }
@@ -207,11 +211,14 @@ __device__ void batch_item(const BatchMat &m, int64_t rb, int64_t re) {
             KT = clamp_tile<KTMAX>(KT);
         }
         for (int c0 = 0; c0 < m.k; c0 += KT) {
-            if (KT == 1) batch_sell_rows<VM, 1>(m, rb, re, c0);
-            if constexpr (KTMAX >= 2) if (KT == 2) batch_sell_rows<VM, 2>(m, rb, re, c0);
-            if constexpr (KTMAX >= 4) if (KT == 4) batch_sell_rows<VM, 4>(m, rb, re, c0);
-            if constexpr (KTMAX >= 8) if (KT == 8) batch_sell_rows<VM, 8>(m, rb, re, c0);
-            if constexpr (KTMAX >= 16) if (KT >= 16) batch_sell_rows<VM, 16>(m, rb, re, c0);
+            if (KT == 1) {  // k = 1, so c0 = 0
+                if (m.ldx == 1) batch_sell_rows<VM, 1, true>(m, rb, re, c0);
+                else batch_sell_rows<VM, 1, false>(m, rb, re, c0);
+            }
+            if constexpr (KTMAX >= 2) if (KT == 2) batch_sell_rows<VM, 2, false>(m, rb, re, c0);
+            if constexpr (KTMAX >= 4) if (KT == 4) batch_sell_rows<VM, 4, false>(m, rb, re, c0);
+            if constexpr (KTMAX >= 8) if (KT == 8) batch_sell_rows<VM, 8, false>(m, rb, re, c0);
+            if constexpr (KTMAX >= 16) if (KT >= 16) batch_sell_rows<VM, 16, false>(m, rb, re, c0);
         }
         return;
     }
@@ -258,7 +265,7 @@ template <int KTMAX>
 __global__ void __launch_bounds__(kBatchThreads, KTMAX == 1 ? 5 : 4)
 batch_kernel(const BatchMat *__restrict__ mats, const BatchWork *__restrict__ work, int64_t n_work,
              int32_t *counter, const volatile int32_t *ready, int32_t *status) {
-    __shared__ int64_t item;
+    __shared__ int64_t next[2];
     __shared__ int32_t go;
     if (threadIdx.x == 0) {
         go = 1;
@@ -278,17 +285,24 @@ batch_kernel(const BatchMat *__restrict__ mats, const BatchWork *__restrict__ wo
     }
     __syncthreads();
     if (!go) return;
-    for (;;) {
-        if (threadIdx.x == 0) item = atomicAdd(counter, 1);
-        __syncthreads();
-        const int64_t w = item;
-        __syncthreads();
+    // Thread 0 claims the next item once its own share of the current one
+    // is done, into the other of two shared slots, so one barrier per item
+    // suffices.  Claiming only then (not ahead) keeps a CTA busy with an
+    // expensive item from holding a cheap one at the tail of the queue.
+    // Which CTA runs an item never changes its result.
+    if (threadIdx.x == 0) next[0] = atomicAdd(counter, 1);
+    __syncthreads();
+    for (int i = 0;; i ^= 1) {
+        const int64_t w = next[i];
         if (w >= n_work) break;
         const BatchWork wk = work[w];
         const BatchMat m = mats[wk.mat];
         if (m.vm == VM_F64) batch_item<VM_F64, KTMAX>(m, wk.rb, wk.re);
         else if (m.vm == VM_F32C) batch_item<VM_F32C, KTMAX>(m, wk.rb, wk.re);
         else batch_item<VM_F32, KTMAX>(m, wk.rb, wk.re);
+        if (threadIdx.x == 0) next[i ^ 1] = atomicAdd(counter, 1);
+        // every thread has read next[i]; next[i ^ 1] is written and visible
+        __syncthreads();
     }
 }
 
