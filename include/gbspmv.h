@@ -398,6 +398,18 @@ gbsp_status gbsp_dval_multi(gbsp_handle crs, int32_t m, const void *d_G, int64_t
                             const void *d_X, int64_t ldx, void *d_dval, int32_t accumulate,
                             void *stream);
 
+/* The same with any element layout: G[row, t] at d_G + row*g_row + t*g_t and
+ * X[col, t] at d_X + col*x_row + t*x_t (elements; all strides >= 1).  With
+ * g_row = x_row = 1 and g_t = x_t = the vector length, G and X are m
+ * separate contiguous vectors (column-major), the layout in which each of
+ * the iterated products reads and writes its vector with unit stride.
+ * Same order of operations, hence the same result, as gbsp_dval_multi on
+ * the same values.  Errors: GBSP_ERR_ARG for m < 1, a stride < 1, NULL
+ * arrays, or dval overlapping G or X. */
+gbsp_status gbsp_dval_multi_strided(gbsp_handle crs, int32_t m, const void *d_G, int64_t g_row,
+                                    int64_t g_t, const void *d_X, int64_t x_row, int64_t x_t,
+                                    void *d_dval, int32_t accumulate, void *stream);
+
 /* -------------------------------------------------------------- batched -- */
 
 /* One item of a batch: Y_b = A_b X_b with k_b right-hand sides (row-major,

@@ -102,6 +102,7 @@ SIGNATURES = {
     "gbsp_attach_transpose": (c_i32, [c_vp, c_vp]),
     "gbsp_dval": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_vp]),
     "gbsp_dval_multi": (c_i32, [c_vp, c_i32, c_vp, c_i64, c_vp, c_i64, c_vp, c_i32, c_vp]),
+    "gbsp_dval_multi_strided": (c_i32, [c_vp, c_i32, c_vp, c_i64, c_i64, c_vp, c_i64, c_i64, c_vp, c_i32, c_vp]),
     "gbsp_batch_plan": (c_i32, [c_i32, P(BatchItem), c_i32, P(c_i64)]),
     "gbsp_batch_create": (c_i32, [c_i32, P(BatchItem), c_i32, c_vp, c_i64, c_vp, c_vp, P(c_vp)]),
     "gbsp_batch_run": (c_i32, [c_vp, c_vp, c_vp]),

@@ -10,7 +10,7 @@ products as in the eigensolvers the paper is about (Sect. 1): the forward
 pass stores x_t only every `checkpoint` steps; the backward pass recomputes
 each segment from its checkpoint, runs g_{t-1} = A^T g_t down the segment
 and adds the segment's value gradient sum_t g_t[row] x_{t-1}[col] with ONE
-fused pass over the entries (gbsp_dval_multi).  The fused kernel adds the
+fused pass over the entries (gbsp_dval_multi_strided).  The fused kernel adds the
 terms for t = m, m-1, ..., 1 in that order into one running sum, so the
 gradients are bit-identical for every checkpoint interval.
 """
@@ -181,13 +181,16 @@ class PowerFunction(torch.autograd.Function):
         for seg in range((m - 1) // c, -1, -1):
             t0 = seg * c
             w = min(t0 + c, m) - t0
-            # X[:, i] = x_{t1-1-i}: recomputed from the checkpoint x_{t0}
-            X = torch.empty((n, w), dtype=dt, device=dev)
+            # X[:, i] = x_{t1-1-i}: recomputed from the checkpoint x_{t0}.
+            # Columns are contiguous vectors (column-major n x w), so every
+            # product reads and writes with unit stride; the fused dval takes
+            # the layout as strides.
+            X = torch.empty((w, n), dtype=dt, device=dev).t()
             X[:, w - 1] = ckpts[seg]
             for j in range(1, w):
                 p.apply(val, X[:, w - j:w - j + 1], out=X[:, w - 1 - j:w - j])
             # G[:, i] = g_{t1-i}, i.e. g_{t-1} = A^T g_t down the segment
-            G = torch.empty((n, w), dtype=dt, device=dev)
+            G = torch.empty((w, n), dtype=dt, device=dev).t()
             G[:, 0] = g
             for i in range(1, w):
                 p.apply_t(val, G[:, i - 1:i], out=G[:, i:i + 1])

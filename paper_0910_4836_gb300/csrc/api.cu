@@ -192,8 +192,7 @@ gbsp_status gbsp_jds_values(gbsp_handle h, const void *d_src_val, void *stream) 
         set_error("gbsp_jds_values: handle was built without a value map");
         return GBSP_ERR_UNSUPPORTED;
     }
-    return gather_values_launch(h->nnz, h->vmap, d_src_val, const_cast<void *>(h->val), h->dtype,
-                                static_cast<cudaStream_t>(stream));
+    return jds_values_launch(*h, d_src_val, static_cast<cudaStream_t>(stream));
 }
 
 gbsp_status gbsp_crs_tile_bytes(gbsp_handle crs, int32_t tile, int64_t *bytes) {
@@ -454,14 +453,29 @@ gbsp_status gbsp_dval(gbsp_handle crs, const void *d_g, const void *d_x, void *d
 
 gbsp_status gbsp_dval_multi(gbsp_handle crs, int32_t m, const void *d_G, int64_t ldg, const void *d_X,
                             int64_t ldx, void *d_dval, int32_t accumulate, void *stream) {
+    if (m < 1 || ldg < m || ldx < m) return arg_error("gbsp_dval: need m >= 1 and ld >= m");
+    return gbsp_dval_multi_strided(crs, m, d_G, ldg, 1, d_X, ldx, 1, d_dval, accumulate, stream);
+}
+
+// bytes from the first to one past the last element of a rows x m array
+static size_t strided_span_bytes(int64_t rows, int64_t row_stride, int32_t m, int64_t t_stride, int dtype) {
+    if (rows <= 0 || m <= 0) return 0;
+    return (size_t)((rows - 1) * row_stride + (int64_t)(m - 1) * t_stride + 1) * elem_size(dtype);
+}
+
+gbsp_status gbsp_dval_multi_strided(gbsp_handle crs, int32_t m, const void *d_G, int64_t g_row, int64_t g_t,
+                                    const void *d_X, int64_t x_row, int64_t x_t, void *d_dval,
+                                    int32_t accumulate, void *stream) {
     if (!crs) return arg_error("gbsp_dval: NULL handle");
     if (crs->kind != KIND_CRS) return arg_error("gbsp_dval: needs the CRS handle");
-    if (m < 1 || ldg < m || ldx < m) return arg_error("gbsp_dval: need m >= 1 and ld >= m");
+    if (m < 1 || g_row < 1 || g_t < 1 || x_row < 1 || x_t < 1)
+        return arg_error("gbsp_dval: need m >= 1 and positive strides");
     if (crs->nnz > 0 && (!d_G || !d_X || !d_dval)) return arg_error("gbsp_dval: NULL vector");
-    if (overlap(d_dval, crs->nnz * elem_size(crs->dtype), d_G, span_bytes(crs->n_rows, ldg, m, crs->dtype)) ||
-        overlap(d_dval, crs->nnz * elem_size(crs->dtype), d_X, span_bytes(crs->n_cols, ldx, m, crs->dtype)))
+    const size_t out_bytes = (size_t)crs->nnz * elem_size(crs->dtype);
+    if (overlap(d_dval, out_bytes, d_G, strided_span_bytes(crs->n_rows, g_row, m, g_t, crs->dtype)) ||
+        overlap(d_dval, out_bytes, d_X, strided_span_bytes(crs->n_cols, x_row, m, x_t, crs->dtype)))
         return arg_error("gbsp_dval: output overlaps an input");
-    return crs_dval_launch(*crs, m, d_G, ldg, d_X, ldx, d_dval, accumulate ? 1 : 0,
+    return crs_dval_launch(*crs, m, d_G, g_row, g_t, d_X, x_row, x_t, d_dval, accumulate ? 1 : 0,
                            static_cast<cudaStream_t>(stream));
 }
 

@@ -948,6 +948,87 @@ __global__ void gather_values_kernel(int64_t nnz, const int32_t *__restrict__ tm
     if (t < nnz) out[t] = val[tmap[t]];
 }
 
+// Value re-gathers in row order.  A thread (or, for SELL, a lane) owns one
+// stored row and walks its slots, so the source entries it reads, one CRS
+// row, are read together and each source sector is fetched once; in entry
+// order the lanes of a warp would take one 8-byte value from each of 32
+// sectors and come back for the rest of those sectors much later.
+template <typename T>
+__global__ void csr_rows_gather_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
+                                       const int32_t *__restrict__ map, const T *__restrict__ src,
+                                       T *__restrict__ dst) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rows) return;
+    const int32_t e1 = __ldg(row_ptr + r + 1);
+    for (int32_t e = __ldg(row_ptr + r); e < e1; ++e) dst[e] = src[__ldg(map + e)];
+}
+
+// JDS storage (JDS, NBJDS, NUJDS): thread r walks the diagonals of permuted row r.
+template <typename T>
+__global__ void jds_rows_gather_kernel(int64_t n, int64_t n_diag, const int32_t *__restrict__ jd_ptr,
+                                       const int32_t *__restrict__ map, const T *__restrict__ src,
+                                       T *__restrict__ dst) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    for (int64_t d = 0; d < n_diag; ++d) {
+        const int32_t p0 = __ldg(jd_ptr + d), p1 = __ldg(jd_ptr + d + 1);
+        if (p1 - p0 <= r) break;
+        const int64_t pos = p0 + r;
+        dst[pos] = src[__ldg(map + pos)];
+    }
+}
+
+// SELL: one warp per 32-row block, lane = row, slots as in the SELL walk.
+template <typename T>
+__global__ void sell_rows_gather_kernel(int64_t n, int64_t nb, const int32_t *__restrict__ rlen,
+                                        const int32_t *__restrict__ blk_ptr, const int32_t *__restrict__ map,
+                                        const T *__restrict__ src, T *__restrict__ dst) {
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= nb) return;  // warp-uniform
+    const int lane = threadIdx.x & 31;
+    const int64_t r = b * 32 + lane;
+    const int32_t len = r < n ? __ldg(rlen + r) : 0;
+    int64_t off = __ldg(blk_ptr + b);
+    for (int32_t d = 0;; ++d) {
+        const unsigned mask = __ballot_sync(0xffffffffu, len > d);
+        if (!mask) break;
+        if (len > d) dst[off + lane] = src[__ldg(map + off + lane)];
+        off += __popc(mask);
+    }
+}
+
+gbsp_status jds_values_launch(const Mat &J, const void *src, cudaStream_t s) {
+    if (J.nnz == 0) return GBSP_OK;
+    const bool jds_storage = J.jd_ptr && (J.format == GBSP_JDS || J.format == GBSP_NBJDS ||
+                                          J.format == GBSP_NUJDS || J.format == GBSP_JDS_LITERAL);
+    const bool f64 = J.dtype == GBSP_F64;
+    void *dst = const_cast<void *>(J.val);
+    if (jds_storage) {
+        const unsigned g = (unsigned)ceil_div(J.n_rows, 256);
+        if (f64)
+            jds_rows_gather_kernel<double><<<g, 256, 0, s>>>(J.n_rows, J.n_diag, J.jd_ptr, J.vmap,
+                                                             static_cast<const double *>(src), static_cast<double *>(dst));
+        else
+            jds_rows_gather_kernel<float><<<g, 256, 0, s>>>(J.n_rows, J.n_diag, J.jd_ptr, J.vmap,
+                                                            static_cast<const float *>(src), static_cast<float *>(dst));
+        GBSP_LAUNCH_CHECK("jds_rows_gather_kernel");
+        return GBSP_OK;
+    }
+    if (J.format == GBSP_SELL && J.rlen && J.blk_ptr) {
+        const int64_t nb = ceil_div(J.n_rows, 32);
+        const unsigned g = (unsigned)ceil_div(nb * 32, 256);
+        if (f64)
+            sell_rows_gather_kernel<double><<<g, 256, 0, s>>>(J.n_rows, nb, J.rlen, J.blk_ptr, J.vmap,
+                                                              static_cast<const double *>(src), static_cast<double *>(dst));
+        else
+            sell_rows_gather_kernel<float><<<g, 256, 0, s>>>(J.n_rows, nb, J.rlen, J.blk_ptr, J.vmap,
+                                                             static_cast<const float *>(src), static_cast<float *>(dst));
+        GBSP_LAUNCH_CHECK("sell_rows_gather_kernel");
+        return GBSP_OK;
+    }
+    return gather_values_launch(J.nnz, J.vmap, src, dst, J.dtype, s);
+}
+
 gbsp_status transpose_workspace_impl(const Mat &A, int64_t *bytes) {
     *bytes = align256(4 * A.nnz) * 2 + sort_ws_bytes(A.nnz) + align256(scan_ws_bytes(A.n_cols + 1)) + 256;
     return GBSP_OK;
@@ -1018,7 +1099,18 @@ gbsp_status gather_values_launch(int64_t n, const int32_t *map, const void *src,
 }
 
 gbsp_status transpose_values_impl(const Mat &T, cudaStream_t s) {
-    return gather_values_launch(T.nnz, T.tmap, T.transpose_src->val, const_cast<void *>(T.val), T.dtype, s);
+    if (T.nnz == 0) return GBSP_OK;
+    const unsigned g = (unsigned)ceil_div(T.n_rows, 256);
+    if (T.dtype == GBSP_F64)
+        csr_rows_gather_kernel<double><<<g, 256, 0, s>>>(T.n_rows, T.row_ptr, T.tmap,
+                                                         static_cast<const double *>(T.transpose_src->val),
+                                                         static_cast<double *>(const_cast<void *>(T.val)));
+    else
+        csr_rows_gather_kernel<float><<<g, 256, 0, s>>>(T.n_rows, T.row_ptr, T.tmap,
+                                                        static_cast<const float *>(T.transpose_src->val),
+                                                        static_cast<float *>(const_cast<void *>(T.val)));
+    GBSP_LAUNCH_CHECK("csr_rows_gather_kernel");
+    return GBSP_OK;
 }
 
 }  // namespace gbsp

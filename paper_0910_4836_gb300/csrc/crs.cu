@@ -133,8 +133,9 @@ crs_spmm_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
 template <typename T, int L>
 __global__ void __launch_bounds__(kThreads)
 crs_dval_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
-                const int32_t *__restrict__ col, int m, const T *__restrict__ G, int64_t ldg,
-                const T *__restrict__ X, int64_t ldx, T *__restrict__ dval, int accumulate) {
+                const int32_t *__restrict__ col, int m, const T *__restrict__ G, int64_t g_row,
+                int64_t g_t, const T *__restrict__ X, int64_t x_row, int64_t x_t, T *__restrict__ dval,
+                int accumulate) {
     constexpr int NG = 32 / L;
     const int lane = threadIdx.x & 31;
     const int grp = lane / L, gl = lane % L;
@@ -146,7 +147,7 @@ crs_dval_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
         for (int kk = k0 + gl; kk < k1; kk += L) {
             const int64_t cj = ld_stream(col + kk);
             T d = accumulate ? dval[kk] : T(0);
-            for (int t = 0; t < m; ++t) d = fma(__ldg(G + r * ldg + t), __ldg(X + cj * ldx + t), d);
+            for (int t = 0; t < m; ++t) d = fma(__ldg(G + r * g_row + t * g_t), __ldg(X + cj * x_row + t * x_t), d);
             dval[kk] = d;
         }
     }
@@ -298,29 +299,31 @@ gbsp_status crs_validate_launch(const Mat &A, int32_t *d_status, cudaStream_t s)
 }
 
 template <typename T>
-static void launch_dval(const Mat &A, int32_t m, const void *G, int64_t ldg, const void *X,
-                        int64_t ldx, void *dval, int32_t accumulate, cudaStream_t s) {
+static void launch_dval(const Mat &A, int32_t m, const void *G, int64_t g_row, int64_t g_t,
+                        const void *X, int64_t x_row, int64_t x_t, void *dval, int32_t accumulate,
+                        cudaStream_t s) {
     const int L = A.kopt.lanes >= 8 ? 8 : (A.kopt.lanes >= 4 ? 4 : 1);
     const int grid = grid_for(ceil_div(A.n_rows, 32 / L));
     auto *g = static_cast<const T *>(G);
     auto *x = static_cast<const T *>(X);
     auto *d = static_cast<T *>(dval);
     if (L == 8)
-        crs_dval_kernel<T, 8><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, m, g, ldg, x,
-                                                        ldx, d, accumulate);
+        crs_dval_kernel<T, 8><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, m, g, g_row, g_t, x,
+                                                        x_row, x_t, d, accumulate);
     else if (L == 4)
-        crs_dval_kernel<T, 4><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, m, g, ldg, x,
-                                                        ldx, d, accumulate);
+        crs_dval_kernel<T, 4><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, m, g, g_row, g_t, x,
+                                                        x_row, x_t, d, accumulate);
     else
-        crs_dval_kernel<T, 1><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, m, g, ldg, x,
-                                                        ldx, d, accumulate);
+        crs_dval_kernel<T, 1><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, m, g, g_row, g_t, x,
+                                                        x_row, x_t, d, accumulate);
 }
 
-gbsp_status crs_dval_launch(const Mat &A, int32_t m, const void *G, int64_t ldg, const void *X,
-                            int64_t ldx, void *dval, int32_t accumulate, cudaStream_t s) {
+gbsp_status crs_dval_launch(const Mat &A, int32_t m, const void *G, int64_t g_row, int64_t g_t,
+                            const void *X, int64_t x_row, int64_t x_t, void *dval, int32_t accumulate,
+                            cudaStream_t s) {
     if (A.n_rows == 0 || A.nnz == 0) return GBSP_OK;
-    if (A.dtype == GBSP_F64) launch_dval<double>(A, m, G, ldg, X, ldx, dval, accumulate, s);
-    else launch_dval<float>(A, m, G, ldg, X, ldx, dval, accumulate, s);
+    if (A.dtype == GBSP_F64) launch_dval<double>(A, m, G, g_row, g_t, X, x_row, x_t, dval, accumulate, s);
+    else launch_dval<float>(A, m, G, g_row, g_t, X, x_row, x_t, dval, accumulate, s);
     GBSP_LAUNCH_CHECK("crs_dval_kernel");
     return GBSP_OK;
 }

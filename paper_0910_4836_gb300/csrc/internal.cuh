@@ -148,8 +148,9 @@ gbsp_status crs_prepare_tiles(Mat &A, int32_t tile, int32_t *table, cudaStream_t
 int64_t crs_tile_table_bytes(const Mat &A, int32_t tile);
 gbsp_status crs_tiled_launch(const Mat &A, const VecArgs &v, cudaStream_t s);
 gbsp_status crs_validate_launch(const Mat &A, int32_t *d_status, cudaStream_t s);
-gbsp_status crs_dval_launch(const Mat &A, int32_t m, const void *G, int64_t ldg, const void *X,
-                            int64_t ldx, void *dval, int32_t accumulate, cudaStream_t s);
+gbsp_status crs_dval_launch(const Mat &A, int32_t m, const void *G, int64_t g_row, int64_t g_t,
+                            const void *X, int64_t x_row, int64_t x_t, void *dval, int32_t accumulate,
+                            cudaStream_t s);
 void crs_default_opts(Mat &A);
 
 // jds.cu ----------------------------------------------------------------
@@ -168,6 +169,7 @@ gbsp_status transpose_workspace_impl(const Mat &A, int64_t *bytes);
 gbsp_status transpose_build_impl(const Mat &A, const gbsp_transpose_buffers &b, int64_t ws_bytes,
                                  cudaStream_t s, Mat *T);
 gbsp_status transpose_values_impl(const Mat &T, cudaStream_t s);
+gbsp_status jds_values_launch(const Mat &J, const void *src, cudaStream_t s);
 gbsp_status gather_values_launch(int64_t n, const int32_t *map, const void *src, void *dst, int dtype,
                                  cudaStream_t s);
 

@@ -270,17 +270,26 @@ class CRSMatrix(_Product):
 
     def dval_multi(self, G: torch.Tensor, X: torch.Tensor, out: torch.Tensor | None = None,
                    accumulate: bool = False, stream=None) -> torch.Tensor:
-        """dval_k = sum_t G[row_k, t] X[col_k, t] for row-major G, X."""
-        if G.stride(-1) != 1 or X.stride(-1) != 1:
-            raise ValueError("G and X must be row-major")
+        """dval_k = sum_t G[row_k, t] X[col_k, t], G and X 2-D in any
+        layout (row-major, or columns that are contiguous vectors)."""
+        for t, name in ((G, "G"), (X, "X")):  # no copy: the layout is passed as strides
+            if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != self.dtype:
+                raise ValueError(f"{name} must be a CUDA tensor of dtype {self.dtype}")
+        if G.dim() != 2 or X.dim() != 2:
+            raise ValueError("G and X must be 2-D")
         m = G.shape[1]
         if X.shape[1] != m:
             raise ValueError("G and X need the same number of columns")
+        if G.shape[0] != self.n_rows or X.shape[0] != self.n_cols:
+            raise ValueError("G needs n_rows rows and X n_cols rows")
         if out is None:
             out = (torch.zeros if accumulate else torch.empty)(self.nnz, dtype=self.dtype, device=G.device)
-        L.check(L.load().gbsp_dval_multi(self._h, m, _vp(G), G.stride(0), _vp(X), X.stride(0),
-                                         _vp(out), int(accumulate), _stream(stream)),
-                "gbsp_dval_multi")
+        if min(G.stride()) < 1 or min(X.stride()) < 1:
+            G, X = G.contiguous(), X.contiguous()  # broadcast (stride 0) views
+        (gr, gt), (xr, xt) = G.stride(), X.stride()
+        L.check(L.load().gbsp_dval_multi_strided(self._h, m, _vp(G), gr, gt, _vp(X), xr, xt,
+                                                 _vp(out), int(accumulate), _stream(stream)),
+                "gbsp_dval_multi_strided")
         return out
 
 

@@ -98,6 +98,13 @@ def test_dval_and_multi():
     M.dval_multi(dev(G[:, :2].copy()), dev(X[:, :2].copy()), out=out, accumulate=True)
     M.dval_multi(dev(G[:, 2:].copy()), dev(X[:, 2:].copy()), out=out, accumulate=True)
     assert np.array_equal(host(out).view(np.int64), dm.view(np.int64))
+    # the same pairs laid out column-major (m contiguous vectors) through the
+    # strided entry point: identical bits
+    Gc = torch.as_tensor(np.ascontiguousarray(G.T), device="cuda").t()
+    Xc = torch.as_tensor(np.ascontiguousarray(X.T), device="cuda").t()
+    assert Gc.stride() == (1, A.n_rows) and Xc.stride() == (1, A.n_cols)
+    dc = host(M.dval_multi(Gc, Xc))
+    assert np.array_equal(dc.view(np.int64), dm.view(np.int64))
 
 
 def _pattern(A, **kw):
