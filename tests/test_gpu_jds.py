@@ -410,3 +410,28 @@ def test_psell_fp32_compensated_and_spmm():
     for c in range(4):
         ref, s = O.crs_spmv_exact(A32.astype(np.float64), X[:, c].astype(np.float64))
         assert np.all(np.abs(Y[:, c] - ref) <= dot2_bound(ref, s, lens)), c
+
+
+REFRESH_MATS = [lambda: S.laplace2d(), lambda: S.zipf_rows(40_000, 31, lmax=3000),
+                lambda: S.small_random(700, 700, 32, density=0.02, empty_rows=0.3),
+                lambda: S.from_coo(3, 3, [1], [2], [1.5])]
+
+
+@pytest.mark.parametrize("mi", range(len(REFRESH_MATS)))
+@pytest.mark.parametrize("perm", ["symmetric", "row_only"])
+def test_value_refresh_every_format(mi, perm):
+    """Re-gathering new CRS values through the value map gives exactly the
+    arrays a fresh conversion of the new values stores, for every layout
+    (row-order re-gathers for JDS storage and SELL, entry order otherwise)."""
+    A = REFRESH_MATS[mi]()
+    v2 = S.vector(A.nnz, 33 + mi)
+    M = crs(A)
+    M2 = crs(S.CRS(A.n_rows, A.n_cols, A.row_ptr, A.col, v2, "new values"))
+    for fmt, kw in (("JDS", {}), ("NBJDS", dict(block=128)), ("NUJDS", dict(unroll=2)),
+                    ("RBJDS", dict(block=256)), ("SOJDS", dict(block=128)), ("JDS_LITERAL", {}),
+                    ("SELL", dict(window=128)), ("PSELL", dict(window=128))):
+        G = M.to_jds(fmt, perm, value_map=True, **kw)
+        G.refresh_values(dev(v2))
+        F = M2.to_jds(fmt, perm, **kw)
+        assert np.array_equal(host(G.val).view(np.int64), host(F.val).view(np.int64)), fmt
+        assert np.array_equal(host(G.col), host(F.col)), fmt
