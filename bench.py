@@ -343,41 +343,40 @@ def run_ours(args):
     h = kernel_source_hash(kname)
     traffic = NCU_TRAFFIC.get((args.config, kname, h))
 
-    # end to end through the public API: every step copies its input from
-    # pinned host memory and its result back to pinned host memory.  Steps
-    # are pipelined over two buffer sets and three streams (copy in,
-    # product, copy out), so one step's copies overlap the next step's
-    # product; a buffer is reused only after its previous use has finished.
+    # end to end through the public API: every step is one C-ABI call with
+    # host vectors (gbsp_spmv_host), which copies x in from pinned host
+    # memory, runs the product and copies y back to pinned host memory, in
+    # order on its stream.  Steps go round-robin over four streams, each
+    # with its own device stages and host output: a stream's copy in,
+    # product and copy out run in order, so four of them keep the copies in
+    # both directions and the products overlapping.
+    nstr = 4
     xh = xin.detach().cpu().pin_memory()
-    yh = [torch.empty(A.n_rows, dtype=torch.float64).pin_memory() for _ in range(2)]
-    xd = [torch.empty_like(xin) for _ in range(2)]
-    yd = [torch.empty_like(y) for _ in range(2)]
-    s_in, s_run, s_out = (torch.cuda.Stream(dev) for _ in range(3))
-    ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("in", "run", "out")}
+    yh = [torch.empty(A.n_rows, dtype=torch.float64).pin_memory() for _ in range(nstr)]
+    stages = [H.host_stage() for _ in range(nstr)]
+    streams = [torch.cuda.Stream(dev) for _ in range(nstr)]
+    main = torch.cuda.current_stream(dev)
 
     def e2e_steps(n):
         for i in range(n):
-            b = i & 1
-            s_in.wait_event(ev["run"][b])    # x buffer b: its last product has read it
-            with torch.cuda.stream(s_in):
-                xd[b].copy_(xh, non_blocking=True)
-            ev["in"][b].record(s_in)
-            s_run.wait_event(ev["in"][b])
-            s_run.wait_event(ev["out"][b])   # y buffer b: its last result is on the host
-            H.spmv(xd[b], out=yd[b], stream=s_run)
-            ev["run"][b].record(s_run)
-            s_out.wait_event(ev["run"][b])
-            with torch.cuda.stream(s_out):
-                yh[b].copy_(yd[b], non_blocking=True)
-            ev["out"][b].record(s_out)
+            b = i % nstr
+            H.spmv_host(xh, out=yh[b], stage=stages[b], stream=streams[b])
 
-    e2e_steps(4)
+    def fenced(n):
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(main)
+        for st in streams:
+            st.wait_event(t0)
+        e2e_steps(n)
+        for st in streams:
+            main.wait_stream(st)
+        t1.record(main)
+        return t0, t1
+
+    fenced(4)
     torch.cuda.synchronize(dev)
     e2e_n = 50
-    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t_start.record(s_in)
-    e2e_steps(e2e_n)
-    t_end.record(s_out)
+    t_start, t_end = fenced(e2e_n)
     torch.cuda.synchronize(dev)
     e2e_ms = t_start.elapsed_time(t_end) / e2e_n
 
@@ -402,8 +401,8 @@ def run_ours(args):
             "e2e": {"value": round(world * flops / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GFlop/s",
                     "h2d_bytes_per_step": 8 * A.n_cols, "d2h_bytes_per_step": 8 * A.n_rows,
                     "ms_per_step": round(e2e_ms, 4),
-                    "how": "pinned host x in and y out every step; copies pipelined with the next step's "
-                           "product over two buffer sets and three streams"},
+                    "how": "one gbsp_spmv_host call per step (pinned host x in, product, pinned host y out, "
+                           "in order on its stream); steps round-robin over four streams and stage sets"},
             "gpu_launches": args.steps * launches_per_step(kname, H),
             "clocks": clk.summary(),
             "formats": table,

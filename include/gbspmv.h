@@ -349,6 +349,21 @@ gbsp_status gbsp_permute_vec(gbsp_handle jds, int32_t dir, int32_t k, const void
 gbsp_status gbsp_spmv(gbsp_handle A, int32_t op, int32_t basis, int32_t accumulate,
                       const void *d_x, void *d_y, void *stream);
 
+/* gbsp_spmv with the vectors in host memory: copies h_x into the device
+ * stage d_x_stage (and h_y into d_y_stage when accumulate), runs the
+ * product into d_y_stage, and copies it back to h_y, all in order on
+ * `stream` and asynchronous to the host: h_y holds the result once the
+ * stream has been synchronised, and h_x and the stages must stay untouched
+ * until then.  Host vectors in page-locked memory move at the full speed of
+ * the host link; pageable ones are staged by the driver.  The stages are
+ * caller-allocated device vectors of the input and output sizes; calls on
+ * different streams with their own stages overlap one product with the
+ * copies of another.  Errors: those of gbsp_spmv, GBSP_ERR_ARG for NULL
+ * vectors or overlapping stages, GBSP_ERR_CUDA for a failed copy. */
+gbsp_status gbsp_spmv_host(gbsp_handle A, int32_t op, int32_t basis, int32_t accumulate,
+                           const void *h_x, void *h_y, void *d_x_stage, void *d_y_stage,
+                           void *stream);
+
 /* Y = op(A) X (+ Y) for k right-hand sides.  X and Y row-major: entry (i, c)
  * at [i*ld + c], ld >= k.  Every stored entry of A is read once per pass of
  * `rhs_tile` columns.  k = 1 with ld > 1 computes one strided column. */

@@ -95,6 +95,7 @@ SIGNATURES = {
     "gbsp_jds_split": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_i64, c_vp]),
     "gbsp_permute_vec": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_i64, c_vp, c_i64, c_vp]),
     "gbsp_spmv": (c_i32, [c_vp, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp]),
+    "gbsp_spmv_host": (c_i32, [c_vp, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "gbsp_spmm": (c_i32, [c_vp, c_i32, c_i32, c_i32, c_vp, c_i64, c_vp, c_i64, c_i32, c_vp]),
     "gbsp_transpose_workspace": (c_i32, [c_vp, P(c_i64)]),
     "gbsp_transpose_build": (c_i32, [c_vp, P(TransposeBuffers), c_i64, c_vp, P(c_vp)]),

@@ -400,6 +400,27 @@ gbsp_status gbsp_spmv(gbsp_handle A, int32_t op, int32_t basis, int32_t accumula
     return gbsp_spmm(A, op, basis, 1, d_x, 1, d_y, 1, accumulate, stream);
 }
 
+gbsp_status gbsp_spmv_host(gbsp_handle A, int32_t op, int32_t basis, int32_t accumulate, const void *h_x,
+                           void *h_y, void *d_x_stage, void *d_y_stage, void *stream) {
+    if (!A) return arg_error("gbsp_spmv_host: NULL handle");
+    if (op != GBSP_OP_N && op != GBSP_OP_T) return arg_error("gbsp_spmv_host: bad op");
+    const int64_t n_in = op == GBSP_OP_N ? A->n_cols : A->n_rows;
+    const int64_t n_out = op == GBSP_OP_N ? A->n_rows : A->n_cols;
+    const size_t es = elem_size(A->dtype);
+    if ((n_in > 0 && (!h_x || !d_x_stage)) || (n_out > 0 && (!h_y || !d_y_stage)))
+        return arg_error("gbsp_spmv_host: NULL vector or stage");
+    if (overlap(d_x_stage, (size_t)n_in * es, d_y_stage, (size_t)n_out * es))
+        return arg_error("gbsp_spmv_host: the stages overlap");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n_in > 0) GBSP_CUDA(cudaMemcpyAsync(d_x_stage, h_x, (size_t)n_in * es, cudaMemcpyHostToDevice, s));
+    if (accumulate && n_out > 0)
+        GBSP_CUDA(cudaMemcpyAsync(d_y_stage, h_y, (size_t)n_out * es, cudaMemcpyHostToDevice, s));
+    gbsp_status st = gbsp_spmm(A, op, basis, 1, d_x_stage, 1, d_y_stage, 1, accumulate, stream);
+    if (st != GBSP_OK) return st;
+    if (n_out > 0) GBSP_CUDA(cudaMemcpyAsync(h_y, d_y_stage, (size_t)n_out * es, cudaMemcpyDeviceToHost, s));
+    return GBSP_OK;
+}
+
 gbsp_status gbsp_transpose_workspace(gbsp_handle crs, int64_t *bytes) {
     if (!crs || !bytes) return arg_error("gbsp_transpose_workspace: NULL argument");
     if (crs->kind != KIND_CRS) return arg_error("gbsp_transpose_workspace: not a CRS handle");

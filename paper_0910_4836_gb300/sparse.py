@@ -94,6 +94,34 @@ class _Product(_Handle):
             raise ValueError("spmv takes a 1-D vector; use spmm for several")
         return self.spmm(x, out, accumulate, transpose, basis, stream)
 
+    def host_stage(self, transpose: bool = False, device=None) -> tuple[torch.Tensor, torch.Tensor]:
+        """Device stages (input, output) for spmv_host, reusable across calls."""
+        dev = device if device is not None else self._device
+        n_in, n_out = (self.n_rows, self.n_cols) if transpose else (self.n_cols, self.n_rows)
+        return (torch.empty(n_in, dtype=self.dtype, device=dev), torch.empty(n_out, dtype=self.dtype, device=dev))
+
+    def spmv_host(self, x: torch.Tensor, out: torch.Tensor | None = None, stage=None, accumulate: bool = False,
+                  transpose: bool = False, basis: int = L.BASIS_PERMUTED, stream=None) -> torch.Tensor:
+        """y = op(A) x with x and y in host memory: copy in, product, copy
+        out, in order on the stream (gbsp_spmv_host).  `out` holds the result
+        once the stream is synchronised; page-locked tensors move at the full
+        speed of the host link."""
+        n_in, n_out = (self.n_rows, self.n_cols) if transpose else (self.n_cols, self.n_rows)
+        for t, n, name in ((x, n_in, "x"), (out, n_out, "out")):
+            if t is None and name == "out":
+                continue
+            if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != self.dtype or t.dim() != 1 or t.numel() != n or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous host vector of {n} {self.dtype} elements")
+        if out is None:
+            out = (torch.zeros if accumulate else torch.empty)(n_out, dtype=self.dtype, pin_memory=True)
+        dx, dy = stage if stage is not None else self.host_stage(transpose)
+        if dx.numel() != n_in or dy.numel() != n_out or not (dx.is_cuda and dy.is_cuda):
+            raise ValueError("stage vectors have the wrong size")
+        L.check(L.load().gbsp_spmv_host(self._h, L.OP_T if transpose else L.OP_N, basis, int(accumulate),
+                                        _vp(x), _vp(out), _vp(dx), _vp(dy), _stream(stream)),
+                "gbsp_spmv_host")
+        return out
+
     def spmv_symmetric(self, x: torch.Tensor, out: torch.Tensor | None = None, accumulate: bool = False,
                        stream=None) -> torch.Tensor:
         """y = (S + S^T - diag S) x for the stored triangle S (FP64 atomics:
