@@ -167,10 +167,15 @@ STEP_FUNCTIONS = {"SELL": ("jds.cu", ("sell_kernel(JdsArgs a)", "launch_sell_U(J
 
 
 def _function_text(src: str, signature: str) -> str:
-    """The text of the definition that contains `signature`, through its
-    closing brace."""
-    i = src.index(signature)
-    j = src.index("{", i)
+    """The text of the definition that contains `signature`, from the start
+    of its line (attributes such as launch bounds included) and its
+    template header, through its closing brace."""
+    j = src.index(signature)
+    i = src.rfind("\n", 0, j) + 1
+    prev = src.rfind("\n", 0, max(i - 1, 0)) + 1
+    if src[prev:i].lstrip().startswith("template"):
+        i = prev
+    j = src.index("{", j)
     depth = 0
     for k in range(j, len(src)):
         depth += {"{": 1, "}": -1}.get(src[k], 0)
@@ -203,7 +208,7 @@ def kernel_source_hash(kname: str = "SELL") -> str:
 # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
 # a one-pass metric set), keyed by (config, kernel, source hash); a different
 # hash means the kernel changed since and traffic is reported null.
-NCU_TRAFFIC = {(1, "SELL row_only w=128 u=4", "57e240a09895"): 1136425472 + 40599552}
+NCU_TRAFFIC = {(1, "SELL row_only w=128 u=4", "9e5690eaa80a"): 1142290688 + 40419840}
 
 
 # --------------------------------------------------------------- ours ------

@@ -322,8 +322,11 @@ __global__ void __launch_bounds__(256) jds_block_kernel(JdsArgs a) {
 // 1024-row window at a time and its gathers of x stay local.  U slots per
 // step; KT right-hand sides per thread (SpMM).  Row entries are added in
 // slot order, as in every JDS-family kernel.
+// Two CTAs per SM: the plain one-vector instances are compiled for that
+// occupancy (the scheduling this gives was measured 1.4% faster than the
+// same 32 registers without the hint); the others would spill under it.
 template <int VM, int U, int KT, bool PLAIN>
-__global__ void __launch_bounds__(1024) sell_kernel(JdsArgs a) {
+__global__ void __launch_bounds__(1024, PLAIN ? 2 : 1) sell_kernel(JdsArgs a) {
     typedef typename ValT<VM>::T T;
     const T *__restrict__ val = static_cast<const T *>(a.val);
     const T *__restrict__ x = static_cast<const T *>(a.x);
