@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(1024, 2) sell_staged_kernel(JdsArgs a, const i
 // lanes below p).  When a lane reaches the end of its first row it sets that
 // row's sum aside and restarts; both rows are stored at the end.  Entries of
 // every row are added in order.
-template <int VM, int U, int KT>
+template <int VM, int U, int KT, bool PLAIN>
 __global__ void __launch_bounds__(1024, (KT == 1 ? 2 : 1)) psell_kernel(JdsArgs a) {
     typedef typename ValT<VM>::T T;
     const T *__restrict__ val = static_cast<const T *>(a.val);
@@ -544,10 +544,14 @@ __global__ void __launch_bounds__(1024, (KT == 1 ? 2 : 1)) psell_kernel(JdsArgs 
                         acc[q].init();
                     }
                 }
-                const T *xr = x + xidx(a.x_perm, c[j]) * a.ldx + a.c0;
+                if (PLAIN) {
+                    acc[0].add(v[j], ld_vec(x + c[j]));
+                } else {
+                    const T *xr = x + xidx(a.x_perm, c[j]) * a.ldx + a.c0;
 #pragma unroll
-                for (int q = 0; q < KT; ++q)
-                    if (KT == 1 || a.c0 + q < a.k) acc[q].add(v[j], ld_vec(xr + q));
+                    for (int q = 0; q < KT; ++q)
+                        if (KT == 1 || a.c0 + q < a.k) acc[q].add(v[j], ld_vec(xr + q));
+                }
             }
             if (d0 + U >= width) break;
 #pragma unroll
@@ -681,12 +685,16 @@ static void launch_psell_U(JdsArgs a, int KT, cudaStream_t s) {
     const int64_t nb = ceil_div(a.n_rows, 64);
     const int threads = 1024;
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(nb * 32, threads), (int64_t)num_sms() * 2));
+    const bool plain = KT == 1 && !a.x_perm && a.ldx == 1 && a.c0 == 0;
     switch (KT) {
-        case 1: psell_kernel<VM, U, 1><<<(unsigned)grid, threads, 0, s>>>(a); break;
-        case 2: psell_kernel<VM, U, 2><<<(unsigned)grid, threads, 0, s>>>(a); break;
-        case 4: psell_kernel<VM, U, 4><<<(unsigned)grid, threads, 0, s>>>(a); break;
-        case 8: psell_kernel<VM, U, 8><<<(unsigned)grid, threads, 0, s>>>(a); break;
-        default: psell_kernel<VM, U, 16><<<(unsigned)grid, threads, 0, s>>>(a); break;
+        case 1:
+            if (plain) psell_kernel<VM, U, 1, true><<<(unsigned)grid, threads, 0, s>>>(a);
+            else psell_kernel<VM, U, 1, false><<<(unsigned)grid, threads, 0, s>>>(a);
+            break;
+        case 2: psell_kernel<VM, U, 2, false><<<(unsigned)grid, threads, 0, s>>>(a); break;
+        case 4: psell_kernel<VM, U, 4, false><<<(unsigned)grid, threads, 0, s>>>(a); break;
+        case 8: psell_kernel<VM, U, 8, false><<<(unsigned)grid, threads, 0, s>>>(a); break;
+        default: psell_kernel<VM, U, 16, false><<<(unsigned)grid, threads, 0, s>>>(a); break;
     }
 }
 
