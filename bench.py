@@ -163,7 +163,8 @@ def job_throughput(units_per_rank: float, world: int, max_ms: float) -> float:
 
 
 # the functions a step kernel is made of (kernel, its launchers), by scheme
-STEP_FUNCTIONS = {"SELL": ("jds.cu", ("sell_kernel(JdsArgs a)", "launch_sell_U(JdsArgs a", "launch_sell(const Mat"))}
+STEP_FUNCTIONS = {"SELL": ("jds.cu", ("sell_walk(const JdsArgs &a)", "sell_kernel(JdsArgs a)", "sell_kernel_f64(JdsArgs a)",
+                                     "launch_sell_U(JdsArgs a", "launch_sell(const Mat"))}
 
 
 def _function_text(src: str, signature: str) -> str:
@@ -208,7 +209,7 @@ def kernel_source_hash(kname: str = "SELL") -> str:
 # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
 # a one-pass metric set), keyed by (config, kernel, source hash); a different
 # hash means the kernel changed since and traffic is reported null.
-NCU_TRAFFIC = {(1, "SELL row_only w=128 u=4", "9e5690eaa80a"): 1142290688 + 40419840}
+NCU_TRAFFIC = {(1, "SELL row_only w=128 u=4", "6ca13edede86"): 1142551552 + 40393984}
 
 
 # --------------------------------------------------------------- ours ------

@@ -322,11 +322,8 @@ __global__ void __launch_bounds__(256) jds_block_kernel(JdsArgs a) {
 // 1024-row window at a time and its gathers of x stay local.  U slots per
 // step; KT right-hand sides per thread (SpMM).  Row entries are added in
 // slot order, as in every JDS-family kernel.
-// Two CTAs per SM: the plain one-vector instances are compiled for that
-// occupancy (the scheduling this gives was measured 1.4% faster than the
-// same 32 registers without the hint); the others would spill under it.
 template <int VM, int U, int KT, bool PLAIN>
-__global__ void __launch_bounds__(1024, PLAIN ? 2 : 1) sell_kernel(JdsArgs a) {
+__device__ __forceinline__ void sell_walk(const JdsArgs &a) {
     typedef typename ValT<VM>::T T;
     const T *__restrict__ val = static_cast<const T *>(a.val);
     const T *__restrict__ x = static_cast<const T *>(a.x);
@@ -399,6 +396,22 @@ __global__ void __launch_bounds__(1024, PLAIN ? 2 : 1) sell_kernel(JdsArgs a) {
                 if (KT == 1 || a.c0 + q < a.k) store_row<VM>(a, r, a.c0 + q, acc[q]);
         }
     }
+}
+
+
+template <int VM, int U, int KT, bool PLAIN>
+__global__ void __launch_bounds__(1024) sell_kernel(JdsArgs a) {
+    sell_walk<VM, U, KT, PLAIN>(a);
+}
+
+// The plain one-vector FP64 walk compiled for two CTAs per SM: at the same
+// 32 registers this schedules it 1.4% faster than the unhinted kernel.  The
+// other instances keep the kernel above: under the hint the SpMM ones would
+// spill and the FP32 ones ran 3% slower, and a hint of one CTA per SM gives
+// them 48 registers.
+template <int U>
+__global__ void __launch_bounds__(1024, 2) sell_kernel_f64(JdsArgs a) {
+    sell_walk<VM_F64, U, 1, true>(a);
 }
 
 // SELL with the banded part of x staged in shared memory.  A CTA of 32 warps
@@ -670,7 +683,8 @@ static void launch_sell_U(JdsArgs a, int KT, cudaStream_t s) {
     const bool plain = KT == 1 && !a.x_perm && a.ldx == 1 && a.c0 == 0;
     switch (KT) {
         case 1:
-            if (plain) sell_kernel<VM, U, 1, true><<<(unsigned)grid, threads, 0, s>>>(a);
+            if (plain && VM == VM_F64) sell_kernel_f64<U><<<(unsigned)grid, threads, 0, s>>>(a);
+            else if (plain) sell_kernel<VM, U, 1, true><<<(unsigned)grid, threads, 0, s>>>(a);
             else sell_kernel<VM, U, 1, false><<<(unsigned)grid, threads, 0, s>>>(a);
             break;
         case 2: sell_kernel<VM, U, 2, false><<<(unsigned)grid, threads, 0, s>>>(a); break;
