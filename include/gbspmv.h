@@ -154,7 +154,7 @@ gbsp_status gbsp_set_status_word(gbsp_handle h, int32_t *d_status);
 
 /* ----------------------------------------------------------------- CRS -- */
 
-/* Create a CRS handle (Sect. 2, "compressed row storage": val, col_idx and
+/* Create a CRS handle (Sect. 2, compressed row storage: val, col_idx and
  * row_ptr, row i owning entries row_ptr[i] .. row_ptr[i+1]-1).
  *   0 <= n_rows, n_cols < 2^31 - 1 and 0 <= nnz <= 2^31 - 2^16 - 1: the
  *   int32 index arrays, with 2^16 entries of headroom for padded layouts.
@@ -533,9 +533,8 @@ gbsp_status gbsp_gather_sum(int32_t op, int32_t access, int64_t n, int64_t strid
 /* ------------------------------------- hybrid storage: DIA + remainder -- */
 
 /* Sect. 3.2 observes that most entries of the Holstein-Hubbard matrix sit
- * in a few dense outer secondary diagonals, each "a potential candidate for
- * special treatment by a dense storage scheme", and leaves such a hybrid
- * unbuilt.  Here the selected diagonals go to DIA storage (one value per
+ * in a few dense outer secondary diagonals, any of which could be stored
+ * densely, and leaves such a hybrid unbuilt.  Here the selected diagonals go to DIA storage (one value per
  * row, zeros where the diagonal has no entry, no column index) and every
  * other entry to a remainder CRS matrix, which may then be converted to any
  * format of this library.  The product is y = DIA x followed by the

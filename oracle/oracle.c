@@ -40,8 +40,8 @@
 #define DIAGLEN(jd, d) ((int64_t)(jd)[(d) + 1] - (int64_t)(jd)[(d)])
 
 /* ------------------------------------------------------------------------
- * CRS  (Sect. 2, CRS kernel: for each row i, for j in row i,
- *       resvec(i) = resvec(i) + val(j) * invec(col_idx(j)))
+ * CRS  (Sect. 2, CRS kernel): y_i = sum over the entries j of row i of
+ *       val_j * x[col_idx_j], added in storage order onto y_i.
  * ---------------------------------------------------------------------- */
 void orc_crs_spmv(int64_t n_rows, const int32_t *row_ptr, const int32_t *col_idx,
                   const double *val, const double *invec, double *resvec, int accumulate)
@@ -798,8 +798,8 @@ void orc_sym_spmv(int64_t n_rows, const int32_t *row_ptr_u, const int32_t *col_u
 
 /* ------------------------------------------------------------------------
  * Hybrid storage (Sect. 3.2: most entries of the Hamiltonian sit in a few
- * dense outer secondary diagonals, "candidates for special treatment by a
- * dense storage scheme"): selected diagonals in DIA form, the rest in CRS.
+ * dense outer secondary diagonals, any of which could be stored densely):
+ * selected diagonals in DIA form, the rest in CRS.
  *
  * Diagonal of offset o = col - row; its length is the number of in-matrix
  * positions (i, i+o).  fill(o) = entries with offset o / length.  The

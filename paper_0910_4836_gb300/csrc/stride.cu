@@ -6,7 +6,8 @@
 // gbsp_warp_sectors: the GB300 counterpart -- for every warp-wide gather the
 // product kernels issue, the number of distinct 32-byte sectors of x it
 // touches (1 to 32; the L2 moves whole sectors, so this is the gather's cost
-// in L2 traffic, the GPU analogue of the paper's "one cache line per entry").
+// in L2 traffic, the GPU analogue of the paper's count of cache lines loaded
+// per entry).
 //
 // Both build a histogram in shared memory per CTA and add it to the caller's
 // int64 array with integer atomics, so the counts are exact and the same on

@@ -845,7 +845,7 @@ def test_sym_spmv_hh_like_matches_crs():
 
 # --------------------------------------------------------------------------
 # Hybrid storage: dense secondary diagonals in DIA form + remainder CRS
-# (Sect. 3.2's "special treatment by a dense storage scheme")
+# (Sect. 3.2 names the dense secondary diagonals as candidates for dense storage)
 # --------------------------------------------------------------------------
 
 def dense_of(offs, dia, rem, n_cols):
