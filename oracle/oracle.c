@@ -351,8 +351,8 @@ void orc_rbjds_spmv(int64_t n_rows, int64_t n_diag, const int32_t *jd_ptr,
 }
 
 /* SOJDS (Sect. 2): inside each block the entries of a row are re-ordered so
- * that down each block column (slot d) invec is read with stride one, or as
- * close to it as possible.  Rule used here (the paper fixes none):
+ * that each block column (slot d) reads invec at consecutive indices where
+ * it can.  Rule used here (the paper fixes none):
  *   - the first row of a block keeps its order;
  *   - for every later row r, slots d = 0, 1, ... are filled in turn with the
  *     not yet placed entry of row r whose column c minimises

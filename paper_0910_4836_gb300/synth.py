@@ -275,9 +275,9 @@ HH_OUTER_OFFSETS = tuple(65536 * k for k in range(1, 7))
 
 def hh_diagonals(n: int = 6_000_000, seed: int = 5, fill: float = 0.8, band: int = 400) -> CRS:
     """Symmetric stand-in that follows Sect. 3.2's description of the
-    Holstein-Hubbard matrix literally: about 60% of the entries in the twelve
-    outermost secondary diagonals, the rest scattered evenly over a band of
-    several hundred diagonals.
+    Holstein-Hubbard matrix literally: some 60% of the entries on 12 outer
+    secondary diagonals, the rest spread evenly over a band a few hundred
+    diagonals wide.
 
     Six upper offsets 65536k (k = 1..6) each hold an entry in row i with
     probability `fill`; row i also draws U{1..4} upper entries at offsets
