@@ -419,6 +419,8 @@ def run_ours(args):
             result["symmetric"] = symmetric_numbers(M, A, x, dev, time_launches, table[kname]["ms"])
             del table
             torch.cuda.empty_cache()
+            result["spmm_adjoint"] = spmm_adjoint_numbers(M, A, x, dev, time_launches, peak)
+            torch.cuda.empty_cache()
             result["batched"] = batched_speedups(dev, time_launches)
             torch.cuda.empty_cache()
             result["fwd_bwd"] = fwd_bwd_speedup(dev, time_launches)
@@ -512,6 +514,51 @@ def fp32_errors(dev):
         out[name] = row
         del M, M32, ref, sabs
         torch.cuda.empty_cache()
+    return out
+
+
+def spmm_adjoint_numbers(M, A, x, dev, time_launches, peak):
+    """The SpMM, adjoint and dval rows on the HH-like matrix, each against
+    its own algorithmic bytes and the HBM peak: Y = A X for k = 4 and 16
+    (CRS and SELL), A^T g through the transposed CRS and through a NUJDS of
+    A^T, and dval_k = g[row_k] x[col_k]."""
+    import torch
+    N, Nc, nnz = A.n_rows, A.n_cols, A.nnz
+    out = {}
+
+    def row(t_ms, nbytes, flops):
+        return {"ms": round(t_ms, 4), "gflops": round(flops / (t_ms * 1e-3) / 1e9, 1),
+                "gbs": round(nbytes / (t_ms * 1e-3) / 1e9, 1),
+                "frac": round(nbytes / (t_ms * 1e-3) / 1e9 / peak, 3)}
+
+    M.set_kernel("vector", lanes=4, rows_per_warp=4)
+    G = M.to_jds("SELL", "row_only", window=128, unroll=4)
+    for k in (4, 16):
+        X = torch.rand(Nc, k, dtype=torch.float64, device=dev)
+        Y = torch.empty(N, k, dtype=torch.float64, device=dev)
+        nb = 12 * nnz + 4 * (N + 1) + 8 * k * (Nc + N)
+        for name, fn in (("CRS", lambda: M.spmm(X, out=Y)), ("SELL row_only w=128", lambda: G.spmm(X, out=Y))):
+            t = statistics.median(time_launches(fn, 10))
+            out[f"spmm k={k} {name}"] = row(t, nb, 2.0 * nnz * k)
+        del X, Y
+    del G
+    torch.cuda.empty_cache()
+    T = M.transpose()
+    g = torch.rand(N, dtype=torch.float64, device=dev)
+    z = torch.empty(Nc, dtype=torch.float64, device=dev)
+    ab = 12 * nnz + 4 * (Nc + 1) + 8 * N + 8 * Nc
+    t = statistics.median(time_launches(lambda: M.spmv(g, out=z, transpose=True), 10))
+    out["adjoint A^T g, transposed CRS"] = row(t, ab, 2.0 * nnz)
+    JT = T.to_jds("NUJDS", "row_only", unroll=2)
+    t = statistics.median(time_launches(lambda: JT.spmv(g, out=z), 10))
+    out["adjoint A^T g, NUJDS of A^T"] = row(t, 12 * nnz + 4 * (JT.n_diag + 1) + 16 * Nc, 2.0 * nnz)
+    del JT
+    d = torch.empty(nnz, dtype=torch.float64, device=dev)
+    db = 8 * nnz + 4 * nnz + 4 * (N + 1) + 8 * N + 8 * Nc
+    t = statistics.median(time_launches(lambda: M.dval(g, x, out=d), 10))
+    out["dval"] = row(t, db, 1.0 * nnz)
+    out["bytes"] = {"spmm": "12 nnz + 4(N+1) + 8k(N_c+N)", "adjoint": "12 nnz + 4(N_c+1) + 8N + 8N_c",
+                    "dval": "8 nnz written + 4 nnz col + 4(N+1) + 8N + 8N_c"}
     return out
 
 

@@ -130,25 +130,38 @@ crs_spmm_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
 // dval_k: d = (accumulate ? dval_k : 0), then d = fma(G[row_k, t], X[col_k, t], d)
 // for t = 0, 1, ..., m-1 (m = 1: g[row] x[col]).  One running sum in a fixed
 // order, so splitting the t range over several calls changes nothing.
-template <typename T, int L>
+// A warp owns 32 consecutive rows and walks their entries 32 at a time, so
+// every col load and dval store is one contiguous warp-wide access; each
+// lane finds its entry's row by stepping forward through the 33 row
+// pointers, which the warp keeps in shared memory.
+constexpr int kDvalWarps = kThreads / 32;
+
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
 crs_dval_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
                 const int32_t *__restrict__ col, int m, const T *__restrict__ G, int64_t g_row,
                 int64_t g_t, const T *__restrict__ X, int64_t x_row, int64_t x_t, T *__restrict__ dval,
                 int accumulate) {
-    constexpr int NG = 32 / L;
-    const int lane = threadIdx.x & 31;
-    const int grp = lane / L, gl = lane % L;
+    __shared__ int32_t srp[kDvalWarps][33];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t *rp = srp[wid];
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = warp * NG + grp; r - grp < n_rows; r += nwarp * NG) {
-        if (r >= n_rows) continue;
-        const int k0 = __ldg(row_ptr + r), k1 = __ldg(row_ptr + r + 1);
-        for (int kk = k0 + gl; kk < k1; kk += L) {
-            const int64_t cj = ld_stream(col + kk);
-            T d = accumulate ? dval[kk] : T(0);
-            for (int t = 0; t < m; ++t) d = fma(__ldg(G + r * g_row + t * g_t), __ldg(X + cj * x_row + t * x_t), d);
-            dval[kk] = d;
+    for (int64_t r0 = warp * 32; r0 < n_rows; r0 += nwarp * 32) {
+        __syncwarp();  // the previous range's row pointers are no longer read
+        rp[lane] = __ldg(row_ptr + min(r0 + lane, n_rows));
+        if (lane == 0) rp[32] = __ldg(row_ptr + min(r0 + 32, n_rows));
+        __syncwarp();
+        const int32_t e1 = rp[32];
+        int r = 0;  // local row of this lane's current entry
+        for (int32_t e = rp[0] + lane; e < e1; e += 32) {
+            while (rp[r + 1] <= e) ++r;  // stops at r <= 31, since e < rp[32]
+            const int64_t row = r0 + r;
+            const int64_t cj = ld_stream(col + e);
+            T d = accumulate ? dval[e] : T(0);
+            for (int t = 0; t < m; ++t)
+                d = fma(__ldg(G + row * g_row + t * g_t), __ldg(X + cj * x_row + t * x_t), d);
+            dval[e] = d;
         }
     }
 }
@@ -253,11 +266,21 @@ static void launch_spmm(const Mat &A, const VecArgs &v, cudaStream_t s) {
     }
 }
 
+// Default VECTOR shape.  FP64: three to six entries per lane.  On GB300
+// every step of a lane group's shuffle reduction is a full FP64 instruction
+// and idle lanes issue their FMAs anyway, so few lanes per row win: on the
+// HH-like matrix (13 entries a row) 4 lanes ran at 362 us, 8 at 555 us and
+// 16 at 1091 us.  FP32 arithmetic is cheap, and the compensated sums are
+// long dependent chains, so FP32 rows get about one lane per entry.
 void crs_default_opts(Mat &A) {
     const double mean = A.n_rows > 0 ? (double)A.nnz / (double)A.n_rows : 0.0;
     int lanes = 1;
-    while (lanes < 32 && lanes < mean) lanes <<= 1;
-    if (lanes > 1 && lanes >= 2 * mean) lanes >>= 1;
+    if (A.dtype == GBSP_F64) {
+        while (lanes < 32 && 3.0 * (2 * lanes) <= mean) lanes <<= 1;
+    } else {
+        while (lanes < 32 && lanes < mean) lanes <<= 1;
+        if (lanes > 1 && lanes >= 2 * mean) lanes >>= 1;
+    }
     A.kopt.kernel = GBSP_KERNEL_VECTOR;
     A.kopt.lanes = lanes;
     A.kopt.rows_per_warp = lanes >= 16 ? 2 : 4;
@@ -302,20 +325,10 @@ template <typename T>
 static void launch_dval(const Mat &A, int32_t m, const void *G, int64_t g_row, int64_t g_t,
                         const void *X, int64_t x_row, int64_t x_t, void *dval, int32_t accumulate,
                         cudaStream_t s) {
-    const int L = A.kopt.lanes >= 8 ? 8 : (A.kopt.lanes >= 4 ? 4 : 1);
-    const int grid = grid_for(ceil_div(A.n_rows, 32 / L));
-    auto *g = static_cast<const T *>(G);
-    auto *x = static_cast<const T *>(X);
-    auto *d = static_cast<T *>(dval);
-    if (L == 8)
-        crs_dval_kernel<T, 8><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, m, g, g_row, g_t, x,
-                                                        x_row, x_t, d, accumulate);
-    else if (L == 4)
-        crs_dval_kernel<T, 4><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, m, g, g_row, g_t, x,
-                                                        x_row, x_t, d, accumulate);
-    else
-        crs_dval_kernel<T, 1><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, m, g, g_row, g_t, x,
-                                                        x_row, x_t, d, accumulate);
+    const int grid = grid_for(ceil_div(A.n_rows, 32));
+    crs_dval_kernel<T><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, m, static_cast<const T *>(G), g_row,
+                                                 g_t, static_cast<const T *>(X), x_row, x_t, static_cast<T *>(dval),
+                                                 accumulate);
 }
 
 gbsp_status crs_dval_launch(const Mat &A, int32_t m, const void *G, int64_t g_row, int64_t g_t,
