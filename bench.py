@@ -22,6 +22,11 @@ import subprocess
 import sys
 import time
 
+# The CPU oracle's OpenMP threads sit one per core, packed (the paper's
+# pinned runs).  Set before any OpenMP runtime in this process starts.
+os.environ.setdefault("OMP_PROC_BIND", "close")
+os.environ.setdefault("OMP_PLACES", "cores")
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -801,18 +806,21 @@ def cpu_baseline(A, x, seconds):
     import oracle as O
     y = np.zeros(A.n_rows)
     O.crs_spmv_omp(A, x, y)  # first touch
-    t0 = time.perf_counter()
-    reps = 0
+    times = []
+    t_all = time.perf_counter()
     while True:
+        t0 = time.perf_counter()
         O.crs_spmv_omp(A, x, y)
-        reps += 1
-        el = time.perf_counter() - t0
-        if el >= seconds or reps >= 200:
+        times.append(time.perf_counter() - t0)
+        el = time.perf_counter() - t_all
+        if (el >= seconds and len(times) >= 5) or len(times) >= 200:
             break
-    per = el / reps
+    per = statistics.median(times)
     out = {"value": round(2.0 * A.nnz / per / 1e9, 3), "unit": "GFlop/s",
            "cores": O.num_threads(), "kind": "oracle",
-           "sample": f"full matrix, {reps} SpMVMs with the OpenMP static CRS loop ({el:.1f} s)"}
+           "cores_in_affinity_mask": len(os.sched_getaffinity(0)),
+           "omp": {k: os.environ.get(k) for k in ("OMP_PROC_BIND", "OMP_PLACES")},
+           "sample": f"full matrix, median of {len(times)} SpMVMs with the OpenMP static CRS loop ({el:.1f} s)"}
     t0 = time.perf_counter()
     O.crs_spmv(A, x)
     out["serial_crs_gflops"] = round(2.0 * A.nnz / (time.perf_counter() - t0) / 1e9, 3)
