@@ -26,6 +26,9 @@ import time
 # pinned runs).  Set before any OpenMP runtime in this process starts.
 os.environ.setdefault("OMP_PROC_BIND", "close")
 os.environ.setdefault("OMP_PLACES", "cores")
+# host cores this process may use, read before any OpenMP binding narrows
+# the main thread's own mask to one core
+AFFINITY_CORES = len(os.sched_getaffinity(0))
 
 import numpy as np
 
@@ -818,7 +821,7 @@ def cpu_baseline(A, x, seconds):
     per = statistics.median(times)
     out = {"value": round(2.0 * A.nnz / per / 1e9, 3), "unit": "GFlop/s",
            "cores": O.num_threads(), "kind": "oracle",
-           "cores_in_affinity_mask": len(os.sched_getaffinity(0)),
+           "cores_in_affinity_mask": AFFINITY_CORES,
            "omp": {k: os.environ.get(k) for k in ("OMP_PROC_BIND", "OMP_PLACES")},
            "sample": f"full matrix, median of {len(times)} SpMVMs with the OpenMP static CRS loop ({el:.1f} s)"}
     t0 = time.perf_counter()
