@@ -22,7 +22,6 @@ invariants and a closed-form banded case.
 from __future__ import annotations
 
 import ctypes
-import os
 
 import numpy as np
 

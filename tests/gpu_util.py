@@ -6,7 +6,6 @@ import functools
 import numpy as np
 import torch
 
-import oracle as O
 from paper_0910_4836_gb300 import synth as S
 
 # FP64 acceptance per entry: |y - y_ref| <= 1e-14 * sum_j |a_ij||x_j|
