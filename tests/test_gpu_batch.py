@@ -149,3 +149,35 @@ def test_autotuned_batch_with_sell_items():
     for Y, ref in zip(Ys, refs):
         assert torch.equal(Y, ref)
     assert all(isinstance(h, JDSMatrix) or h.__class__.__name__ == "CRSMatrix" for h in handles)
+
+
+def test_all_sell_one_vector_batch():
+    """A batch of one-vector FP64 SELL items (the plain batched SELL walk):
+    each result equals the handle's own product bit for bit, also when one
+    item reads and writes a strided column."""
+    from paper_0910_4836_gb300 import Batch
+    mats = small_batch(20, 11)
+    items, refs = [], []
+    for b, A in enumerate(mats):
+        H = crs(A).to_jds("SELL", "row_only", window=(128, 1024)[b % 2], unroll=(2, 4)[b % 2])
+        X = dev(S.vector(A.n_cols, 200 + b))
+        Y = torch.full((A.n_rows,), 3.0, dtype=torch.float64, device="cuda")
+        items.append((H, X, Y))
+        refs.append(H.spmv(X))
+    bt = Batch(items, chunk=2048)
+    bt.run()
+    torch.cuda.synchronize()
+    for (_, _, Y), ref in zip(items, refs):
+        assert torch.equal(Y, ref)
+    # one item reading and writing a strided column: same bits
+    A0 = mats[0]
+    X2 = dev(np.stack([S.vector(A0.n_cols, 200), S.vector(A0.n_cols, 201)], axis=1))
+    Y2 = torch.zeros((A0.n_rows, 2), dtype=torch.float64, device="cuda")
+    items2 = [(items[0][0], X2[:, :1], Y2[:, :1])] + items[1:]
+    for _, _, Y in items2[1:]:
+        Y.fill_(-1.0)
+    Batch(items2, chunk=2048).run()
+    torch.cuda.synchronize()
+    assert torch.equal(Y2[:, 0], refs[0])
+    for (_, _, Y), ref in zip(items2[1:], refs[1:]):
+        assert torch.equal(Y, ref)
