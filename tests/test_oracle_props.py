@@ -106,3 +106,44 @@ def test_gather_sums_exact_on_integers(n, k, seed):
     assert O.gather_sum("SCP", "CS", n, b, a=a, k=k) == ref
     assert O.gather_sum("SCP", "IND", n, b, a=a, ind=ind) == ref
     assert O.gather_sum_exact("SCP", "IND", n, b, a=a, ind=ind)[0] == ref
+
+
+@SETTINGS
+@given(int_matrices(square=False), st.integers(1, 6), st.integers(0, 1000))
+def test_spmm_and_exact_spmm_are_dense_products(A, k, seed):
+    """Every column of the SpMM loops, plain and exact (with its Σ|a||x|), is
+    the dense integer product."""
+    X = np.stack([S.int_vector(A.n_cols, seed + c, 1000) for c in range(k)], axis=1)
+    D = dense_int(A)
+    ref = (D @ X.astype(np.int64)).astype(float)
+    assert np.array_equal(O.crs_spmm(A, X), ref)
+    Y, Sabs = O.crs_spmm_exact(A, X)
+    assert np.array_equal(Y, ref)
+    assert np.array_equal(Sabs, (np.abs(D) @ np.abs(X.astype(np.int64))).astype(float))
+
+
+@SETTINGS
+@given(int_matrices(square=False), st.integers(0, 1000))
+def test_adjoint_and_dval_are_their_definitions(A, seed):
+    """A^T g is the dense transposed product; dval_k = g[row_k] x[col_k]."""
+    g = S.int_vector(A.n_rows, seed, 1000)
+    x = S.int_vector(A.n_cols, seed + 1, 1000)
+    D = dense_int(A)
+    assert np.array_equal(O.crs_spmv_t(A, g), (D.T @ g.astype(np.int64)).astype(float))
+    t, st_ = O.crs_spmv_t_exact(A, g)
+    assert np.array_equal(t, (D.T @ g.astype(np.int64)).astype(float))
+    rid = A.row_ids().astype(np.int64)
+    want = (g.astype(np.int64)[rid] * x.astype(np.int64)[A.col]).astype(float)
+    assert np.array_equal(O.dval(A, g, x), want)
+
+
+@SETTINGS
+@given(int_matrices(square=False), st.integers(0, 1000))
+def test_fp32_loop_exact_below_2_24(A, seed):
+    """With |a|, |x| <= 64 and at most 40 entries a row every partial sum is
+    an integer below 2^24, so the FP32 loop is exact."""
+    Ai = S.integer_values(A, seed, 64) if A.nnz else A
+    x = S.int_vector(A.n_cols, seed + 2, 64)
+    ref = (dense_int(Ai) @ x.astype(np.int64))
+    assert np.abs(ref).max(initial=0) < 2 ** 24
+    assert np.array_equal(O.crs_spmv_f32(Ai, x), ref.astype(np.float32))
