@@ -33,3 +33,25 @@ def test_algorithmic_bytes():
     # val + col once, row_ptr once, x at least once, y once
     assert bench.algorithmic_bytes(10, 20, 100) == 8 * 100 + 4 * 100 + 4 * 11 + 8 * 20 + 8 * 10
     assert bench.algorithmic_bytes(10, 20, 100, vbytes=4) == 4 * 100 + 4 * 100 + 4 * 11 + 4 * 20 + 4 * 10
+
+
+def test_reference_arm_line_contract(monkeypatch):
+    """--impl reference times the CPU oracle and prints the contract's keys
+    (here on the small Laplacian workload, rank 0 of one)."""
+    import argparse
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    args = argparse.Namespace(config=0, steps=3, warmup=1)
+    r = bench.run_reference(args)
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "impl", "config", "cpu_baseline", "e2e"):
+        assert key in r, key
+    assert r["impl"] == "reference" and r["value"] > 0 and r["steps"] == 3 and r["higher_is_better"] is True
+    assert r["config"]["workload"] and r["config"]["n_rows"] == 4096
+    cb = r["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == r["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert r["e2e"] == {"value": r["value"], "unit": r["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    # other ranks print nothing
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    assert bench.run_reference(args) is None
