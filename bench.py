@@ -37,7 +37,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SpMVM GFlop/s & HBM GB/s vs roofline; batched & fwd+bwd speedup vs plain"
 WORKLOAD = ("hh_like N=6,000,000 FP64 SpMVM, fastest of CRS and the JDS family "
-            "(symmetric banded + 20% scattered, ~13 nnz/row)")
+            "(symmetric banded + 20% scattered, ~13 nnz/row)
+WORKLOADS = {
+    0: "laplace2d 64x64 FP64 SpMVM (5-point, Dirichlet; latency-bound)",
+    1: WORKLOAD,
+    2: "zipf_rows N=4,000,000 FP64 SpMVM (Zipf(2) row lengths up to 5000, random columns)",
+    4: "stencil27 100^3 FP64 SpMVM (27-point, N=1,000,000)",
+}")
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -403,7 +409,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64; stand-in for the paper's Holstein-Hubbard matrix)",
             "hbm_gbs": round(gbs, 1),
-            "config": {"workload": WORKLOAD, "config_index": args.config, "n_rows": A.n_rows,
+            "config": {"workload": WORKLOADS.get(args.config, WORKLOAD), "config_index": args.config, "n_rows": A.n_rows,
                        "nnz": A.nnz, "kernel": kname, "vectors": basis,
                        "l2": "inputs larger than L2 (matrix ~1 GB), no flush",
                        "parallelism": f"replicas x{world}"},
@@ -857,7 +863,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": round(per * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "config_index": args.config, "n_rows": A.n_rows,
+            "config": {"workload": WORKLOADS.get(args.config, WORKLOAD), "config_index": args.config, "n_rows": A.n_rows,
                        "nnz": A.nnz, "kernel": "oracle CRS loop, OpenMP static schedule"},
             "cpu_baseline": {"value": val, "unit": "GFlop/s", "cores": O.num_threads(),
                              "kind": "oracle", "sample": f"full matrix, {args.steps} timed SpMVMs"},

@@ -47,7 +47,7 @@ def test_reference_arm_line_contract(monkeypatch):
                 "scaling", "vs_baseline", "dtype", "data", "impl", "config", "cpu_baseline", "e2e"):
         assert key in r, key
     assert r["impl"] == "reference" and r["value"] > 0 and r["steps"] == 3 and r["higher_is_better"] is True
-    assert r["config"]["workload"] and r["config"]["n_rows"] == 4096
+    assert r["config"]["workload"].startswith("laplace2d") and r["config"]["n_rows"] == 4096
     cb = r["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == r["value"] and cb["cores"] >= 1 and cb["sample"]
     assert r["e2e"] == {"value": r["value"], "unit": r["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
