@@ -37,13 +37,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SpMVM GFlop/s & HBM GB/s vs roofline; batched & fwd+bwd speedup vs plain"
 WORKLOAD = ("hh_like N=6,000,000 FP64 SpMVM, fastest of CRS and the JDS family "
-            "(symmetric banded + 20% scattered, ~13 nnz/row)
+            "(symmetric banded + 20% scattered, ~13 nnz/row)")
 WORKLOADS = {
     0: "laplace2d 64x64 FP64 SpMVM (5-point, Dirichlet; latency-bound)",
     1: WORKLOAD,
     2: "zipf_rows N=4,000,000 FP64 SpMVM (Zipf(2) row lengths up to 5000, random columns)",
     4: "stencil27 100^3 FP64 SpMVM (27-point, N=1,000,000)",
-}")
+}
 FALLBACK_HBM_GBS = 6800.0
 
 
