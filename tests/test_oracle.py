@@ -512,6 +512,21 @@ def test_power_gradient_closed_form_symmetric():
 
 # -------------------------------------------------------- generators ----
 
+def test_splitmix64_published_sequence():
+    """Draw t of a stream is mix(key + (t+1)*GAMMA); with key 0 that is the
+    SplitMix64 generator started from state 0, whose first outputs are
+    published (Steele, Lea & Flood 2014; Vigna's reference code)."""
+    gamma = np.uint64(0x9E3779B97F4A7C15)
+    with np.errstate(over="ignore"):
+        z = np.array([np.uint64(t + 1) * gamma for t in range(4)], dtype=np.uint64)
+    got = [int(v) for v in S._mix(z)]
+    assert got == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC]
+    # uniform01 uses the top 53 bits
+    u = S.uniform01(0, 0, np.arange(4))
+    assert np.all((u >= 0) & (u < 1))
+    assert np.array_equal(u, (S.bits(0, 0, np.arange(4)) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53)
+
+
 def test_generator_shapes():
     A = S.hh_like(20000, 1)
     D = A.to_dense() if A.n_rows <= 2000 else None
