@@ -137,16 +137,20 @@ const char *gbsp_status_string(gbsp_status s);
  * (thread-local, static storage, empty if none). */
 const char *gbsp_last_error(void);
 
-/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH (library plumbing; no
+ * counterpart in the paper). */
 int32_t gbsp_version(void);
 
-/* Release a matrix handle (never the borrowed buffers).  NULL is a no-op. */
+/* Release a matrix handle (never the borrowed buffers).  NULL is a no-op.
+ * Library plumbing; no counterpart in the paper. */
 gbsp_status gbsp_destroy(gbsp_handle h);
 
-/* Copy a device status word to *h_out (synchronises `stream`). */
+/* Copy a device status word to *h_out (synchronises `stream`).  Library
+ * plumbing for the bounded waits; no counterpart in the paper. */
 gbsp_status gbsp_read_status(const int32_t *d_status, void *stream, int32_t *h_out);
 
-/* Give a handle a device status word (int32, caller memory, NULL to clear).
+/* Library plumbing, no counterpart in the paper.
+ * Give a handle a device status word (int32, caller memory, NULL to clear).
  * Kernels with bounded waits (the TILED pipeline) store GBSP_ERR_TIMEOUT
  * there if a wait exceeds its limit (2 s) instead of hanging; the caller
  * resets it to 0.  Without a word such a timeout is silent. */
@@ -168,25 +172,29 @@ gbsp_status gbsp_crs_create(int64_t n_rows, int64_t n_cols, int64_t nnz,
                             const int32_t *d_row_ptr, const int32_t *d_col,
                             const void *d_val, gbsp_dtype dtype, gbsp_handle *out);
 
-/* Point a CRS or JDS-family handle at new values (same pattern, same dtype,
+/* Sect. 2 storage: the val array of a handle.
+ * Point a CRS or JDS-family handle at new values (same pattern, same dtype,
  * d_val borrowed like the original).  Host-side only: no device work.  For
  * a JDS-family handle built with a value map (gbsp_jds_buffers.vmap) use
  * gbsp_jds_values to re-gather its values instead. */
 gbsp_status gbsp_set_values(gbsp_handle h, const void *d_val);
 
-/* Check the CRS arrays on the device: row_ptr[0] == 0, row_ptr
+/* Sect. 2, the CRS arrays and what they must satisfy.
+ * Check the CRS arrays on the device: row_ptr[0] == 0, row_ptr
  * non-decreasing, row_ptr[n_rows] == nnz, 0 <= col < n_cols.  Writes 0 to
  * *d_status when all hold, else a GBSP_ERR_MATRIX code (no trap, no abort).
  * d_status: int32 in device memory.  Asynchronous on `stream`. */
 gbsp_status gbsp_crs_validate(gbsp_handle crs, int32_t *d_status, void *stream);
 
-/* Choose the kernel used by gbsp_spmv / gbsp_spmm for this CRS handle.
+/* Sect. 2 CRS kernel; the lane / row / tile shapes are the GPU's own.
+ * Choose the kernel used by gbsp_spmv / gbsp_spmm for this CRS handle.
  * Only fields that differ from 0 override the current choice.  Errors:
  * GBSP_ERR_ARG for out-of-range values. */
 gbsp_status gbsp_set_kernel(gbsp_handle h, const gbsp_kernel_opts *opts);
 gbsp_status gbsp_get_kernel(gbsp_handle h, gbsp_kernel_opts *out);
 
-/* TILED kernel set-up: bytes of the tile table for `tile` (1024 or 2048)
+/* Sect. 2 CRS kernel, TILED GPU variant (no counterpart in the paper).
+ * TILED kernel set-up: bytes of the tile table for `tile` (1024 or 2048)
  * merge items per tile (the first row of every tile, then 16 bytes of
  * offsets per tile), and a device pass that fills it into caller memory
  * (16-byte aligned; borrowed until destroy or the next prepare).  The table
@@ -236,7 +244,9 @@ typedef struct {
 gbsp_status gbsp_jds_plan(gbsp_handle crs, const gbsp_jds_opts *opts, int32_t *d_scratch,
                           void *stream, gbsp_jds_sizes *out);
 
-/* Build the JDS-family arrays on the device and return a handle over them
+/* Sect. 2, JDS construction and its refinements (NBJDS, RBJDS, NUJDS,
+ * SOJDS); SELL / PSELL have no counterpart in the paper.
+ * Build the JDS-family arrays on the device and return a handle over them
  * (borrowing `bufs`, except workspace).  Steps: row lengths; stable sort by
  * decreasing length (ties keep original row order, empty rows last) giving
  * perm / iperm; jd_ptr from #{rows with length > d}; entries shifted left
@@ -264,13 +274,15 @@ gbsp_status gbsp_jds_build(gbsp_handle crs, const gbsp_jds_opts *opts,
  * Host-side only.  Errors: GBSP_ERR_ARG for a negative cap. */
 gbsp_status gbsp_set_grid_limit(gbsp_handle h, int32_t max_ctas);
 
-/* Switch a built JDS-family handle between the formats that share its
+/* Sect. 2: JDS, NBJDS and NUJDS read the same storage.
+ * Switch a built JDS-family handle between the formats that share its
  * storage pattern (JDS <-> NBJDS <-> NUJDS <-> JDS_LITERAL) and set block
  * or unroll.  RBJDS / SOJDS handles accept only a block size equal to the
  * one they were built with.  Errors: GBSP_ERR_UNSUPPORTED otherwise. */
 gbsp_status gbsp_jds_set_format(gbsp_handle jds, int32_t format, int32_t block, int32_t unroll);
 
-/* Re-gather a JDS-family handle's values from CRS-ordered values d_src_val
+/* Sect. 2 storage: the permuted val array.
+ * Re-gather a JDS-family handle's values from CRS-ordered values d_src_val
  * (nnz entries, the handle's dtype): val[i] = d_src_val[vmap[i]].  For
  * values that change while the pattern stays (training, time stepping).
  * Errors: GBSP_ERR_UNSUPPORTED if the handle was built without vmap. */
@@ -323,7 +335,8 @@ gbsp_status gbsp_jds_split_bytes(gbsp_handle jds, int32_t depth, int32_t chunk, 
 gbsp_status gbsp_jds_split(gbsp_handle jds, int32_t depth, int32_t chunk, void *d_ws,
                            int64_t ws_bytes, void *stream);
 
-/* Read back the JDS-family shape (host-side, no device work). */
+/* Read back the JDS-family shape (host-side, no device work).  Library
+ * plumbing; no counterpart in the paper. */
 gbsp_status gbsp_jds_info(gbsp_handle jds, gbsp_jds_sizes *out, gbsp_jds_opts *opts);
 
 /* Vector basis change (Sect. 2, "all further calculations are performed in
@@ -349,7 +362,8 @@ gbsp_status gbsp_permute_vec(gbsp_handle jds, int32_t dir, int32_t k, const void
 gbsp_status gbsp_spmv(gbsp_handle A, int32_t op, int32_t basis, int32_t accumulate,
                       const void *d_x, void *d_y, void *stream);
 
-/* gbsp_spmv with the vectors in host memory: copies h_x into the device
+/* Sect. 2 product; the host transfers are library plumbing.
+ * gbsp_spmv with the vectors in host memory: copies h_x into the device
  * stage d_x_stage (and h_y into d_y_stage when accumulate), runs the
  * product into d_y_stage, and copies it back to h_y, all in order on
  * `stream` and asynchronous to the host: h_y holds the result once the
@@ -364,7 +378,8 @@ gbsp_status gbsp_spmv_host(gbsp_handle A, int32_t op, int32_t basis, int32_t acc
                            const void *h_x, void *h_y, void *d_x_stage, void *d_y_stage,
                            void *stream);
 
-/* Y = op(A) X (+ Y) for k right-hand sides.  X and Y row-major: entry (i, c)
+/* The Sect. 2 sums applied to k vectors at once (no counterpart in the paper).
+ * Y = op(A) X (+ Y) for k right-hand sides.  X and Y row-major: entry (i, c)
  * at [i*ld + c], ld >= k.  Every stored entry of A is read once per pass of
  * `rhs_tile` columns.  k = 1 with ld > 1 computes one strided column. */
 gbsp_status gbsp_spmm(gbsp_handle A, int32_t op, int32_t basis, int32_t k, const void *d_X,
@@ -372,7 +387,9 @@ gbsp_status gbsp_spmm(gbsp_handle A, int32_t op, int32_t basis, int32_t k, const
 
 /* ------------------------------------------------------- adjoint, dval -- */
 
-/* Transposed structure of a CRS handle: a CRS of A^T (n_cols rows) whose
+/* Transpose of the Sect. 2 CRS sum, for the adjoint A^T g (no counterpart
+ * in the paper).
+ * Transposed structure of a CRS handle: a CRS of A^T (n_cols rows) whose
  * entries are listed per column of A in ascending entry order, plus
  * tmap[t] = index in A of transposed entry t.  Values are gathered with
  * gbsp_transpose_values (again whenever A's values change).  The result
@@ -390,21 +407,26 @@ typedef struct {
 gbsp_status gbsp_transpose_workspace(gbsp_handle crs, int64_t *bytes);
 gbsp_status gbsp_transpose_build(gbsp_handle crs, const gbsp_transpose_buffers *bufs,
                                  int64_t workspace_bytes, void *stream, gbsp_handle *out);
-/* t_val[t] = val[tmap[t]] for the transpose built from `crs`. */
+/* Transpose of the Sect. 2 CRS sum (no counterpart in the paper).
+ * t_val[t] = val[tmap[t]] for the transpose built from `crs`. */
 gbsp_status gbsp_transpose_values(gbsp_handle crs, void *stream);
 
-/* Make `at` (any handle holding A^T, e.g. a JDS of the transpose) the one
+/* Transpose of the Sect. 2 CRS sum (no counterpart in the paper).
+ * Make `at` (any handle holding A^T, e.g. a JDS of the transpose) the one
  * used for gbsp_spmv(A, OP_T, ...).  Borrowed; no checks of its content. */
 gbsp_status gbsp_attach_transpose(gbsp_handle A, gbsp_handle at);
 
-/* Value gradient of a CRS product: dval_k = g[row_k] * x[col_k] (the
+/* Derivative of the Sect. 2 sum with respect to val (no counterpart in
+ * the paper).
+ * Value gradient of a CRS product: dval_k = g[row_k] * x[col_k] (the
  * derivative of g.(A x) with respect to val_k), written (or added with one
  * fused multiply-add, if accumulate) in CRS entry order.  g: n_rows,
  * x: n_cols, dval: nnz. */
 gbsp_status gbsp_dval(gbsp_handle crs, const void *d_g, const void *d_x, void *d_dval,
                       int32_t accumulate, void *stream);
 
-/* Fused multi-step value gradient: d = (accumulate ? dval_k : 0), then
+/* Derivative of iterated Sect. 2 products A^m x (Sect. 1: eigensolvers).
+ * Fused multi-step value gradient: d = (accumulate ? dval_k : 0), then
  * d = fma(G[row_k, t], X[col_k, t], d) for t = 0 .. m-1, with G (n_rows x m,
  * ld ldg) and X (n_cols x m, ld ldx) row-major: one pass over the entries
  * for m product pairs of an iterated product A^m x.  The fixed order makes
@@ -413,7 +435,8 @@ gbsp_status gbsp_dval_multi(gbsp_handle crs, int32_t m, const void *d_G, int64_t
                             const void *d_X, int64_t ldx, void *d_dval, int32_t accumulate,
                             void *stream);
 
-/* The same with any element layout: G[row, t] at d_G + row*g_row + t*g_t and
+/* Derivative of iterated Sect. 2 products A^m x (Sect. 1: eigensolvers).
+ * The same with any element layout: G[row, t] at d_G + row*g_row + t*g_t and
  * X[col, t] at d_X + col*x_row + t*x_t (elements; all strides >= 1).  With
  * g_row = x_row = 1 and g_t = x_t = the vector length, G and X are m
  * separate contiguous vectors (column-major), the layout in which each of
@@ -441,12 +464,14 @@ typedef struct {
     int64_t ldy;
 } gbsp_batch_item;
 
-/* Bytes of the device work table for n items (work items of about
+/* Many Sect. 2 products in one launch (no counterpart in the paper).
+ * Bytes of the device work table for n items (work items of about
  * `chunk` entries each; 0 = 4096). */
 gbsp_status gbsp_batch_plan(int32_t n, const gbsp_batch_item *items, int32_t chunk,
                             int64_t *table_bytes);
 
-/* Write the work table into caller memory d_table (256-byte aligned,
+/* Many Sect. 2 products in one launch (no counterpart in the paper).
+ * Write the work table into caller memory d_table (256-byte aligned,
  * table_bytes from the plan) and return a batch object.  Reads each
  * matrix's row pointers back to the host once and synchronises `stream`.
  * d_ready (may be NULL): an int32 flag in device or host-mapped memory;
@@ -457,7 +482,8 @@ gbsp_status gbsp_batch_create(int32_t n, const gbsp_batch_item *items, int32_t c
                               void *d_table, int64_t table_bytes, const int32_t *d_ready,
                               void *stream, gbsp_batch *out);
 
-/* All items in one persistent launch: CTAs take work items from the table
+/* Many Sect. 2 products in one launch (no counterpart in the paper).
+ * All items in one persistent launch: CTAs take work items from the table
  * through a device counter (reset by a memset on `stream` first, so the
  * memset + kernel pair can be captured in a CUDA graph and replayed).
  * Items are written, never accumulated.  CRS items use the VECTOR
@@ -468,7 +494,8 @@ gbsp_status gbsp_batch_create(int32_t n, const gbsp_batch_item *items, int32_t c
  * does no work); the caller resets it. */
 gbsp_status gbsp_batch_run(gbsp_batch b, int32_t *d_status, void *stream);
 
-/* Number of work items and persistent CTAs of a batch (host-side). */
+/* Number of work items and persistent CTAs of a batch (host-side).
+ * Library plumbing; no counterpart in the paper. */
 gbsp_status gbsp_batch_info(gbsp_batch b, int64_t *n_work, int32_t *grid);
 gbsp_status gbsp_batch_destroy(gbsp_batch b);
 
@@ -510,11 +537,13 @@ gbsp_status gbsp_crs_spmv_noalloc(int64_t n_rows, int64_t n_cols, int64_t nnz,
 typedef enum { GBSP_GATHER_ADD = 0, GBSP_GATHER_SCP = 1 } gbsp_gather_op;
 typedef enum { GBSP_ACCESS_PD = 0, GBSP_ACCESS_CS = 1, GBSP_ACCESS_IND = 2 } gbsp_access;
 
-/* Number of FP64 partial sums gbsp_gather_sum needs for n elements on the
+/* Sect. 3.1, the basic sparse vector operations.
+ * Number of FP64 partial sums gbsp_gather_sum needs for n elements on the
  * current device (one per CTA of its grid). */
 gbsp_status gbsp_gather_partials(int64_t n, int32_t *n_partials);
 
-/* *d_out = the sum above, FP64.  d_a [n] (SCP only), d_b [len_b], d_ind [n]
+/* Sect. 3.1, the basic sparse vector operations.
+ * *d_out = the sum above, FP64.  d_a [n] (SCP only), d_b [len_b], d_ind [n]
  * (IND only) int32, all device memory borrowed for the call; d_partials is
  * caller scratch of n_partials doubles (>= gbsp_gather_partials(n)).  Each
  * thread sums its elements in ascending i, then fixed reduction trees: the
@@ -534,8 +563,9 @@ gbsp_status gbsp_gather_sum(int32_t op, int32_t access, int64_t n, int64_t strid
 
 /* Sect. 3.2 observes that most entries of the Holstein-Hubbard matrix sit
  * in a few dense outer secondary diagonals, any of which could be stored
- * densely, and leaves such a hybrid unbuilt.  Here the selected diagonals go to DIA storage (one value per
- * row, zeros where the diagonal has no entry, no column index) and every
+ * densely, and leaves such a hybrid unbuilt.  Here the selected diagonals
+ * go to DIA storage (one value per row, zeros where the diagonal has no
+ * entry, no column index) and every
  * other entry to a remainder CRS matrix, which may then be converted to any
  * format of this library.  The product is y = DIA x followed by the
  * remainder's product with accumulate = 1, so y_i = (DIA sum) + (remainder
@@ -598,7 +628,8 @@ gbsp_status gbsp_upper_plan(gbsp_handle crs, int32_t *d_row_ptr_u, void *d_ws, i
 gbsp_status gbsp_upper_build(gbsp_handle crs, const int32_t *d_row_ptr_u, int32_t *d_col_u, void *d_val_u,
                              int64_t nnz_upper, void *stream, gbsp_handle *out);
 
-/* y = (S + S^T - diag S) x for the stored entries S of handle `S` -- A x
+/* Sect. 3.2: the Hamiltonian is symmetric (the paper stores it in full).
+ * y = (S + S^T - diag S) x for the stored entries S of handle `S` -- A x
  * when S holds the upper triangle of a symmetric A.  S: a CRS handle
  * (thread per row) or a SELL handle with the row-only permutation (warp per
  * 32-row block; vectors in the original basis either way).  FP64 only.
@@ -642,7 +673,9 @@ gbsp_status gbsp_warp_sectors(gbsp_handle A, int32_t lanes, int32_t elem_bytes, 
 
 /* ------------------------------------------------------------ autotuner -- */
 
-/* Time the candidate kernels for `A` with k right-hand sides on the device
+/* Chooses among the Sect. 2 kernels and block sizes, the GPU counterpart
+ * of the paper's block-size sweeps (Sect. 4).
+ * Time the candidate kernels for `A` with k right-hand sides on the device
  * (CUDA events on `stream`, a few repetitions each, X and Y are scratch
  * vectors of the right sizes) and keep the fastest option set on the handle.
  * For CRS handles the candidates are VECTOR with every lanes/rows_per_warp
