@@ -61,12 +61,14 @@ def parse():
     p.add_argument("--ncu-case", action="store_true",
                    help="no timing: run 3 launches of the --kernel candidate on a 2,000,000-row "
                         "HH-like matrix (larger than L2, small enough for an ncu capture)")
+    p.add_argument("--ncu-full", action="store_true",
+                   help="with --ncu-case: the full-size workload instead of the 2,000,000-row one")
     p.add_argument("--micro", action="store_true",
-                   help="instead of the SpMVM step: the basic gather operations of Sect. 3.1 "
+                   help="instead of the SpMVM step: the basic gather operations of Sect. 4.1 "
                         "(ADD/SCP over PD, CS, IS, IR; stride sweep; Gaussian stride plane), one JSON line")
     p.add_argument("--analysis", action="store_true",
                    help="instead of the SpMVM step: stride distribution and sectors per warp gather of "
-                        "every storage scheme, and block / lanes / window sweeps (Sect. 4), one JSON line")
+                        "every storage scheme, and block / lanes / window sweeps (Sect. 4.2), one JSON line")
     return p.parse_args()
 
 
@@ -177,7 +179,7 @@ def job_throughput(units_per_rank: float, world: int, max_ms: float) -> float:
 
 
 # the functions a step kernel is made of (kernel, its launchers), by scheme
-STEP_FUNCTIONS = {"SELL": ("jds.cu", ("sell_walk(const JdsArgs &a)", "sell_kernel(JdsArgs a)", "sell_kernel_f64(JdsArgs a)",
+STEP_FUNCTIONS = {"SELL": ("jds.cu", ("store_row(const JdsArgs &a", "sell_walk(const JdsArgs &a)", "sell_kernel(JdsArgs a)", "sell_kernel_f64(JdsArgs a)",
                                      "launch_sell_U(JdsArgs a", "launch_sell(const Mat"))}
 
 
@@ -223,7 +225,7 @@ def kernel_source_hash(kname: str = "SELL") -> str:
 # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
 # a one-pass metric set), keyed by (config, kernel, source hash); a different
 # hash means the kernel changed since and traffic is reported null.
-NCU_TRAFFIC = {(1, "SELL row_only w=128 u=4", "6ca13edede86"): 1142551552 + 40393984}
+NCU_TRAFFIC = {}
 
 
 # --------------------------------------------------------------- ours ------
@@ -245,52 +247,102 @@ def _timer(dev):
     return time_launches
 
 
+def jds_method_bytes(A, ptr_entries):
+    """Sect. 8(d) method bytes of one JDS-family SpMVM in one basis: val and
+    col once (12 B an entry), the format's pointer array (jd_ptr or blk_ptr,
+    4 B an entry), x read once and y written once.  The format's own extras
+    (SELL's row lengths, the permutation read by a fused basis change) are
+    overhead, reported separately."""
+    return 12 * A.nnz + 4 * ptr_entries + 8 * A.n_cols + 8 * A.n_rows
+
+
+class Cand:
+    """One timed form of the step: a handle, the vector it reads, the basis
+    of x and y, its method bytes and format overhead bytes.  `credited` is
+    False for the one form whose output is not A x in a single basis (x in
+    the original order, y in the permuted order), kept only for comparison."""
+
+    def __init__(self, name, H, xin, basis, nbytes, overhead=0, how=("fixed",), credited=True):
+        self.name, self.H, self.xin, self.basis = name, H, xin, basis
+        self.nbytes, self.overhead, self.how, self.credited = nbytes, overhead, how, credited
+
+    def run(self, y):
+        from paper_0910_4836_gb300 import _lib as L
+        b = L.BASIS_ORIGINAL if self.basis == "original" else L.BASIS_PERMUTED
+        self.H.spmv(self.xin, out=y, basis=b)
+
+    def lane_slots(self):
+        """FP64 lane-slots of one SELL launch: every block issues 32 lanes
+        for each slot of its longest (first) row."""
+        H = self.H
+        if getattr(H, "fmt", None) != "SELL" or H.rlen is None:
+            return None
+        import torch
+        return int(32 * H.rlen[::32].to(torch.int64).sum().item())
+
+
+BASIS_LABEL = {
+    "original": "original basis: x and y in the user's row order",
+    "permuted": "permuted basis (Sect. 2): x and y both in the scheme's row order, y_p = (P A P^T) x_p",
+    "mixed": "NOT one basis: x in the original order, y in the permuted row order (uncredited)",
+}
+
+
 def candidates(M, A, x, only=None):
-    """(name, handle, input vector, algorithmic bytes, setting) of every
-    storage scheme and kernel option on this matrix (the paper's serial
-    comparison of Sect. 3.2, on GB300).  JDS-family inputs are in their
-    permuted basis.  `only`: a name prefix; other schemes are not built."""
+    """Every storage scheme and kernel option on this matrix (the paper's
+    serial comparison, Sect. 4.2, on GB300), each in a form whose output is
+    A x in one basis: CRS in the original basis; the JDS family with the
+    symmetric permutation in the permuted basis (x permuted once, as the
+    paper keeps all vectors of a run in that basis); row-only SELL / NUJDS in
+    the original basis (y scattered through the permutation inside the
+    kernel).  `only`: a name prefix; other schemes are not built."""
+    N = A.n_rows
     crs_b = algorithmic_bytes(A.n_rows, A.n_cols, A.nnz)
     out = []
-    want = lambda name: only is None or name.startswith(only)
+    want = lambda name: only is None or name.startswith(only) or only.startswith(name)
     for l, r in ((4, 4), (8, 2), (16, 2)):
-        out.append((f"CRS vector l{l} r{r}", M, x, crs_b, ("vector", l, r)))
+        out.append(Cand(f"CRS vector l{l} r{r}", M, x, "original", crs_b, how=("vector", l, r)))
     for t in (1024, 2048):
-        out.append((f"CRS tiled {t}", M, x, crs_b, ("tiled", t)))
-    for perm, w, u in (("row_only", 128, 2), ("row_only", 128, 4), ("row_only", 512, 4),
-                       ("row_only", 4096, 4)):
-        name = f"SELL {perm} w={w} u={u}"
+        out.append(Cand(f"CRS tiled {t}", M, x, "original", crs_b, how=("tiled", t)))
+    for w, u in ((128, 4), (64, 4), (256, 4), (128, 2)):
+        name = f"SELL symmetric w={w} u={u}"
         if want(name):
-            G = M.to_jds("SELL", perm, window=w, unroll=u)
-            xs = G.permute(x) if perm == "symmetric" else x
-            gb = 12 * A.nnz + 4 * (G.n_blocks + 1) + 4 * A.n_rows + 8 * A.n_cols + 8 * A.n_rows
-            out.append((name, G, xs, gb, ("fixed",)))
-    for perm, w, u in (("row_only", 64, 2), ("row_only", 64, 4), ("row_only", 128, 4)):
-        name = f"PSELL {perm} w={w} u={u}"
+            G = M.to_jds("SELL", "symmetric", window=w, unroll=u)
+            out.append(Cand(name, G, G.permute(x), "permuted", jds_method_bytes(A, G.n_blocks + 1), 4 * N))
+    for w, u in ((128, 4), (64, 4)):
+        name = f"SELL row_only w={w} u={u} original"
+        if want(name) or want(f"SELL row_only w={w} u={u} mixed"):
+            G = M.to_jds("SELL", "row_only", window=w, unroll=u)
+            mb = jds_method_bytes(A, G.n_blocks + 1)
+            if want(name):
+                out.append(Cand(name, G, x, "original", mb, 8 * N))
+            if w == 128 and want(f"SELL row_only w={w} u={u} mixed"):
+                out.append(Cand(f"SELL row_only w={w} u={u} mixed", G, x, "mixed", mb, 4 * N, credited=False))
+    for w, u in ((64, 2), (128, 4)):
+        name = f"PSELL symmetric w={w} u={u}"
         if want(name):
-            G = M.to_jds("PSELL", perm, window=w, unroll=u)
-            xs = G.permute(x) if perm == "symmetric" else x
-            gb = 12 * A.nnz + 4 * (G.n_blocks + 1) + 4 * A.n_rows + 8 * A.n_cols + 8 * A.n_rows
-            out.append((name, G, xs, gb, ("fixed",)))
-    for perm in ("symmetric", "row_only"):
-        if only is not None and not any(f"{f} {perm}".startswith(only) or only.startswith(f"{f} {perm}")
-                                        for f in ("JDS", "NUJDS", "NBJDS", "JDS_LITERAL", "RBJDS", "SOJDS")):
-            continue
-        J = M.to_jds("JDS", perm)
-        xp = J.permute(x) if perm == "symmetric" else x
-        jb = 12 * A.nnz + 4 * (J.n_diag + 1) + 8 * A.n_cols + 8 * A.n_rows
+            P = M.to_jds("PSELL", "symmetric", window=w, unroll=u)
+            out.append(Cand(name, P, P.permute(x), "permuted", jds_method_bytes(A, P.n_blocks + 1), 4 * N))
+    if only is None or any(f.startswith(only) or only.startswith(f)
+                           for f in ("JDS", "NUJDS", "NBJDS", "JDS_LITERAL", "RBJDS", "SOJDS")):
+        J = M.to_jds("JDS", "symmetric")
+        xp = J.permute(x)
+        jb = jds_method_bytes(A, J.n_diag + 1)
         for fmt, b, u, r in (("JDS", 0, 0, 1), ("NUJDS", 0, 2, 1), ("NUJDS", 0, 4, 1), ("NUJDS", 0, 8, 1),
-                             ("NUJDS", 0, 2, 2), ("NUJDS", 0, 4, 2), ("NUJDS", 0, 2, 4), ("NUJDS", 0, 4, 4),
+                             ("NUJDS", 0, 2, 2), ("NUJDS", 0, 4, 2), ("NUJDS", 0, 2, 4),
                              ("NBJDS", 1024, 0, 1), ("NBJDS", 2048, 0, 1), ("JDS_LITERAL", 0, 0, 1)):
-            name = (f"{fmt} {perm}" + (f" b={b}" if b else "") + (f" u={u}" if u else "")
+            name = (f"{fmt} symmetric" + (f" b={b}" if b else "") + (f" u={u}" if u else "")
                     + (f" r={r}" if r > 1 else ""))
-            out.append((name, J, xp, jb, ("jds", fmt, b, u, r)))
+            out.append(Cand(name, J, xp, "permuted", jb, how=("jds", fmt, b, u, r)))
         for fmt in ("RBJDS", "SOJDS"):
-            if not want(f"{fmt} {perm} b=1024"):
-                continue
-            R = M.to_jds(fmt, perm, block=1024)
-            rb = jb + 4 * (R.n_blocks + 1)
-            out.append((f"{fmt} {perm} b=1024", R, xp, rb, ("fixed",)))
+            if want(f"{fmt} symmetric b=1024"):
+                R = M.to_jds(fmt, "symmetric", block=1024)
+                out.append(Cand(f"{fmt} symmetric b=1024", R, xp, "permuted",
+                                jb + 4 * (R.n_blocks + 1)))
+    if want("NUJDS row_only u=2 original"):
+        Jr = M.to_jds("NUJDS", "row_only", unroll=2)
+        out.append(Cand("NUJDS row_only u=2 original", Jr, x, "original", jds_method_bytes(A, Jr.n_diag + 1),
+                        4 * N))
     return out
 
 
@@ -302,6 +354,47 @@ def configure(H, how):
     elif how[0] == "jds":
         H.set_format(how[1], block=how[2], unroll=how[3])
         H.set_kernel("vector", rows_per_warp=how[4])
+
+
+def fp64_rate(dev, time_launches):
+    """The FP64 FMA issue rate of this GPU (gbsp_fma_chain): every SM full
+    (8 CTAs of 256 threads), 8 independent FMA chains a thread, median of 5
+    launches; again with half the lanes of every warp idle, which takes the
+    same time when an idle lane costs what a busy one does."""
+    import torch
+    from paper_0910_4836_gb300.gather import FmaChain
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    out = {"sms": sms, "threads": sms * 2048, "iters": 1024}
+    for active in (32, 16):
+        f = FmaChain(sms * 2048, active_lanes=active, iters=1024, device=dev)
+        f()
+        t = statistics.median(time_launches(f, 5))
+        out[f"tflops_{active}_lanes"] = round(f.flops / (t * 1e-3) / 1e12, 4)
+        out[f"ms_{active}_lanes"] = round(t, 4)
+        # every warp-wide FMA instruction, idle lanes counted as busy
+        out[f"lane_slot_tflops_{active}_lanes"] = round(16.0 * 1024 * sms * 2048 / (t * 1e-3) / 1e12, 4)
+        del f
+    out["tflops"] = out["tflops_32_lanes"]
+    return out
+
+
+def cold_times(fn, dev, reps=20):
+    """Times of `fn` with L2 flushed before each launch (a 512 MB write,
+    four times the 129 MB L2), CUDA events around the launch only."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 2 ** 20, dtype=torch.float64, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    del flush
+    return out
 
 
 def run_ours(args):
@@ -324,26 +417,32 @@ def run_ours(args):
     x = torch.as_tensor(x_host).to(dev)
     y = torch.empty(A.n_rows, dtype=torch.float64, device=dev)
     peak, peak_kind = peaks()
+    fp64 = fp64_rate(dev, time_launches)
 
-    # every scheme timed (median of 10 launches); the fastest is the step
+    # every form timed (median of 10 launches); the fastest credited one is
+    # the step
     table, best = {}, None
-    for name, H, xin, nbytes, how in candidates(M, A, x, None if args.kernel == "auto" else args.kernel):
-        if args.kernel != "auto" and not name.startswith(args.kernel):
+    for c in candidates(M, A, x, None if args.kernel == "auto" else args.kernel):
+        if args.kernel != "auto" and not c.name.startswith(args.kernel):
             continue
-        configure(H, how)
-        t = statistics.median(time_launches(lambda: H.spmv(xin, out=y), 10))
-        table[name] = {"gflops": round(2.0 * A.nnz / (t * 1e-3) / 1e9, 1),
-                       "gbs": round(nbytes / (t * 1e-3) / 1e9, 1), "ms": round(t, 4),
-                       "frac": round(nbytes / (t * 1e-3) / 1e9 / peak, 3)}
+        configure(c.H, c.how)
+        t = statistics.median(time_launches(lambda: c.run(y), 10))
+        table[c.name] = {"gflops": round(2.0 * A.nnz / (t * 1e-3) / 1e9, 1),
+                         "gbs": round(c.nbytes / (t * 1e-3) / 1e9, 1), "ms": round(t, 4),
+                         "frac": round(c.nbytes / (t * 1e-3) / 1e9 / peak, 3), "basis": c.basis}
+        if not c.credited:
+            table[c.name]["credited"] = False
+            continue
         # a later scheme replaces the choice only when more than 1% faster,
         # so near-ties keep the earlier (listed first) scheme from run to run
         if best is None or t < 0.99 * best[0]:
-            best = (t, name, H, xin, nbytes, how)
-    _, kname, H, xin, alg, how = best
-    configure(H, how)
+            best = (t, c)
+    _, step_c = best
+    kname, H, xin, alg = step_c.name, step_c.H, step_c.xin, step_c.nbytes
+    configure(H, step_c.how)
 
     def step():
-        H.spmv(xin, out=y)
+        step_c.run(y)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -362,25 +461,33 @@ def run_ours(args):
     gbs = alg / (ms * 1e-3) / 1e9
     h = kernel_source_hash(kname)
     traffic = NCU_TRAFFIC.get((args.config, kname, h))
+    cold_ms = statistics.median(cold_times(step, dev))
+    slots = step_c.lane_slots()
 
-    # end to end through the public API: every step is one C-ABI call with
-    # host vectors (gbsp_spmv_host), which copies x in from pinned host
-    # memory, runs the product and copies y back to pinned host memory, in
-    # order on its stream.  Steps go round-robin over four streams, each
-    # with its own device stages and host output: a stream's copy in,
-    # product and copy out run in order, so four of them keep the copies in
-    # both directions and the products overlapping.
+    # end to end through the public API, in the original basis so that the
+    # host gets y = A x in its own row order: every step is one C-ABI call
+    # with host vectors (gbsp_spmv_host), which copies x in from pinned host
+    # memory, runs the product (row-only SELL, y scattered through the
+    # permutation in the kernel) and copies y back to pinned host memory, in
+    # order on its stream.  Steps go round-robin over four streams, each with
+    # its own device stages and host output, so copies in both directions and
+    # the products overlap.
+    from paper_0910_4836_gb300 import _lib as L
+    if step_c.basis == "original":
+        He, e2e_kernel = H, kname
+    else:
+        He, e2e_kernel = M.to_jds("SELL", "row_only", window=128, unroll=4), "SELL row_only w=128 u=4 original"
     nstr = 4
-    xh = xin.detach().cpu().pin_memory()
+    xh = x.detach().cpu().pin_memory()
     yh = [torch.empty(A.n_rows, dtype=torch.float64).pin_memory() for _ in range(nstr)]
-    stages = [H.host_stage() for _ in range(nstr)]
+    stages = [He.host_stage() for _ in range(nstr)]
     streams = [torch.cuda.Stream(dev) for _ in range(nstr)]
     main = torch.cuda.current_stream(dev)
 
     def e2e_steps(n):
         for i in range(n):
             b = i % nstr
-            H.spmv_host(xh, out=yh[b], stage=stages[b], stream=streams[b])
+            He.spmv_host(xh, out=yh[b], stage=stages[b], stream=streams[b], basis=L.BASIS_ORIGINAL)
 
     def fenced(n):
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -399,10 +506,11 @@ def run_ours(args):
     t_start, t_end = fenced(e2e_n)
     torch.cuda.synchronize(dev)
     e2e_ms = t_start.elapsed_time(t_end) / e2e_n
+    del He, stages
 
     result = None
     if rank == 0:
-        basis = "original basis" if kname.startswith("CRS") else "permuted basis (Sect. 2)"
+        rate = fp64["tflops"] * 1e12
         result = {
             "metric": METRIC, "value": round(gflops, 2), "unit": "GFlop/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 5),
@@ -410,25 +518,43 @@ def run_ours(args):
             "data": "synthetic (seeded SplitMix64; stand-in for the paper's Holstein-Hubbard matrix)",
             "hbm_gbs": round(gbs, 1),
             "config": {"workload": WORKLOADS.get(args.config, WORKLOAD), "config_index": args.config, "n_rows": A.n_rows,
-                       "nnz": A.nnz, "kernel": kname, "vectors": basis,
-                       "l2": "inputs larger than L2 (matrix ~1 GB), no flush",
+                       "nnz": A.nnz, "kernel": kname, "vectors": BASIS_LABEL[step_c.basis],
+                       "l2": "inputs larger than L2 (matrix ~1 GB), no flush between timed steps; "
+                             "roofline.cold_ms flushes L2 before each launch",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(gbs / peak, 4), "traffic": traffic,
                          "frac_of_8tbs_spec": round(gbs / 8000.0, 4),
-                         "algorithmic_bytes": alg, "peak_source": f"{peak_kind} hbm_gbs (burst)",
-                         "kernel_source_hash": h},
+                         "algorithmic_bytes": alg,
+                         "algorithmic_bytes_formula": "12 nnz + 4 (pointer entries) + 8 N_c + 8 N",
+                         "format_overhead_bytes": step_c.overhead,
+                         "format_overhead": ("row lengths 4N" + (" + permutation 4N read by the fused basis change"
+                                                                  if step_c.basis == "original" and
+                                                                  not kname.startswith("CRS") else ""))
+                         if not kname.startswith("CRS") else "none",
+                         "peak_source": f"{peak_kind} hbm_gbs (burst)",
+                         "kernel_source_hash": h,
+                         "cold_ms": round(cold_ms, 5),
+                         "cold_frac": round(alg / (cold_ms * 1e-3) / 1e9 / peak, 4),
+                         "fp64_fma_tflops": fp64["tflops"],
+                         "fp64_floor_us": round(2.0 * A.nnz / rate * 1e6, 1),
+                         "fp64_lane_slots": slots,
+                         "fp64_slot_floor_us": None if slots is None else round(2.0 * slots / rate * 1e6, 1),
+                         "hbm_floor_us": round(alg / (peak * 1e9) * 1e6, 1)},
+            "fp64_rate": fp64,
             "e2e": {"value": round(world * flops / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GFlop/s",
                     "h2d_bytes_per_step": 8 * A.n_cols, "d2h_bytes_per_step": 8 * A.n_rows,
-                    "ms_per_step": round(e2e_ms, 4),
+                    "ms_per_step": round(e2e_ms, 4), "kernel": e2e_kernel,
+                    "vectors": BASIS_LABEL["original"],
                     "how": "one gbsp_spmv_host call per step (pinned host x in, product, pinned host y out, "
                            "in order on its stream); steps round-robin over four streams and stage sets"},
             "gpu_launches": args.steps * launches_per_step(kname, H),
             "clocks": clk.summary(),
             "formats": table,
         }
+        fp32_dev = None
         if not args.no_extras:
-            result["fp32"] = fp32_numbers(M, A, x, y, dev, time_launches, table[kname]["ms"])
+            result["fp32"], fp32_dev = fp32_numbers(M, A, x, y, dev, time_launches, table[kname]["ms"])
             torch.cuda.empty_cache()
             result["symmetric"] = symmetric_numbers(M, A, x, dev, time_launches, table[kname]["ms"])
             del table
@@ -444,7 +570,9 @@ def run_ours(args):
             result["hybrid_dia"] = hybrid_numbers(dev, time_launches, peak)
             torch.cuda.empty_cache()
             result["laplace_64x64"] = small_numbers(dev, time_launches)
-        result["cpu_baseline"] = cpu_baseline(A, x_host, args.cpu_seconds)
+        result["cpu_baseline"] = cpu_baseline(A, x_host, args.cpu_seconds, fp32_dev)
+        if "fp32" in result:
+            result["fp32"]["per_config"] = result["cpu_baseline"].pop("fp32_error_vs_oracle")
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -461,8 +589,10 @@ def launches_per_step(kname, H):
 # ------------------------------------------------------------- extras ------
 
 def fp32_numbers(M, A, x, y64, dev, time_launches, ms64):
-    """FP32 values with compensated (Dot2) row sums on the same matrix: speed
-    and the error against the FP64 GPU result, relative to sum |a||x|."""
+    """FP32 values with compensated (Dot2) row sums on the same matrix: the
+    speed of each FP32 kernel against the FP64 step.  Also returns, for the
+    CPU leg, the FP32 products (compensated and plain) of every workload,
+    whose errors against the FP64 oracle that leg states."""
     import torch
     from paper_0910_4836_gb300 import CRSMatrix
     M32 = CRSMatrix(M.row_ptr, M.col, M.val.float(), A.n_cols)
@@ -471,63 +601,76 @@ def fp32_numbers(M, A, x, y64, dev, time_launches, ms64):
     y32 = torch.empty(A.n_rows, dtype=torch.float32, device=dev)
     J32 = M32.to_jds("NUJDS", "symmetric", unroll=4)
     xp32 = J32.permute(x32)
-    G32 = M32.to_jds("SELL", "row_only", window=128, unroll=4)
-    G32w = M32.to_jds("SELL", "row_only", window=1024, unroll=4)
+    G32 = M32.to_jds("SELL", "symmetric", window=128, unroll=4)
+    G32o = M32.to_jds("SELL", "row_only", window=128, unroll=4)
+    xs32 = G32.permute(x32)
     res = {}
-    opts = [("CRS vector l4 r4", M32, x32, lambda: M32.set_kernel("vector", lanes=4, rows_per_warp=4)),
-            ("CRS tiled 1024", M32, x32, lambda: M32.prepare_tiled(1024)),
-            ("NUJDS symmetric u=4", J32, xp32, lambda: None),
-            ("SELL row_only w=128 u=4", G32, x32, lambda: None),
-            ("SELL row_only w=1024 u=4", G32w, x32, lambda: None)]
+    opts = [("CRS vector l4 r4", M32, x32, lambda: M32.set_kernel("vector", lanes=4, rows_per_warp=4), 0),
+            ("CRS tiled 1024", M32, x32, lambda: M32.prepare_tiled(1024), 0),
+            ("NUJDS symmetric u=4", J32, xp32, lambda: None, 0),
+            ("SELL symmetric w=128 u=4", G32, xs32, lambda: None, 0),
+            ("SELL row_only w=128 u=4 original", G32o, x32, lambda: None, 1)]
     best = None
-    for name, H, xin, conf in opts:
+    for name, H, xin, conf, basis in opts:
         conf()
-        t = statistics.median(time_launches(lambda: H.spmv(xin, out=y32), 10))
+        t = statistics.median(time_launches(lambda: H.spmv(xin, out=y32, basis=basis), 10))
         res[name] = {"gflops": round(2.0 * A.nnz / (t * 1e-3) / 1e9, 1), "ms": round(t, 4),
                      "gbs": round((8 * A.nnz + 4 * (A.n_rows + 1) + 4 * (A.n_rows + A.n_cols))
                                   / (t * 1e-3) / 1e9, 1)}
         if best is None or t < best[0]:
             best = (t, name)
-    # accuracy against the FP64 product on the GPU (itself within 1e-14 of the oracle)
-    M.set_kernel("vector", lanes=4, rows_per_warp=4)
-    ref = M.spmv(x)
-    Mabs = CRSMatrix(M.row_ptr, M.col, M.val.abs(), A.n_cols)
-    sabs = Mabs.spmv(x.abs())
-    M32.set_kernel("vector", lanes=4, rows_per_warp=4, compensated=True)
-    yc = M32.spmv(x32).double()
-    M32.set_kernel("vector", lanes=4, rows_per_warp=4, compensated=False)
-    yp = M32.spmv(x32).double()
-    den = sabs.clamp_min(1e-300)
-    return {"best": best[1], "speedup_vs_fp64": round(ms64 / best[0], 3), "kernels": res,
-            "max_err_over_sum_abs_compensated": float(((yc - ref).abs() / den).max()),
-            "max_err_over_sum_abs_plain": float(((yp - ref).abs() / den).max()),
-            "per_config": fp32_errors(dev),
-            "note": "error of FP32 data and FP32 vector against the FP64 product of the FP64 data"}
+    del M32, J32, G32, G32o
+    torch.cuda.empty_cache()
+    out = {"best": best[1], "speedup_vs_fp64": round(ms64 / best[0], 3), "kernels": res,
+           "note": "error of the FP32 product (FP32 values and vector) against the FP64 oracle, max over rows "
+                   "of |y32 - y| / sum|a||x|; 'dot2_bound_ok' checks the compensated sums against the Dot2 "
+                   "bound relative to the exact product of the FP32-rounded data"}
+    return out, fp32_products(dev)
 
 
-def fp32_errors(dev):
-    """Max |y32 - y64| / sum|a||x| per workload (FP32 values and vector,
-    compensated and plain row sums, against the FP64 GPU product of the
-    FP64 data): the Laplacian, the HH-like matrix, the Zipf rows and the
-    27-point stencil."""
+def fp32_products(dev):
+    """FP32 products of each workload on the GPU (FP32 values and vector; CRS
+    with compensated and with plain row sums), copied to the host for the
+    oracle comparison: the Laplacian, the HH-like matrix, the Zipf rows and
+    the 27-point stencil."""
     import torch
     from paper_0910_4836_gb300 import CRSMatrix, synth as S
     out = {}
     for i, name in ((0, "laplace_64x64"), (1, "hh_like_6M"), (2, "zipf_rows_4M"), (4, "stencil27_100^3")):
         A = S.config(i)
-        M = CRSMatrix.from_host(A, device=dev)
-        x = torch.as_tensor(S.vector(A.n_cols, i)).to(dev)
-        ref = M.spmv(x)
-        sabs = CRSMatrix(M.row_ptr, M.col, M.val.abs(), A.n_cols).spmv(x.abs()).clamp_min(1e-300)
-        M32 = CRSMatrix(M.row_ptr, M.col, M.val.float(), A.n_cols)
-        row = {}
+        xh = S.vector(A.n_cols, i)
+        M32 = CRSMatrix.from_host(A, device=dev, dtype=torch.float32)
+        x32 = torch.as_tensor(xh).to(dev).float()
+        ys = {}
         for comp in (True, False):
             M32.set_kernel("vector", lanes=4, rows_per_warp=4, compensated=comp)
-            y = M32.spmv(x.float()).double()
-            row["compensated" if comp else "plain"] = float(((y - ref).abs() / sabs).max())
-        out[name] = row
-        del M, M32, ref, sabs
+            ys["compensated" if comp else "plain"] = M32.spmv(x32).cpu().numpy()
+        out[name] = (A, xh, ys)
+        del M32
         torch.cuda.empty_cache()
+    return out
+
+
+def fp32_error_vs_oracle(products):
+    """For each workload: max over rows of |y32 - y_oracle| / sum|a||x|,
+    y_oracle the accurate FP64 oracle product of the FP64 data; and whether
+    the compensated sums meet the Dot2 bound against the exact product of
+    the FP32-rounded data."""
+    import oracle as O
+    from paper_0910_4836_gb300 import synth as S
+    out = {}
+    for name, (A, xh, ys) in products.items():
+        ref, s = O.crs_spmv_exact(A, xh)
+        den = np.maximum(s, 1e-300)
+        row = {k: float(np.max(np.abs(v.astype(np.float64) - ref) / den)) for k, v in ys.items()}
+        A32 = S.CRS(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val.astype(np.float32).astype(np.float64), A.name)
+        r32, s32 = O.crs_spmv_exact(A32, xh.astype(np.float32).astype(np.float64))
+        n = np.maximum(A.row_lengths(), 1).astype(np.float64) + 6.0
+        u = 2.0 ** -24
+        gam = n * u / (1 - n * u)
+        bound = 2 * u * np.abs(r32) + (gam * gam + n * u * u) * s32
+        row["dot2_bound_ok"] = bool(np.all(np.abs(ys["compensated"].astype(np.float64) - r32) <= bound))
+        out[name] = row
     return out
 
 
@@ -551,7 +694,8 @@ def spmm_adjoint_numbers(M, A, x, dev, time_launches, peak):
         X = torch.rand(Nc, k, dtype=torch.float64, device=dev)
         Y = torch.empty(N, k, dtype=torch.float64, device=dev)
         nb = 12 * nnz + 4 * (N + 1) + 8 * k * (Nc + N)
-        for name, fn in (("CRS", lambda: M.spmm(X, out=Y)), ("SELL row_only w=128", lambda: G.spmm(X, out=Y))):
+        for name, fn in (("CRS", lambda: M.spmm(X, out=Y)),
+                         ("SELL row_only w=128 original", lambda: G.spmm(X, out=Y, basis=1))):
             t = statistics.median(time_launches(fn, 10))
             out[f"spmm k={k} {name}"] = row(t, nb, 2.0 * nnz * k)
         del X, Y
@@ -564,8 +708,8 @@ def spmm_adjoint_numbers(M, A, x, dev, time_launches, peak):
     t = statistics.median(time_launches(lambda: M.spmv(g, out=z, transpose=True), 10))
     out["adjoint A^T g, transposed CRS"] = row(t, ab, 2.0 * nnz)
     JT = T.to_jds("NUJDS", "row_only", unroll=2)
-    t = statistics.median(time_launches(lambda: JT.spmv(g, out=z), 10))
-    out["adjoint A^T g, NUJDS of A^T"] = row(t, 12 * nnz + 4 * (JT.n_diag + 1) + 16 * Nc, 2.0 * nnz)
+    t = statistics.median(time_launches(lambda: JT.spmv(g, out=z, basis=1), 10))
+    out["adjoint A^T g, NUJDS of A^T, original basis"] = row(t, 12 * nnz + 4 * (JT.n_diag + 1) + 16 * Nc, 2.0 * nnz)
     del JT
     d = torch.empty(nnz, dtype=torch.float64, device=dev)
     db = 8 * nnz + 4 * nnz + 4 * (N + 1) + 8 * N + 8 * Nc
@@ -594,7 +738,7 @@ def symmetric_numbers(M, A, x, dev, time_launches, ms_full):
 
 def hybrid_numbers(dev, time_launches, peak):
     """The DIA + remainder hybrid on the second HH stand-in (60% of the
-    entries on twelve dense outer diagonals, as Sect. 3.2 describes the real
+    entries on twelve dense outer diagonals, as Sect. 4.2 describes the real
     matrix), against SELL and CRS on the same matrix."""
     import torch
     from paper_0910_4836_gb300 import CRSMatrix, HybridMatrix, synth as S
@@ -615,7 +759,7 @@ def hybrid_numbers(dev, time_launches, peak):
     M.set_kernel("vector", lanes=4, rows_per_warp=4)
     rec("CRS vector l4 r4", lambda: M.spmv(x, out=y), crs_b)
     G = M.to_jds("SELL", "row_only", window=128, unroll=4)
-    rec("SELL row_only w=128 u=4", lambda: G.spmv(x, out=y),
+    rec("SELL row_only w=128 u=4 original", lambda: G.spmv(x, out=y, basis=1),
         12 * A.nnz + 4 * (G.n_blocks + 1) + 20 * A.n_rows)
     del G
     for rem in ("SELL", "CRS"):
@@ -638,24 +782,46 @@ def small_numbers(dev, time_launches):
     M = CRSMatrix.from_host(A, device=dev)
     x = torch.as_tensor(S.vector(A.n_cols, 0)).to(dev)
     out = {"n_rows": A.n_rows, "nnz": A.nnz}
-    for name, H, xin in (("CRS vector", M, x), ("SELL row_only w=128 u=4", M.to_jds("SELL", "row_only", window=128, unroll=4), x),
-                         ("NUJDS row_only u=2", M.to_jds("NUJDS", "row_only", unroll=2), x)):
+    for name, H, xin in (("CRS vector", M, x),
+                         ("SELL row_only w=128 u=4 original", M.to_jds("SELL", "row_only", window=128, unroll=4), x),
+                         ("NUJDS row_only u=2 original", M.to_jds("NUJDS", "row_only", unroll=2), x)):
         if name.startswith("CRS"):
             H.autotune()
         y = torch.empty(A.n_rows, dtype=torch.float64, device=dev)
-        eager = statistics.median(time_launches(lambda: H.spmv(xin, out=y), 200))
+        b = 0 if name.startswith("CRS") else 1
+        eager = statistics.median(time_launches(lambda: H.spmv(xin, out=y, basis=b), 200))
         s = torch.cuda.Stream(dev)
         s.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.stream(s):
-            H.spmv(xin, out=y)
+            H.spmv(xin, out=y, basis=b)
         torch.cuda.current_stream(dev).wait_stream(s)
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
             for _ in range(100):
-                H.spmv(xin, out=y)
+                H.spmv(xin, out=y, basis=b)
         replay = statistics.median(time_launches(g.replay, 20)) / 100
         out[name] = {"eager_us": round(eager * 1e3, 2), "graph_us": round(replay * 1e3, 2)}
     return out
+
+
+def zipf_candidates(M, A, x, y):
+    """(name, launch, method bytes) of the Zipf-rows forms: CRS vector and
+    tiled, and NUJDS with the deep-diagonal split in the permuted basis
+    (columns are uniform random, so the symmetric renumbering costs no
+    locality; x is permuted once)."""
+    crs_b = algorithmic_bytes(A.n_rows, A.n_cols, A.nnz)
+    runs = []
+    M.set_kernel("vector", lanes=4, rows_per_warp=4)
+    runs.append(("CRS vector l4 r4", lambda: M.spmv(x, out=y), crs_b))
+    from paper_0910_4836_gb300 import CRSMatrix
+    M2 = CRSMatrix(M.row_ptr, M.col, M.val, A.n_cols)
+    M2.prepare_tiled(1024)
+    runs.append(("CRS tiled 1024", lambda: M2.spmv(x, out=y), crs_b))
+    J = M.to_jds("NUJDS", "symmetric", unroll=2)
+    xp = J.permute(x)
+    J.split(16, 64)
+    runs.append(("NUJDS symmetric u=2 split 16/64", lambda: J.spmv(xp, out=y), jds_method_bytes(A, J.n_diag + 1)))
+    return runs
 
 
 def zipf_numbers(dev, time_launches, peak):
@@ -668,20 +834,9 @@ def zipf_numbers(dev, time_launches, peak):
     M = CRSMatrix.from_host(A, device=dev)
     x = torch.as_tensor(S.vector(A.n_cols, 2)).to(dev)
     y = torch.empty(A.n_rows, dtype=torch.float64, device=dev)
-    crs_b = algorithmic_bytes(A.n_rows, A.n_cols, A.nnz)
     out = {"n_rows": A.n_rows, "nnz": A.nnz, "max_row": int(A.row_lengths().max())}
-    runs = []
-    M.set_kernel("vector", lanes=4, rows_per_warp=4)
-    runs.append(("CRS vector l4 r4", lambda: M.spmv(x, out=y), crs_b))
-    M2 = CRSMatrix(M.row_ptr, M.col, M.val, A.n_cols)
-    M2.prepare_tiled(1024)
-    runs.append(("CRS tiled 1024", lambda: M2.spmv(x, out=y), crs_b))
-    J = M.to_jds("NUJDS", "row_only", unroll=2)
-    jb = 12 * A.nnz + 4 * (J.n_diag + 1) + 16 * A.n_rows
-    J.split(16, 64)
-    runs.append(("NUJDS row_only u=2 split 16/64", lambda: J.spmv(x, out=y), jb))
     table, best = {}, None
-    for name, fn, nbytes in runs:
+    for name, fn, nbytes in zipf_candidates(M, A, x, y):
         t = statistics.median(time_launches(fn, 10))
         table[name] = {"gflops": round(2.0 * A.nnz / (t * 1e-3) / 1e9, 1), "ms": round(t, 4),
                        "gbs": round(nbytes / (t * 1e-3) / 1e9, 1),
@@ -807,11 +962,12 @@ def host_copy_gbs(nbytes=1 << 30, reps=5):
     return round(2 * nbytes / best / 1e9, 1)
 
 
-def cpu_baseline(A, x, seconds):
+def cpu_baseline(A, x, seconds, fp32_products=None):
     """The oracle on the host cores: its OpenMP static-schedule CRS loop (the
     paper's best parallel setting) on the full matrix, repeated for about
     `seconds`; the serial literal CRS and JDS loops on one core, once each;
-    and the host copy bandwidth."""
+    the host copy bandwidth; and, given the GPU's FP32 products, their error
+    against the oracle's accurate FP64 product."""
     import oracle as O
     y = np.zeros(A.n_rows)
     O.crs_spmv_omp(A, x, y)  # first touch
@@ -840,6 +996,8 @@ def cpu_baseline(A, x, seconds):
     out["serial_jds_gflops"] = round(2.0 * A.nnz / (time.perf_counter() - t0) / 1e9, 3)
     out["serial_cores"] = 1
     out["host_copy_gbs"] = host_copy_gbs()
+    if fp32_products is not None:
+        out["fp32_error_vs_oracle"] = fp32_error_vs_oracle(fp32_products)
     return out
 
 
@@ -871,7 +1029,7 @@ def run_reference(args):
 
 
 def run_micro(args):
-    """The basic sparse vector operations of Sect. 3.1 on the device: the
+    """The basic sparse vector operations of Sect. 4.1 on the device: the
     table of ADD / SCP over packed dense (PD), constant stride (CS) and
     indirect (IS: ind(i) = k i; IR: random strides of mean k, as the paper
     draws them) access at the paper's strides 1, 8 and 530; the IS / IR
@@ -938,14 +1096,14 @@ def run_micro(args):
         for var in (0, 1, 16, 256, 4096, 65536):
             ind = S.gaussian_indices(n, float(mean), float(var), length, 300 + mean)
             plane[f"mean={mean} var={var}"] = point("SCP", "IND", n, ind=ind)
-    return {"metric": "basic gather operations (Sect. 3.1): G element updates/s", "unit": "G updates/s",
+    return {"metric": "basic gather operations (Sect. 4.1): G element updates/s", "unit": "G updates/s",
             "dtype": "f64", "data": "synthetic (torch.rand values; SplitMix64 index arrays)",
             "l2": "flushed before every launch", "table": table, "stride_sweep": sweep,
             "gaussian_plane": plane}
 
 
 def run_analysis(args):
-    """Sect. 4's analysis of the storage schemes on the bench workload: the
+    """Sect. 4.2's analysis of the storage schemes on the bench workload: the
     stride distribution of the x accesses in storage order (Fig. 4a: CRS,
     JDS, RBJDS with block 1 and 1024, SOJDS 1024, plus SELL-32-sigma), the
     sectors per warp-wide gather of the GPU kernels, and the block-size
@@ -973,10 +1131,16 @@ def run_analysis(args):
         h = warp_sectors(H, lanes)
         out["warp_sectors"][name] = {"mean": round(mean_sectors(h), 3), "hist": h.tolist()}
 
+    def basis_of(H):
+        # row-only handles: the original basis (y scattered in the kernel);
+        # symmetric ones: the permuted basis with x permuted; CRS: original
+        return 1 if getattr(H, "symmetric", True) is False else 0
+
     def timed(name, H, xin, configure_fn=None):
         if configure_fn:
             configure_fn()
-        t = statistics.median(time_launches(lambda: H.spmv(xin, out=y), 10))
+        b = basis_of(H)
+        t = statistics.median(time_launches(lambda: H.spmv(xin, out=y, basis=b), 10))
         out["sweep"][name] = {"us": round(t * 1e3, 1), "gflops": round(2.0 * A.nnz / (t * 1e-3) / 1e9, 1)}
 
     # throughput against the number of CTAs in use (the GPU counterpart of
@@ -986,9 +1150,10 @@ def run_analysis(args):
 
     def scaling(name, H, xin, limits):
         row = {}
+        b = basis_of(H)
         for lim in limits:
             H.set_grid_limit(lim)
-            t = statistics.median(time_launches(lambda: H.spmv(xin, out=y), 10))
+            t = statistics.median(time_launches(lambda: H.spmv(xin, out=y, basis=b), 10))
             row[str(lim or "all")] = {"us": round(t * 1e3, 1), "gbs": round(alg / (t * 1e-3) / 1e9, 1)}
         H.set_grid_limit(0)
         out["cta_scaling"][name] = row
@@ -1046,40 +1211,43 @@ def run_analysis(args):
 
 
 def run_ncu_case(args):
-    """A few launches of one kernel on a 2e6-row HH-like matrix (~350 MB,
-    above the 129 MB L2) for an ncu capture; prints nothing to time.  With
-    --config 2: the Zipf-rows matrix (345 MB) and its NUJDS walk split at
-    depth 16 in chunks of 64."""
+    """A few launches of one kernel for an ncu capture; prints nothing to
+    time.  Config 1: a 2e6-row HH-like matrix (~350 MB, above the 129 MB
+    L2), or with --ncu-full the full 6e6-row workload (for one-pass
+    counters only).  Config 2: the Zipf-rows matrix (345 MB) and the
+    kernel named by --kernel among its candidates."""
     import torch
     from paper_0910_4836_gb300 import CRSMatrix, build, synth as S
     build()
+    only = None if args.kernel == "auto" else args.kernel
     if args.config == 2:
         A = S.config(2)
         M = CRSMatrix.from_host(A)
         x = torch.as_tensor(S.vector(A.n_cols, 2)).cuda()
         y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
-        J = M.to_jds("NUJDS", "row_only", unroll=2)
-        J.split(16, 64)
-        for _ in range(3):
-            J.spmv(x, out=y)
-        torch.cuda.synchronize()
-        print("ran NUJDS row_only u=2 split 16/64 on the Zipf rows")
+        for name, fn, _ in zipf_candidates(M, A, x, y):
+            if only is not None and name != only:
+                continue
+            torch.cuda.synchronize()
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            print("ran", name, "on the Zipf rows")
         return
-    A = S.hh_like(2_000_000, 1)
+    A = S.config(1) if args.ncu_full else S.hh_like(2_000_000, 1)
     M = CRSMatrix.from_host(A)
     x = torch.as_tensor(S.vector(A.n_cols, 1)).cuda()
     y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
-    only = None if args.kernel == "auto" else args.kernel
-    for name, H, xin, _, how in candidates(M, A, x, only):
-        if only is not None and name != only:
+    for c in candidates(M, A, x, only):
+        if only is not None and c.name != only:
             continue
-        configure(H, how)
+        configure(c.H, c.how)
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
         for _ in range(3):
-            H.spmv(xin, out=y)
+            c.run(y)
         torch.cuda.synchronize()
-        print("ran", name)
+        print("ran", c.name)
 
 
 def main():

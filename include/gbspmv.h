@@ -9,6 +9,12 @@
  * multiple right-hand sides, the adjoint A^T*g, the per-entry value gradient,
  * a batched persistent launch and an FP32 path with compensated sums.
  *
+ * Section numbers follow the paper's own order: 1 Introduction, 2 Common
+ * storage schemes, 3 Test bed, 4 Limitations of serial performance (4.1
+ * Basic sparse vector operations, 4.2 Resulting performance for SpMVM),
+ * 5 Shared-memory parallel SpMVM (5.1 Intra-socket, 5.2 Inter-socket,
+ * 5.3 HLRB-II scalability), 6 Conclusion and outlook.
+ *
  * Conventions used by every entry point
  *   - Indices are 0-based int32; sizes and counts are int64.
  *   - Pointers named d_* are DEVICE pointers on the current CUDA device;
@@ -269,7 +275,7 @@ gbsp_status gbsp_jds_build(gbsp_handle crs, const gbsp_jds_opts *opts,
 /* Cap the grid (number of CTAs) of the handle's SELL, JDS / NUJDS walk and
  * CRS VECTOR product kernels at max_ctas (0 removes the cap).  A measurement
  * knob, the GPU counterpart of running the paper's OpenMP kernels on fewer
- * threads (Sect. 5, intra-socket scaling): the SELL kernel places at most
+ * threads (Sect. 5.1, "Intra-socket performance"): the SELL kernel places at most
  * two 1024-thread CTAs per SM, the others up to eight 256-thread CTAs.
  * Host-side only.  Errors: GBSP_ERR_ARG for a negative cap. */
 gbsp_status gbsp_set_grid_limit(gbsp_handle h, int32_t max_ctas);
@@ -517,9 +523,15 @@ gbsp_status gbsp_batch_destroy(gbsp_batch b);
  * be at most about 4.1e8; larger sizes return GBSP_ERR_ARG with a message.
  * The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress), so make the first call on each device before any
- * stream capture.  All calls share the one array and rewrite it fully:
- * calls that can overlap on the GPU (different streams without ordering)
- * race and give wrong results; calls ordered on one stream are safe. */
+ * stream capture.  The address is looked up again when the device's current
+ * context changes (after cudaDeviceReset, for example), so that call too
+ * should come before any capture.  All calls share the one array and
+ * rewrite it fully: calls that can overlap on the GPU (different streams
+ * without ordering) race and give wrong results; calls ordered on one stream
+ * are safe.  The TILED kernel's bounded waits have no status word here: if
+ * one gives up (a stalled copy; none was ever observed), y is left partly
+ * written and the call still returned GBSP_OK.  Callers that need that
+ * reported use a handle with gbsp_set_status_word. */
 gbsp_status gbsp_crs_spmv_noalloc(int64_t n_rows, int64_t n_cols, int64_t nnz,
                                   const int32_t *d_row_ptr, const int32_t *d_col,
                                   const void *d_val, gbsp_dtype dtype, int32_t accumulate,
@@ -527,7 +539,7 @@ gbsp_status gbsp_crs_spmv_noalloc(int64_t n_rows, int64_t n_cols, int64_t nnz,
 
 /* ------------------------------------------------ basic gather operations -- */
 
-/* The basic sparse vector operations of Sect. 3.1 (its table of ADD and SCP
+/* The basic sparse vector operations of Sect. 4.1 ("Basic sparse vector operations"; its table of ADD and SCP
  * kernels), which isolate the cost of the indirect x access of the SpMVM
  * inner loop:
  *     ADD:  s = sum_{i<n} B(idx(i))        SCP:  s = sum_{i<n} A(i) * B(idx(i))
@@ -537,12 +549,12 @@ gbsp_status gbsp_crs_spmv_noalloc(int64_t n_rows, int64_t n_cols, int64_t nnz,
 typedef enum { GBSP_GATHER_ADD = 0, GBSP_GATHER_SCP = 1 } gbsp_gather_op;
 typedef enum { GBSP_ACCESS_PD = 0, GBSP_ACCESS_CS = 1, GBSP_ACCESS_IND = 2 } gbsp_access;
 
-/* Sect. 3.1, the basic sparse vector operations.
+/* Sect. 4.1, the basic sparse vector operations.
  * Number of FP64 partial sums gbsp_gather_sum needs for n elements on the
  * current device (one per CTA of its grid). */
 gbsp_status gbsp_gather_partials(int64_t n, int32_t *n_partials);
 
-/* Sect. 3.1, the basic sparse vector operations.
+/* Sect. 4.1, the basic sparse vector operations.
  * *d_out = the sum above, FP64.  d_a [n] (SCP only), d_b [len_b], d_ind [n]
  * (IND only) int32, all device memory borrowed for the call; d_partials is
  * caller scratch of n_partials doubles (>= gbsp_gather_partials(n)).  Each
@@ -559,9 +571,25 @@ gbsp_status gbsp_gather_sum(int32_t op, int32_t access, int64_t n, int64_t strid
                             const int32_t *d_ind, double *d_partials, int32_t n_partials,
                             double *d_out, int32_t *d_status, void *stream);
 
+/* The FP64 issue rate that bounds every kernel here besides HBM.  The paper
+ * sets SpMVM against both the memory bandwidth and the peak Flop rate of
+ * each machine (Sect. 4, "Limitations of serial performance"); GB300's FP64
+ * rate is low enough to be a roofline of its own, so it is measured.  Each
+ * of n_threads threads (256 per CTA) runs 8 independent chains
+ * x_j <- fma(x_j, a, b), x_j starting at in[0] + j, for `iters` steps, with
+ * a = d_in[1] and b = d_in[2] (device, 3 doubles); d_out[t] (device,
+ * n_threads doubles) = the sum of thread t's chains, in chain order.  Lanes
+ * >= active_lanes (0..32) of each warp skip the chains and write 0; their
+ * warp's FMAs still issue, which is what the count of idle lanes costs.
+ * Flops of a launch: 16 * iters * (active lanes in all warps).  One launch
+ * on `stream`, asynchronous.  Errors: GBSP_ERR_ARG for negative sizes,
+ * active_lanes > 32 or NULL pointers. */
+gbsp_status gbsp_fma_chain(int64_t n_threads, int32_t active_lanes, int32_t iters, const double *d_in,
+                           double *d_out, void *stream);
+
 /* ------------------------------------- hybrid storage: DIA + remainder -- */
 
-/* Sect. 3.2 observes that most entries of the Holstein-Hubbard matrix sit
+/* Sect. 4.2 ("Resulting performance for SpMVM") observes that most entries of the Holstein-Hubbard matrix sit
  * in a few dense outer secondary diagonals, any of which could be stored
  * densely, and leaves such a hybrid unbuilt.  Here the selected diagonals
  * go to DIA storage (one value per row, zeros where the diagonal has no
@@ -607,7 +635,7 @@ gbsp_status gbsp_dia_build(gbsp_handle crs, const gbsp_dia_sizes *sizes, void *d
 
 /* --------------------------------------------- symmetric SpMVM (one triangle) -- */
 
-/* The Hamiltonian of Sect. 3.2 is symmetric, which the paper notes would
+/* The Hamiltonian of Sect. 4.2 ("Resulting performance for SpMVM") is symmetric, which the paper notes would
  * allow a further saving of data transfer and does not pursue.  These calls
  * store only the upper triangle U (col >= row) of a square CRS matrix and
  * apply it as A = U + U^T - diag(U), reading half of the off-diagonal
@@ -628,7 +656,7 @@ gbsp_status gbsp_upper_plan(gbsp_handle crs, int32_t *d_row_ptr_u, void *d_ws, i
 gbsp_status gbsp_upper_build(gbsp_handle crs, const int32_t *d_row_ptr_u, int32_t *d_col_u, void *d_val_u,
                              int64_t nnz_upper, void *stream, gbsp_handle *out);
 
-/* Sect. 3.2: the Hamiltonian is symmetric (the paper stores it in full).
+/* Sect. 4.2: the Hamiltonian is symmetric (the paper stores it in full).
  * y = (S + S^T - diag S) x for the stored entries S of handle `S` -- A x
  * when S holds the upper triangle of a symmetric A.  S: a CRS handle
  * (thread per row) or a SELL handle with the row-only permutation (warp per
@@ -644,7 +672,7 @@ gbsp_status gbsp_spmv_symmetric(gbsp_handle S, const void *d_x, void *d_y, int32
 
 /* -------------------------------------------------- access-pattern analysis -- */
 
-/* Stride distribution of the x accesses (Sect. 4, Fig. 4a).  For a
+/* Stride distribution of the x accesses (Sect. 4.2, "Resulting performance for SpMVM", Fig. 4a).  For a
  * column-index array read in storage order -- the order in which the
  * paper's serial CRS, JDS, RBJDS and SOJDS loops read x -- counts every jump
  * s = col[i+1] - col[i] by size: bin 0 is s = 0, bin b >= 1 holds
@@ -674,7 +702,7 @@ gbsp_status gbsp_warp_sectors(gbsp_handle A, int32_t lanes, int32_t elem_bytes, 
 /* ------------------------------------------------------------ autotuner -- */
 
 /* Chooses among the Sect. 2 kernels and block sizes, the GPU counterpart
- * of the paper's block-size sweeps (Sect. 4).
+ * of the paper's block-size sweeps (Sect. 4.2).
  * Time the candidate kernels for `A` with k right-hand sides on the device
  * (CUDA events on `stream`, a few repetitions each, X and Y are scratch
  * vectors of the right sizes) and keep the fastest option set on the handle.

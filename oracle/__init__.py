@@ -13,7 +13,7 @@ rational sums, identity / diagonal / integer inputs, Laplacian closed forms,
 the JDS special cases the paper states (NUJDS with u = N_j is CRS in the
 permuted basis; RBJDS with block 1 is row-by-row access; JDS is NBJDS with
 block = N), a hand-worked JDS example, the adjoint identity and finite
-differences; the basic gather sums of Sect. 3.1 against closed forms
+differences; the basic gather sums of Sect. 4.1 against closed forms
 (dense and constant-stride sums of integers), exact rational sums and
 math.fsum, with the IR index law checked against the paper's per-position
 draw.  SOJDS: parity unpinned (the paper fixes no sorting rule), only
@@ -119,7 +119,7 @@ def crs_spmv_f32(A, x):
 
 
 def crs_spmv_omp(A, x, out=None):
-    """Sect. 4: CRS with an OpenMP static schedule (the CPU baseline)."""
+    """Sect. 5.2: CRS with an OpenMP static schedule (the CPU baseline)."""
     out = np.zeros(A.n_rows) if out is None else out
     lib().orc_crs_spmv_omp(A.n_rows, _i32(A.row_ptr), _i32(A.col), _f64(A.val), _f64(x), out, 0)
     return out
@@ -327,7 +327,7 @@ def power_loss_grad(A, x, m):
 
 
 # ---------------------------------------------------------------------------
-# Basic sparse vector operations (Sect. 3.1): ADD / SCP over PD, CS, IS / IR
+# Basic sparse vector operations (Sect. 4.1): ADD / SCP over PD, CS, IS / IR
 # ---------------------------------------------------------------------------
 
 GATHER_OPS = {"ADD": 0, "SCP": 1}
@@ -370,7 +370,7 @@ def _gather_inputs(op, access, n, b, a, k, ind):
 
 
 # ---------------------------------------------------------------------------
-# Stride distribution (Sect. 4, Fig. 4a) and sectors per warp-wide gather
+# Stride distribution (Sect. 4.2, Fig. 4a) and sectors per warp-wide gather
 # ---------------------------------------------------------------------------
 
 def stride_hist(col):

@@ -66,7 +66,7 @@ void orc_crs_spmv_f32(int64_t n_rows, const int32_t *row_ptr, const int32_t *col
     }
 }
 
-/* Sect. 4: the paper's best shared-memory setting is the CRS loop with an
+/* Sect. 5.2: the paper's best shared-memory setting is the CRS loop with an
  * OpenMP static schedule over rows (first-touch placed arrays).  Same
  * per-row arithmetic as orc_crs_spmv, so the results are bit-identical. */
 void orc_crs_spmv_omp(int64_t n_rows, const int32_t *row_ptr, const int32_t *col_idx,
@@ -502,7 +502,7 @@ void orc_sell_spmv(int64_t n_rows, const int32_t *rlen, const int32_t *blk_ptr,
 }
 
 /* ------------------------------------------------------------------------
- * Basic sparse vector operations (Sect. 3.1, the table of ADD and SCP
+ * Basic sparse vector operations (Sect. 4.1, the table of ADD and SCP
  * kernels): one running sum over i < n of
  *     ADD:  s = s + B(idx(i))          SCP:  s = s + A(i) * B(idx(i))
  * with idx(i) = i (PD, packed dense), k*i (CS, constant stride computed in
@@ -545,7 +545,7 @@ void orc_gather_sum_exact(int op, int access, int64_t n, int64_t k, const double
 }
 
 /* ------------------------------------------------------------------------
- * Stride distribution of the invec accesses (Sect. 4, Fig. 4a): walking a
+ * Stride distribution of the invec accesses (Sect. 4.2, Fig. 4a): walking a
  * column-index array in storage order -- the order in which the paper's
  * serial CRS, JDS, RBJDS and SOJDS loops read invec -- every jump
  * s = col[i+1] - col[i] is counted once.  Bins by size: bin 0 holds s = 0,
@@ -752,7 +752,7 @@ void orc_psell_spmv(int64_t n_rows, const int32_t *rlen, const int32_t *blk_ptr,
 }
 
 /* ------------------------------------------------------------------------
- * Symmetric SpMVM from the upper triangle (Sect. 3.2 names the option of
+ * Symmetric SpMVM from the upper triangle (Sect. 4.2 names the option of
  * using the symmetry of the Hamiltonian to save data transfer and does not
  * pursue it).  U holds the entries with col >= row of a symmetric A, so
  * A = U + U^T - diag(U):
@@ -797,7 +797,7 @@ void orc_sym_spmv(int64_t n_rows, const int32_t *row_ptr_u, const int32_t *col_u
 }
 
 /* ------------------------------------------------------------------------
- * Hybrid storage (Sect. 3.2: most entries of the Hamiltonian sit in a few
+ * Hybrid storage (Sect. 4.2: most entries of the Hamiltonian sit in a few
  * dense outer secondary diagonals, any of which could be stored densely):
  * selected diagonals in DIA form, the rest in CRS.
  *

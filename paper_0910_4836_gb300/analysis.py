@@ -1,6 +1,6 @@
 """Access-pattern analysis of the x gather (argument marshalling over
 ``gbsp_stride_hist`` and ``gbsp_warp_sectors``): the stride distribution of
-Sect. 4 (Fig. 4a) and the sectors touched per warp-wide gather."""
+Sect. 4.2 (Fig. 4a) and the sectors touched per warp-wide gather."""
 from __future__ import annotations
 
 import numpy as np

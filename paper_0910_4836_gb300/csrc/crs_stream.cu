@@ -25,6 +25,7 @@
 //        rows longer than kShort are summed by whole warps; a last row too
 //        long for the stage is summed by all consumers from global memory.
 // Every row is summed by a fixed thread in a fixed order: deterministic.
+#include <atomic>
 #include <algorithm>
 
 #include "accum.cuh"
@@ -305,6 +306,8 @@ crs_stream_kernel(int64_t n_tiles, const int4 *__restrict__ tile_meta, int64_t n
 
 // ------------------------------------------------------------------ host --
 
+constexpr int kStreamMaxDevices = 64;
+
 static int64_t n_tiles_for(const Mat &A, int32_t tile) { return ceil_div(A.n_rows + A.nnz, tile); }
 
 int64_t crs_tile_table_bytes(const Mat &A, int32_t tile) {
@@ -332,12 +335,18 @@ template <int VM, int T, int S>
 static gbsp_status launch_stream_T(const Mat &A, const VecArgs &v, cudaStream_t st) {
     typedef typename ValT<VM>::T V;
     const size_t smem = sizeof(StreamSmem<VM, T, S>);
-    static int configured[1] = {0};
-    if (!configured[0]) {
+    // the attribute belongs to the kernel on one device: set it once per
+    // device (it is cheap, and allowed during stream capture, so a device
+    // index out of the table's range simply sets it on every launch)
+    static std::atomic<int> configured[kStreamMaxDevices];
+    int dev = 0;
+    GBSP_CUDA(cudaGetDevice(&dev));
+    const bool tracked = dev >= 0 && dev < kStreamMaxDevices;
+    if (!tracked || !configured[dev].load()) {
         cudaError_t e = cudaFuncSetAttribute(crs_stream_kernel<VM, T, S>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(crs_stream_kernel)");
-        configured[0] = 1;
+        if (tracked) configured[dev].store(1);
     }
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, crs_stream_kernel<VM, T, S>,

@@ -1,5 +1,5 @@
 // Hybrid storage: dense secondary diagonals in DIA form, the rest in a
-// remainder matrix.  Sect. 3.2 observes that most entries of the
+// remainder matrix.  Sect. 4.2 observes that most entries of the
 // Holstein-Hubbard matrix lie in a few dense outer secondary diagonals, each
 // a candidate for a dense storage scheme, and leaves the hybrid unbuilt.
 //

@@ -1,4 +1,4 @@
-// Basic sparse vector operations (Sect. 3.1, the table of ADD and SCP
+// Basic sparse vector operations (Sect. 4.1, the table of ADD and SCP
 // kernels): one sum over i < n of B(idx(i)) (ADD) or A(i) * B(idx(i)) (SCP),
 // where idx(i) = i (PD, packed dense), k * i (CS, constant stride computed in
 // the loop) or ind(i) (IS / IR, read from an index array).  The paper uses
@@ -112,6 +112,37 @@ void launch_gather(int32_t access, int32_t grid, int64_t n, int64_t k, const dou
     }
 }
 
+// FP64 FMA issue rate.  The paper compares SpMVM against each machine's
+// peak Flop rate as well as its memory bandwidth; on GB300 the FP64 rate is
+// low enough to be a second roofline, so it is measured, not assumed.  Each
+// thread runs F independent chains x <- fma(x, a, b) for `iters` steps
+// (independent, so the pipe, not latency, is the limit).  Lanes at or above
+// `active` skip the loop: the FMAs of their warp still issue, so the time of
+// a launch shows what an idle lane costs.  out[t] = the sum of the thread's
+// chains in a fixed order (0 for skipped lanes).
+constexpr int F_CHAINS = 8;
+
+__global__ void __launch_bounds__(G_THREADS)
+    fma_chain_kernel(int64_t n, int32_t active, int32_t iters, const double *__restrict__ in,
+                     double *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * G_THREADS + threadIdx.x;
+    if (t >= n) return;
+    const double a = __ldg(in + 1), b = __ldg(in + 2);
+    double x[F_CHAINS];
+#pragma unroll
+    for (int j = 0; j < F_CHAINS; ++j) x[j] = __ldg(in) + (double)j;
+    double s = 0.0;
+    if ((int)(threadIdx.x & 31) < active) {
+        for (int32_t k = 0; k < iters; ++k) {
+#pragma unroll
+            for (int j = 0; j < F_CHAINS; ++j) x[j] = fma(x[j], a, b);
+        }
+#pragma unroll
+        for (int j = 0; j < F_CHAINS; ++j) s += x[j];
+    }
+    out[t] = s;
+}
+
 }  // namespace
 
 }  // namespace gbsp
@@ -155,5 +186,19 @@ extern "C" gbsp_status gbsp_gather_sum(int32_t op, int32_t access, int64_t n, in
     }
     gather_final_kernel<<<1, G_THREADS, 0, s>>>(d_partials, n > 0 ? grid : 0, d_out);
     GBSP_LAUNCH_CHECK("gather_final_kernel");
+    return GBSP_OK;
+}
+
+extern "C" gbsp_status gbsp_fma_chain(int64_t n_threads, int32_t active_lanes, int32_t iters, const double *d_in,
+                                      double *d_out, void *stream) {
+    if (n_threads < 0 || active_lanes < 0 || active_lanes > 32 || iters < 0)
+        return arg_error("gbsp_fma_chain: bad sizes");
+    if (n_threads == 0) return GBSP_OK;
+    if (!d_in || !d_out) return arg_error("gbsp_fma_chain: NULL pointer");
+    const int64_t grid = ceil_div(n_threads, G_THREADS);
+    if (grid > INT32_MAX) return arg_error("gbsp_fma_chain: too many threads");
+    fma_chain_kernel<<<(unsigned)grid, G_THREADS, 0, static_cast<cudaStream_t>(stream)>>>(
+        n_threads, active_lanes, iters, d_in, d_out);
+    GBSP_LAUNCH_CHECK("fma_chain_kernel");
     return GBSP_OK;
 }

@@ -20,21 +20,51 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 static std::mutex g_noalloc_mu;
 constexpr int kMaxDevices = 64;
+// per device: the context the address was looked up in, and the address
+static void *g_noalloc_ctx[kMaxDevices] = {nullptr};
 static void *g_noalloc_ptr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch array on the current device.  The host-side
-// name of a __device__ array is only a stand-in, so the address comes from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cuCtxGetCurrent through the runtime's driver entry-point lookup (the
+// library links only the CUDA runtime).  NULL if the lookup failed.
+typedef int (*CtxGetCurrentFn)(void **);
+static CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(f);
+    }
+    return fn;
+}
+
+// Device address of the scratch array in the current context.  The
+// host-side name of a __device__ array is only a stand-in, so the address
+// comes from cudaGetSymbolAddress, with the device current.  It is looked up
+// again whenever the device's current context differs from the one it was
+// looked up in (the module can load at another address after a device reset
+// or a new primary context); if the context cannot be identified, on every
+// call.
 static gbsp_status noalloc_scratch(void **out) {
     int dev = 0;
     GBSP_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return arg_error("gbsp_crs_spmv_noalloc: device index out of range");
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    CtxGetCurrentFn get = ctx_get_current();
+    void *ctx = nullptr;
+    bool known = get != nullptr && get(&ctx) == 0 && ctx != nullptr;
+    if (!known || !g_noalloc_ptr[dev] || g_noalloc_ctx[dev] != ctx) {
         void *p = nullptr;
+        // also makes the runtime's context of this device current, if none was
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(noalloc scratch)");
+        ctx = nullptr;
+        known = get != nullptr && get(&ctx) == 0 && ctx != nullptr;
         g_noalloc_ptr[dev] = p;
+        g_noalloc_ctx[dev] = known ? ctx : nullptr;
     }
     *out = g_noalloc_ptr[dev];
     return GBSP_OK;

@@ -1,6 +1,6 @@
 // Access-pattern analysis of the x gather.
 //
-// gbsp_stride_hist: the stride distribution of Sect. 4 (its Fig. 4a) -- the
+// gbsp_stride_hist: the stride distribution of Sect. 4.2 (its Fig. 4a) -- the
 // jumps between consecutive column indices in storage order, which is the
 // order the paper's serial CRS, JDS, RBJDS and SOJDS loops read x.
 // gbsp_warp_sectors: the GB300 counterpart -- for every warp-wide gather the

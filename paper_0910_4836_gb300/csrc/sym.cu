@@ -1,4 +1,4 @@
-// Symmetric SpMVM from one triangle.  Sect. 3.2 notes that the Hamiltonian
+// Symmetric SpMVM from one triangle.  Sect. 4.2 notes that the Hamiltonian
 // is symmetric, which would allow a further saving of data transfer, and
 // does not pursue it.  Here the stored entries S (the upper triangle of a
 // symmetric A: col >= row) are read once and applied twice:

@@ -1,6 +1,6 @@
 // Autotuner: times the candidate kernels of one handle on the device and
 // keeps the fastest.  The analogue of the paper's block-size and schedule
-// sweeps (Sect. 3.2 and 4): on GB300 the knobs are lanes per row, rows in
+// sweeps (Sect. 4.2 and 4): on GB300 the knobs are lanes per row, rows in
 // flight per lane group, the tile of the TILED kernel, the right-hand-side
 // tile, and for the JDS family the walk (JDS / NUJDS unroll / NBJDS block).
 // Results are cached per matrix signature so that a batch of similar

@@ -1,4 +1,4 @@
-"""The basic sparse vector operations of Sect. 3.1 (ADD / SCP over packed
+"""The basic sparse vector operations of Sect. 4.1 (ADD / SCP over packed
 dense, constant-stride and indirect access) on the device: argument
 marshalling over ``gbsp_gather_sum``."""
 from __future__ import annotations
@@ -59,3 +59,24 @@ def gather_sum(op: str, access: str, n: int, b: torch.Tensor, a: torch.Tensor | 
     """s = sum_i B(idx(i)) (ADD) or sum_i A(i) B(idx(i)) (SCP), idx(i) = i
     (PD), k i (CS) or ind(i) (IND), as a 1-element FP64 device tensor."""
     return GatherSum(op, access, n, b, a, k, ind, status)()
+
+
+class FmaChain:
+    """The FP64 issue-rate launch (``gbsp_fma_chain``): n_threads threads,
+    each running 8 independent chains x <- fma(x, a, b) for `iters` steps;
+    lanes >= active_lanes of each warp skip the chains.  ``flops`` counts
+    the arithmetic of the active lanes only."""
+
+    def __init__(self, n_threads: int, active_lanes: int = 32, iters: int = 4096, x0: float = 1.0,
+                 a: float = 0.5, b: float = 1.0, device="cuda"):
+        self.n, self.active, self.iters = int(n_threads), int(active_lanes), int(iters)
+        self.inp = torch.tensor([x0, a, b], dtype=torch.float64, device=device)
+        self.out = torch.empty(max(self.n, 1), dtype=torch.float64, device=device)
+        full, rest = divmod(self.n, 32)
+        self.active_threads = full * self.active + min(rest, self.active)
+        self.flops = 16.0 * self.iters * self.active_threads
+
+    def __call__(self, stream=None) -> torch.Tensor:
+        L.check(L.load().gbsp_fma_chain(self.n, self.active, self.iters, _vp(self.inp), _vp(self.out),
+                                        _stream(stream)), "gbsp_fma_chain")
+        return self.out

@@ -426,7 +426,7 @@ class DIAMatrix(_Product):
 
 
 class HybridMatrix:
-    """Dense secondary diagonals in DIA form plus the remainder (Sect. 3.2's
+    """Dense secondary diagonals in DIA form plus the remainder (Sect. 4.2's
     suggested hybrid): ``y = DIA x`` then the remainder's product added to
     it.  The remainder is kept in CRS or converted to SELL-32-sigma with the
     row-only permutation (vectors stay in the original basis)."""

@@ -12,12 +12,12 @@ every machine and numpy version, and any single entry can be regenerated.
 Matrices are returned as 0-based CRS (``row_ptr`` int32 of length n_rows+1,
 ``col`` int32, ``val`` float64) with column indices sorted inside each row.
 
-Workload recipes (the paper's Holstein-Hubbard matrix, Sect. 3.2, is not
+Workload recipes (the paper's Holstein-Hubbard matrix, Sect. 4.2, is not
 available, so these stand in for it):
 
 * ``laplace2d``     2D 5-point Laplacian, Dirichlet, 4 on the diagonal.
 * ``hh_like``       symmetric banded-plus-scattered matrix shaped like the
-                    paper's electron-phonon Hamiltonian (Sect. 3.2: dense
+                    paper's electron-phonon Hamiltonian (Sect. 4.2: dense
                     secondary diagonals, scattered entries, ~14 nnz/row).
 * ``zipf_rows``     irregular rows, lengths truncated Zipf(2) on [1, 5000],
                     uniform random columns.
@@ -161,7 +161,7 @@ def int_vector(n: int, seed: int, bound: int, stream: int = 103) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
-# Index arrays for the basic gather operations (Sect. 3.1: dense, constant
+# Index arrays for the basic gather operations (Sect. 4.1: dense, constant
 # stride, indirect with constant or random stride)
 # --------------------------------------------------------------------------
 
@@ -173,7 +173,7 @@ def stride_indices(n: int, k: int) -> np.ndarray:
 
 
 def bernoulli_indices(length: int, p: float, seed: int, stream: int = 211) -> np.ndarray:
-    """The IR index array as Sect. 3.1 draws it: every position j < length
+    """The IR index array as Sect. 4.1 draws it: every position j < length
     of the gathered vector is taken when a uniform draw is below p = 1/k."""
     j = np.arange(length, dtype=np.int64)
     return j[uniform01(seed, stream, j) < p].astype(np.int32)
@@ -199,7 +199,7 @@ def gaussian_indices(n: int, mean: float, var: float, length: int, seed: int,
                      stream: int = 217) -> np.ndarray:
     """Indices whose strides are normal(mean, var) rounded to integers, so
     that backward jumps occur once the variance is large enough (the
-    mean/variance plane of Sect. 3.1).  ind(0) = 0 and every step wraps
+    mean/variance plane of Sect. 4.1).  ind(0) = 0 and every step wraps
     modulo `length`, which keeps the walk inside the vector."""
     z = normal(seed, stream, np.arange(1, n))
     steps = np.rint(mean + np.sqrt(var) * z).astype(np.int64)
@@ -232,7 +232,7 @@ HH_BAND_OFFSETS = (1, 256, 512, 768, 1024, 65536, 131072, 196608, 262144)
 
 def hh_like(n: int = 6_000_000, seed: int = 1) -> CRS:
     """Symmetric banded-plus-scattered matrix shaped like a Holstein-Hubbard
-    Hamiltonian (Sect. 3.2).
+    Hamiltonian (Sect. 4.2).
 
     Row i draws m_i ~ U{3..10} upper-triangle neighbours.  Each neighbour is,
     with probability 0.8, at a band offset drawn uniformly from
@@ -274,7 +274,7 @@ HH_OUTER_OFFSETS = tuple(65536 * k for k in range(1, 7))
 
 
 def hh_diagonals(n: int = 6_000_000, seed: int = 5, fill: float = 0.8, band: int = 400) -> CRS:
-    """Symmetric stand-in that follows Sect. 3.2's description of the
+    """Symmetric stand-in that follows Sect. 4.2's description of the
     Holstein-Hubbard matrix literally: some 60% of the entries on 12 outer
     secondary diagonals, the rest spread evenly over a band a few hundred
     diagonals wide.

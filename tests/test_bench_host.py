@@ -55,3 +55,15 @@ def test_reference_arm_line_contract(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     monkeypatch.setenv("WORLD_SIZE", "2")
     assert bench.run_reference(args) is None
+
+
+def test_method_bytes_and_basis_labels():
+    """The JDS family's method bytes (val + col, the pointer array, x once,
+    y once) leave out the format's own arrays; every credited form names one
+    basis for both vectors."""
+    class A:
+        nnz, n_rows, n_cols = 100, 10, 20
+    assert bench.jds_method_bytes(A, 4) == 12 * 100 + 4 * 4 + 8 * 20 + 8 * 10
+    c = bench.Cand("x", None, None, "mixed", 1, credited=False)
+    assert not c.credited and "NOT one basis" in bench.BASIS_LABEL["mixed"]
+    assert set(bench.BASIS_LABEL) == {"original", "permuted", "mixed"}

@@ -1,4 +1,4 @@
-"""The basic gather sums of Sect. 3.1 (ADD / SCP over PD, CS, IS, IR and
+"""The basic gather sums of Sect. 4.1 (ADD / SCP over PD, CS, IS, IR and
 Gaussian strides) on the GPU against the oracle."""
 import math
 
@@ -121,3 +121,19 @@ def test_gather_argument_errors():
         GatherSum("ADD", "PD", 101, b)()
     with pytest.raises(GbspError):
         GatherSum("ADD", "CS", 5, b, k=0)()
+
+
+def test_fma_chain_closed_form():
+    """The FP64 issue-rate launch computes what it claims: with x0 = 1,
+    a = 1/2, b = 1, chain j after k steps is 2 + (j - 1) 2^-k exactly, so a
+    thread's sum of its 8 chains is 16 + 20 / 2^k; idle lanes write 0."""
+    from paper_0910_4836_gb300 import build
+    from paper_0910_4836_gb300.gather import FmaChain
+    build()
+    for n, active, k in ((1000, 32, 3), (4096, 5, 3), (257, 32, 0), (2048, 16, 40)):
+        f = FmaChain(n, active_lanes=active, iters=k)
+        out = f().cpu().numpy()
+        lanes = np.arange(n) % 32
+        want = np.where(lanes < active, 16.0 + 20.0 / 2.0 ** k, 0.0)
+        assert np.array_equal(out, want), (n, active, k)
+        assert f.flops == 16.0 * k * np.count_nonzero(lanes < active)

@@ -1,5 +1,5 @@
 """Access-pattern analysis on the GPU against the oracle: the stride
-distribution of Sect. 4 (Fig. 4a) and the sectors per warp-wide gather.
+distribution of Sect. 4.2 (Fig. 4a) and the sectors per warp-wide gather.
 Integer counts, so bit-exact."""
 import numpy as np
 import pytest

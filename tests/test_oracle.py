@@ -246,7 +246,7 @@ def test_jds_family_equals_crs_in_permuted_basis(sym):
     """JDS / NBJDS / NUJDS / RBJDS all add each row's entries in slot order
     from zero, so they are bit-identical to CRS on P A P^T; NUJDS with
     u = N_j is stated to be exactly that (Sect. 2), RBJDS with block 1 is
-    row-by-row access and JDS is NBJDS with block = N (Sect. 3.2)."""
+    row-by-row access and JDS is NBJDS with block = N (Sect. 4.2)."""
     A = S.hh_like(5000, 31)
     x = S.vector(A.n_cols, 31)
     J = O.jds_build(A, symmetric=sym)
@@ -554,7 +554,7 @@ def test_generator_shapes():
 
 
 # --------------------------------------------------------------------------
-# Basic sparse vector operations (Sect. 3.1 table: ADD / SCP over PD, CS,
+# Basic sparse vector operations (Sect. 4.1 table: ADD / SCP over PD, CS,
 # IS, IR)
 # --------------------------------------------------------------------------
 
@@ -647,7 +647,7 @@ def test_gaussian_indices_zero_variance_is_constant_stride():
 
 
 # --------------------------------------------------------------------------
-# Stride distribution (Sect. 4, Fig. 4a) and sectors per warp-wide gather
+# Stride distribution (Sect. 4.2, Fig. 4a) and sectors per warp-wide gather
 # --------------------------------------------------------------------------
 
 def tridiagonal(n):
@@ -809,7 +809,7 @@ def test_psell_pairs_long_with_short():
 
 
 # --------------------------------------------------------------------------
-# Symmetric SpMVM from the upper triangle (Sect. 3.2's unused symmetry)
+# Symmetric SpMVM from the upper triangle (Sect. 4.2's unused symmetry)
 # --------------------------------------------------------------------------
 
 def symmetric_random(n, seed, density):
@@ -860,7 +860,7 @@ def test_sym_spmv_hh_like_matches_crs():
 
 # --------------------------------------------------------------------------
 # Hybrid storage: dense secondary diagonals in DIA form + remainder CRS
-# (Sect. 3.2 names the dense secondary diagonals as candidates for dense storage)
+# (Sect. 4.2 names the dense secondary diagonals as candidates for dense storage)
 # --------------------------------------------------------------------------
 
 def dense_of(offs, dia, rem, n_cols):
