@@ -47,6 +47,12 @@ template <int VM> struct Acc {
         o.s = __shfl_xor_sync(0xffffffffu, s, off);
         merge(o);
     }
+    // this += (the partner lane's `send`), partner = lane ^ off
+    __device__ __forceinline__ void merge_shfl_xor(const Acc &send, int off) {
+        Acc o;
+        o.s = __shfl_xor_sync(0xffffffffu, send.s, off);
+        merge(o);
+    }
     __device__ __forceinline__ T result() const { return s; }
 };
 
@@ -77,6 +83,12 @@ template <> struct Acc<VM_F32C> {
         Acc o;
         o.s = __shfl_xor_sync(0xffffffffu, s, off);
         o.c = __shfl_xor_sync(0xffffffffu, c, off);
+        merge(o);
+    }
+    __device__ __forceinline__ void merge_shfl_xor(const Acc &send, int off) {
+        Acc o;
+        o.s = __shfl_xor_sync(0xffffffffu, send.s, off);
+        o.c = __shfl_xor_sync(0xffffffffu, send.c, off);
         merge(o);
     }
     __device__ __forceinline__ float result() const { return s + c; }

@@ -47,10 +47,13 @@ crs_vector_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
             }
             len = max(len, k1[i] - k0[i]);
         }
+        // one trip count for the whole warp (the base loop is warp-uniform),
+        // so that every lane reaches the warp-wide vote below
+        len = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
         Acc<VM> acc[R];
 #pragma unroll
         for (int i = 0; i < R; ++i) acc[i].init();
-        for (int j = gl; j < len; j += L) {
+        for (int j = gl; j - gl < len; j += L) {
             int c[R];
             T v[R];
 #pragma unroll
@@ -63,18 +66,49 @@ crs_vector_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
                 v[i] = ok ? __ldg(val + k) : T(0);
             }
 #pragma unroll
-            for (int i = 0; i < R; ++i)
-                if (c[i] >= 0) acc[i].add(v[i], ld_vec(x + (int64_t)c[i] * ldx));
-        }
-#pragma unroll
-        for (int i = 0; i < R; ++i) group_reduce<L, VM>(acc[i]);
-        if (gl == 0) {
-#pragma unroll
             for (int i = 0; i < R; ++i) {
-                const int64_t r = base + i * G + grp;
-                if (r < n_rows) {
-                    if (accumulate) acc[i].add_value(y[r * ldy]);
-                    y[r * ldy] = acc[i].result();
+                // row slot i of every group past its end: skip the warp's
+                // gather and FMA (an idle lane's FP64 FMA costs as much as a
+                // busy one's)
+                if (R > 1 && !__any_sync(0xffffffffu, c[i] >= 0)) continue;
+                if (c[i] >= 0) acc[i].add(v[i], ld_vec(x + (int64_t)c[i] * ldx));
+            }
+        }
+        if (R == L && VM != VM_F32C) {
+            // reduce-scatter: log2(L) steps, each lane trading half of its
+            // partial sums with its partner, so lane gl ends with row gl's
+            // total after L - 1 additions instead of R log2(L).  The tree per
+            // row is the xor butterfly of group_reduce with some additions'
+            // operands swapped, which plain sums do not notice: every row's
+            // sum is bit-identical to it.  (The compensated merge is not
+            // symmetric in its error terms, so FP32C keeps the butterfly.)
+#pragma unroll
+            for (int o = L / 2, h = R / 2; o > 0; o >>= 1, h >>= 1) {
+                const bool up = (gl & o) != 0;
+#pragma unroll
+                for (int k = 0; k < h; ++k) {
+                    Acc<VM> send = up ? acc[k] : acc[k + h];
+                    Acc<VM> keep = up ? acc[k + h] : acc[k];
+                    keep.merge_shfl_xor(send, o);
+                    acc[k] = keep;
+                }
+            }
+            const int64_t r = base + gl * G + grp;
+            if (r < n_rows) {
+                if (accumulate) acc[0].add_value(y[r * ldy]);
+                y[r * ldy] = acc[0].result();
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < R; ++i) group_reduce<L, VM>(acc[i]);
+            if (gl == 0) {
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const int64_t r = base + i * G + grp;
+                    if (r < n_rows) {
+                        if (accumulate) acc[i].add_value(y[r * ldy]);
+                        y[r * ldy] = acc[i].result();
+                    }
                 }
             }
         }

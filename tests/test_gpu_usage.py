@@ -37,8 +37,7 @@ def test_documented_usage():
 
     M.transpose()
     g = M.spmv(torch.as_tensor(ref).cuda(), transpose=True)
-    At = O.transpose(A)
-    rt, st = O.crs_spmv_exact(At, ref)
+    rt, st = O.crs_spmv_t_exact(A, ref)
     assert_close64(host(g), rt, st, "adjoint")
     d = host(M.dval(torch.as_tensor(ref).cuda(), x))
     assert np.array_equal(d, O.dval(A, ref, xh))  # one rounded product per entry
