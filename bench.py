@@ -179,7 +179,7 @@ def job_throughput(units_per_rank: float, world: int, max_ms: float) -> float:
 
 
 # the functions a step kernel is made of (kernel, its launchers), by scheme
-STEP_FUNCTIONS = {"SELL": ("jds.cu", ("store_row(const JdsArgs &a", "sell_walk(const JdsArgs &a)", "sell_kernel(JdsArgs a)", "sell_kernel_f64(JdsArgs a)",
+STEP_FUNCTIONS = {"SELL": ("jds.cu", ("store_row_sell(const JdsArgs &a", "sell_walk(const JdsArgs &a)", "sell_kernel(JdsArgs a)", "sell_kernel_f64(JdsArgs a)",
                                      "launch_sell_U(JdsArgs a", "launch_sell(const Mat"))}
 
 
@@ -1214,7 +1214,8 @@ def run_ncu_case(args):
     """A few launches of one kernel for an ncu capture; prints nothing to
     time.  Config 1: a 2e6-row HH-like matrix (~350 MB, above the 129 MB
     L2), or with --ncu-full the full 6e6-row workload (for one-pass
-    counters only).  Config 2: the Zipf-rows matrix (345 MB) and the
+    counters only); --kernel names a step candidate, or "dval" for the
+    value gradient.  Config 2: the Zipf-rows matrix (345 MB) and the
     kernel named by --kernel among its candidates."""
     import torch
     from paper_0910_4836_gb300 import CRSMatrix, build, synth as S
@@ -1238,6 +1239,14 @@ def run_ncu_case(args):
     M = CRSMatrix.from_host(A)
     x = torch.as_tensor(S.vector(A.n_cols, 1)).cuda()
     y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+    if only == "dval":
+        g = torch.as_tensor(S.vector(A.n_rows, 7)).cuda()
+        d = torch.empty(A.nnz, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            M.dval(g, x, out=d)
+        torch.cuda.synchronize()
+        print("ran dval")
+        return
     for c in candidates(M, A, x, only):
         if only is not None and c.name != only:
             continue

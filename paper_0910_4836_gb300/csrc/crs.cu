@@ -6,7 +6,11 @@
 // group keeps R rows in flight: the loads of all R rows are issued before
 // any product is formed, which is what keeps enough bytes in flight to
 // saturate HBM with short rows.  The partial sums are combined by a fixed
-// butterfly of warp shuffles.
+// butterfly of warp shuffles; when a group holds as many rows as it has
+// lanes, by a reduce-scatter that leaves each lane one row's total (same
+// tree, fewer FP64 additions: on GB300 each one is a full-rate-limited FP64
+// instruction).  A warp whose rows include one longer than kLongRow works
+// on its rows one at a time with the whole warp instead.
 //
 // SpMM: lanes over right-hand sides -- a group of KT lanes owns one row and
 // lane c accumulates column c of the RHS tile, so each entry (val, col) is
@@ -19,6 +23,45 @@
 namespace gbsp {
 
 constexpr int kThreads = 256;
+// row length beyond which a VECTOR warp gives every row all 32 lanes
+constexpr int kLongRow = 512;
+
+// Rows [base, base + n) with the whole warp on each row in turn: lanes
+// stride through the row four loads deep, then a full-warp sum.  Kept out of
+// line so that it does not raise the register count of the common path.
+template <int VM>
+__device__ __noinline__ void crs_warp_rows(int64_t base, int64_t n, const int32_t *__restrict__ row_ptr,
+                                           const int32_t *__restrict__ col,
+                                           const typename ValT<VM>::T *__restrict__ val,
+                                           const typename ValT<VM>::T *__restrict__ x, int64_t ldx,
+                                           typename ValT<VM>::T *__restrict__ y, int64_t ldy, int accumulate) {
+    typedef typename ValT<VM>::T T;
+    const int lane = threadIdx.x & 31;
+    for (int64_t q = 0; q < n; ++q) {
+        const int64_t r = base + q;
+        const int s0 = __ldg(row_ptr + r), s1 = __ldg(row_ptr + r + 1);
+        Acc<VM> a;
+        a.init();
+        for (int j = s0 + lane; j < s1; j += 4 * 32) {
+            int c[4];
+            T v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = j + 32 * u < s1;
+                c[u] = ok ? __ldg(col + j + 32 * u) : -1;
+                v[u] = ok ? __ldg(val + j + 32 * u) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (c[u] >= 0) a.add(v[u], ld_vec(x + (int64_t)c[u] * ldx));
+        }
+        group_reduce<32, VM>(a);
+        if (lane == 0) {
+            if (accumulate) a.add_value(y[r * ldy]);
+            y[r * ldy] = a.result();
+        }
+    }
+}
 
 template <int VM, int L, int R>
 __global__ void __launch_bounds__(kThreads)
@@ -47,13 +90,18 @@ crs_vector_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
             }
             len = max(len, k1[i] - k0[i]);
         }
-        // one trip count for the whole warp (the base loop is warp-uniform),
-        // so that every lane reaches the warp-wide vote below
-        len = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
+        // A warp holding a very long row (heavy-tailed row lengths) would
+        // keep its L lanes on that row long after the rest of the grid is
+        // done.  Such a warp instead takes its rows one at a time with all
+        // 32 lanes, four loads in flight per lane, and a full-warp sum.
+        if (__reduce_max_sync(0xffffffffu, (unsigned)len) > (unsigned)kLongRow) {
+            crs_warp_rows<VM>(base, min((int64_t)RW, n_rows - base), row_ptr, col, val, x, ldx, y, ldy, accumulate);
+            continue;
+        }
         Acc<VM> acc[R];
 #pragma unroll
         for (int i = 0; i < R; ++i) acc[i].init();
-        for (int j = gl; j - gl < len; j += L) {
+        for (int j = gl; j < len; j += L) {
             int c[R];
             T v[R];
 #pragma unroll
@@ -66,13 +114,8 @@ crs_vector_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
                 v[i] = ok ? __ldg(val + k) : T(0);
             }
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-                // row slot i of every group past its end: skip the warp's
-                // gather and FMA (an idle lane's FP64 FMA costs as much as a
-                // busy one's)
-                if (R > 1 && !__any_sync(0xffffffffu, c[i] >= 0)) continue;
+            for (int i = 0; i < R; ++i)
                 if (c[i] >= 0) acc[i].add(v[i], ld_vec(x + (int64_t)c[i] * ldx));
-            }
         }
         if (R == L && VM != VM_F32C) {
             // reduce-scatter: log2(L) steps, each lane trading half of its
@@ -164,15 +207,71 @@ crs_spmm_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
 // dval_k: d = (accumulate ? dval_k : 0), then d = fma(G[row_k, t], X[col_k, t], d)
 // for t = 0, 1, ..., m-1 (m = 1: g[row] x[col]).  One running sum in a fixed
 // order, so splitting the t range over several calls changes nothing.
-// A warp owns 32 consecutive rows and walks their entries 32 at a time, so
-// every col load and dval store is one contiguous warp-wide access; each
-// lane finds its entry's row by stepping forward through the 33 row
-// pointers, which the warp keeps in shared memory.
+// Both kernels give a warp 32 consecutive rows and walk their entries in
+// chunks of 32: lane l takes entry c + l of chunk c, so every col load and
+// dval store is one contiguous warp-wide access.
+//   m = 1 (crs_dval_kernel): kDvalU chunks in flight together (their
+//     gathers are what the kernel waits for); the warp's 32 row pointers sit
+//     one per lane and a lane finds its entry's row by a five-step binary
+//     search over them with shuffles; dval is written evict-first (it is not
+//     read again here), which leaves L2 to the gathered vectors.  HH-like
+//     6M: 285 us against 405 us for one chunk at a time.
+//   m > 1 (crs_dval_multi_kernel): one chunk at a time, rows found by
+//     stepping forward through the row pointers in shared memory.  With
+//     the loop over t inside, several chunks in flight took 72 registers
+//     and ran slower (27-point stencil, m = 5: 287 us against 249 us).
 constexpr int kDvalWarps = kThreads / 32;
+constexpr int kDvalU = 4;
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 crs_dval_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
+                const int32_t *__restrict__ col, int m, const T *__restrict__ G, int64_t g_row,
+                int64_t g_t, const T *__restrict__ X, int64_t x_row, int64_t x_t, T *__restrict__ dval,
+                int accumulate) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r0 = warp * 32; r0 < n_rows; r0 += nwarp * 32) {
+        // lane i: start of row r0 + i (rows past the end start at nnz)
+        const int32_t rpl = __ldg(row_ptr + min(r0 + lane, n_rows));
+        const int32_t e1 = __ldg(row_ptr + min(r0 + 32, n_rows));
+        const int32_t eb = __shfl_sync(0xffffffffu, rpl, 0);
+        const T *Gw = G + r0 * g_row;
+        for (int32_t c = eb; c < e1; c += 32 * kDvalU) {
+            int32_t cj[kDvalU], rl[kDvalU];
+            T d[kDvalU];
+#pragma unroll
+            for (int u = 0; u < kDvalU; ++u) {
+                const int32_t e = c + 32 * u + lane;
+                // the last row i (of the warp's 32) with start <= e; every
+                // lane takes part, so the shuffles see the whole warp
+                int lo = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int32_t v = __shfl_sync(0xffffffffu, rpl, lo + step);
+                    if (v <= e) lo += step;
+                }
+                rl[u] = lo;
+                cj[u] = e < e1 ? ld_stream(col + e) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kDvalU; ++u) {
+                const int32_t e = c + 32 * u + lane;
+                d[u] = cj[u] >= 0 ? fma(__ldg(Gw + rl[u] * g_row), __ldg(X + (int64_t)cj[u] * x_row),
+                                        accumulate ? dval[e] : T(0))
+                                  : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < kDvalU; ++u)
+                if (cj[u] >= 0) __stcs(dval + c + 32 * u + lane, d[u]);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+crs_dval_multi_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
                 const int32_t *__restrict__ col, int m, const T *__restrict__ G, int64_t g_row,
                 int64_t g_t, const T *__restrict__ X, int64_t x_row, int64_t x_t, T *__restrict__ dval,
                 int accumulate) {
@@ -360,9 +459,14 @@ static void launch_dval(const Mat &A, int32_t m, const void *G, int64_t g_row, i
                         const void *X, int64_t x_row, int64_t x_t, void *dval, int32_t accumulate,
                         cudaStream_t s) {
     const int grid = grid_for(ceil_div(A.n_rows, 32));
-    crs_dval_kernel<T><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, m, static_cast<const T *>(G), g_row,
-                                                 g_t, static_cast<const T *>(X), x_row, x_t, static_cast<T *>(dval),
-                                                 accumulate);
+    if (m == 1)
+        crs_dval_kernel<T><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, m, static_cast<const T *>(G), g_row,
+                                                     g_t, static_cast<const T *>(X), x_row, x_t,
+                                                     static_cast<T *>(dval), accumulate);
+    else
+        crs_dval_multi_kernel<T><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, m, static_cast<const T *>(G),
+                                                           g_row, g_t, static_cast<const T *>(X), x_row, x_t,
+                                                           static_cast<T *>(dval), accumulate);
 }
 
 gbsp_status crs_dval_launch(const Mat &A, int32_t m, const void *G, int64_t g_row, int64_t g_t,

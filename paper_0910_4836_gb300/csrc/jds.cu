@@ -53,6 +53,7 @@ struct JdsArgs {
     int64_t split_rows;    // those rows: [0, split_rows)
     int64_t n_cols;
     int32_t grid_limit;    // 0 = none
+    int32_t y_evict_first; // y too large to stay in L2 until its next use: write it evict-first
 };
 
 __device__ __forceinline__ int64_t xidx(const int32_t *x_perm, int32_t c) {
@@ -65,9 +66,24 @@ __device__ __forceinline__ void store_row(const JdsArgs &a, int64_t r, int c, Ac
     const int64_t row = a.y_perm ? (int64_t)__ldg(a.y_perm + r) : r;
     T *yp = static_cast<T *>(a.y) + row * a.ldy + c;
     if (a.accumulate) acc.add_value(*yp);
-    // evict-first: y is not read again by the product, and keeping it out
-    // of L2 leaves room for the gathered x (measured 1% on the SELL step)
-    __stcs(yp, acc.result());
+    *yp = acc.result();
+}
+
+// store_row for the SELL walks.  A y larger than a quarter of L2 is written
+// evict-first: it cannot survive the next product's matrix stream anyway,
+// and keeping it out of L2 leaves room for the gathered x (SELL step,
+// HH-like 6M: about 1%).  A smaller y stays cached for the next product
+// that reads it, as in a power iteration.  (The SELL kernels have a fixed
+// register budget; in the JDS row walk the extra branch cost 6 registers
+// and a quarter of its occupancy, so the other walks store plainly.)
+template <int VM>
+__device__ __forceinline__ void store_row_sell(const JdsArgs &a, int64_t r, int c, Acc<VM> &acc) {
+    typedef typename ValT<VM>::T T;
+    const int64_t row = a.y_perm ? (int64_t)__ldg(a.y_perm + r) : r;
+    T *yp = static_cast<T *>(a.y) + row * a.ldy + c;
+    if (a.accumulate) acc.add_value(*yp);
+    if (a.y_evict_first) __stcs(yp, acc.result());
+    else *yp = acc.result();
 }
 
 // JDS (U = 1) and NUJDS (U > 1): one thread per permuted row, U diagonals
@@ -396,7 +412,7 @@ __device__ __forceinline__ void sell_walk(const JdsArgs &a) {
         if (r < a.n_rows) {
 #pragma unroll
             for (int q = 0; q < KT; ++q)
-                if (KT == 1 || a.c0 + q < a.k) store_row<VM>(a, r, a.c0 + q, acc[q]);
+                if (KT == 1 || a.c0 + q < a.k) store_row_sell<VM>(a, r, a.c0 + q, acc[q]);
         }
     }
 }
@@ -885,6 +901,10 @@ gbsp_status jds_launch(const Mat &A, const VecArgs &v, cudaStream_t s) {
     a.split_shallow = nullptr;
     a.n_cols = A.n_cols;
     a.grid_limit = A.grid_limit;
+    {
+        const int64_t ybytes = A.n_rows * std::max<int64_t>(v.ldy, v.k) * (A.dtype == GBSP_F64 ? 8 : 4);
+        a.y_evict_first = ybytes > (int64_t(32) << 20) ? 1 : 0;
+    }
     gbsp_status st;
     if (A.dtype == GBSP_F64) st = launch_family<VM_F64>(A, a, s);
     else if (A.kopt.accum == GBSP_ACC_COMPENSATED) st = launch_family<VM_F32C>(A, a, s);
