@@ -225,7 +225,7 @@ def kernel_source_hash(kname: str = "SELL") -> str:
 # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
 # a one-pass metric set), keyed by (config, kernel, source hash); a different
 # hash means the kernel changed since and traffic is reported null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {(1, "SELL symmetric w=128 u=4", "1eb4028f7acd"): 1087842304 + 42059776}
 
 
 # --------------------------------------------------------------- ours ------
@@ -934,13 +934,17 @@ def fwd_bwd_speedup(dev, time_launches):
             return v.grad, xx.grad
 
         for _ in range(2):
-            plain(), tuned()
+            plain(), tuned(), tuned(1)
         tp = statistics.median(time_launches(plain, 5))
         tt = statistics.median(time_launches(tuned, 5))
+        t1 = statistics.median(time_launches(lambda: tuned(1), 5))
         key = "f64" if dtype == torch.float64 else "f32"
         res[key] = {"plain_ms": round(tp, 3), "tuned_ms": round(tt, 3), "speedup": round(tp / tt, 3),
                     "vectors_stored_plain": m + 1, "vectors_stored_tuned": m // 5 + 5,
-                    "tuned_forward": getattr(pt.F, "fmt", "CRS"), "tuned_adjoint": getattr(pt._adj, "fmt", "CRS")}
+                    "tuned_forward": getattr(pt.F, "fmt", "CRS"), "tuned_adjoint": getattr(pt._adj, "fmt", "CRS"),
+                    "checkpoint": 5,
+                    "tuned_all_stored": {"checkpoint": 1, "ms": round(t1, 3), "speedup": round(tp / t1, 3),
+                                         "vectors_stored": m + 1}}
     return res
 
 
@@ -1066,7 +1070,7 @@ def run_micro(args):
         ind_d = None if ind is None else torch.as_tensor(ind).to(dev)
         g = GatherSum(op, access, n, B, a=A[:n] if op == "SCP" else None, k=k, ind=ind_d)
         ms = timed(g)
-        useful = n * (8 + (8 if op == "SCP" else 0) + (4 if access == "IND" else 0))
+        useful = n * (8 + (8 if op == "SCP" else 0) + (4 if access in ("IND", "IND_TMA") else 0))
         res = {"n": n, "us": round(ms * 1e3, 2), "gups": round(n / (ms * 1e-3) / 1e9, 2),
                "useful_gbs": round(useful / (ms * 1e-3) / 1e9, 1)}
         return res
@@ -1089,6 +1093,24 @@ def run_micro(args):
         n = n_for(k, 2 ** 25)
         sweep[str(k)] = {"ISSCP": point("SCP", "IND", n, ind=S.stride_indices(n, k)),
                          "IRSCP": point("SCP", "IND", n, ind=S.geometric_indices(n, 1.0 / k, 200 + k))}
+    # the x gathers of the Zipf-rows workload (22.1M entries, uniform random
+    # columns over 4M rows): one load per lane (IND) against TMA gather4
+    # copies into shared memory (IND_TMA), and the floor of a column-panel
+    # design, in which every SM reads all of x through shared memory
+    from paper_0910_4836_gb300.gather import stage_sweep
+    nz, lz = 22_098_169, 4_000_000
+    zind = S.uniform_indices(nz, lz, 401)
+    zipf_like = {"n": nz, "vector": lz}
+    for op in ("ADD", "SCP"):
+        for acc in ("IND", "IND_TMA"):
+            zipf_like[f"{op} {acc}"] = point(op, acc, nz, ind=zind)
+    xs = B[:lz]
+    ms = timed(lambda: stage_sweep(xs))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    zipf_like["stage_sweep"] = {"us": round(ms * 1e3, 1), "sms": sms,
+                                "l2_to_smem_tbs": round(sms * lz * 8 / (ms * 1e-3) / 1e12, 2),
+                                "what": "every SM reads all of x through shared memory once"}
+    table["zipf_like_gathers"] = zipf_like
     plane = {}
     n = 2 ** 23
     for mean in (1, 4, 16, 64, 256):
@@ -1221,6 +1243,22 @@ def run_ncu_case(args):
     from paper_0910_4836_gb300 import CRSMatrix, build, synth as S
     build()
     only = None if args.kernel == "auto" else args.kernel
+    if only in ("gather IND", "gather IND_TMA", "stage sweep"):
+        # the Zipf-rows x gathers as a basic gather sum (22.1M uniform
+        # indices over a 4M vector), or the staging floor
+        from paper_0910_4836_gb300.gather import GatherSum, stage_sweep
+        xz = torch.as_tensor(S.vector(4_000_000, 2)).cuda()
+        if only == "stage sweep":
+            for _ in range(3):
+                stage_sweep(xz)
+        else:
+            ind = torch.as_tensor(S.uniform_indices(22_098_169, 4_000_000, 401)).cuda()
+            gs = GatherSum("ADD", only.split()[1], ind.numel(), xz, ind=ind)
+            for _ in range(3):
+                gs()
+        torch.cuda.synchronize()
+        print("ran", only)
+        return
     if args.config == 2:
         A = S.config(2)
         M = CRSMatrix.from_host(A)

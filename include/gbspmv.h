@@ -547,7 +547,11 @@ gbsp_status gbsp_crs_spmv_noalloc(int64_t n_rows, int64_t n_cols, int64_t nnz,
  * in the loop) or ind(i) (IND: the paper's IS with ind(i) = k*i and IR with
  * random strides differ only in the index array the caller passes). */
 typedef enum { GBSP_GATHER_ADD = 0, GBSP_GATHER_SCP = 1 } gbsp_gather_op;
-typedef enum { GBSP_ACCESS_PD = 0, GBSP_ACCESS_CS = 1, GBSP_ACCESS_IND = 2 } gbsp_access;
+/* IND_TMA is IND with B fetched by the tensor memory accelerator (tile::
+ * gather4 copies of 16-byte rows into shared memory) instead of one load
+ * per lane: the GB300 alternative for gathers that miss L1, measured beside
+ * IND.  It needs len_b >= 2, len_b / 2 < 2^31 and B 16-byte aligned. */
+typedef enum { GBSP_ACCESS_PD = 0, GBSP_ACCESS_CS = 1, GBSP_ACCESS_IND = 2, GBSP_ACCESS_IND_TMA = 3 } gbsp_access;
 
 /* Sect. 4.1, the basic sparse vector operations.
  * Number of FP64 partial sums gbsp_gather_sum needs for n elements on the
@@ -570,6 +574,21 @@ gbsp_status gbsp_gather_sum(int32_t op, int32_t access, int64_t n, int64_t strid
                             const double *d_a, const double *d_b, int64_t len_b,
                             const int32_t *d_ind, double *d_partials, int32_t n_partials,
                             double *d_out, int32_t *d_status, void *stream);
+
+/* Sect. 4.1, the cost of the other way around the indirect access: stage
+ * the gathered vector in shared memory by panels and read it from there.
+ * For uniformly random indices every SM needs every panel, so B crosses
+ * from L2 into each SM's shared memory once per product; this launch does
+ * exactly that and nothing else (one CTA per SM, each streaming the whole
+ * 16-byte blocks of d_b [len_b] into shared memory with 32 KB bulk copies,
+ * four in flight), so its time is a floor for any column-panel gather of
+ * such indices.  d_out [n_out >= the SM count] receives, per CTA, the sum
+ * of the first double of every 32 KB chunk.  A bounded wait that gives up
+ * (1 s) writes GBSP_ERR_TIMEOUT to *d_status when d_status (device int32)
+ * is given.  One launch on `stream`.  Errors: GBSP_ERR_ARG for NULL
+ * pointers, B not 16-byte aligned or n_out too small. */
+gbsp_status gbsp_stage_sweep(const double *d_b, int64_t len_b, double *d_out, int32_t n_out, int32_t *d_status,
+                             void *stream);
 
 /* The FP64 issue rate that bounds every kernel here besides HBM.  The paper
  * sets SpMVM against both the memory bandwidth and the peak Flop rate of

@@ -127,6 +127,7 @@ SIGNATURES = {
     "gbsp_upper_build": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(c_vp)]),
     "gbsp_spmv_symmetric": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_vp]),
     "gbsp_warp_sectors": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_vp]),
+    "gbsp_stage_sweep": (c_i32, [c_vp, c_i64, c_vp, c_i32, c_vp, c_vp]),
     "gbsp_fma_chain": (c_i32, [c_i64, c_i32, c_i32, c_vp, c_vp, c_vp]),
     "gbsp_gather_sum": (c_i32, [c_i32, c_i32, c_i64, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_i32, c_vp,
                                 c_vp, c_vp]),

@@ -11,7 +11,7 @@ from . import _lib as L
 from .sparse import _need_cuda, _stream, _vp
 
 OPS = {"ADD": 0, "SCP": 1}
-ACCESS = {"PD": 0, "CS": 1, "IND": 2}
+ACCESS = {"PD": 0, "CS": 1, "IND": 2, "IND_TMA": 3}
 
 
 def partials_needed(n: int) -> int:
@@ -30,7 +30,7 @@ class GatherSum:
             raise ValueError(f"unknown op {op!r} or access {access!r}")
         self.b = _need_cuda(b, "b", torch.float64)
         self.a = _need_cuda(a, "a", torch.float64) if op == "SCP" else None
-        self.ind = _need_cuda(ind, "ind", torch.int32) if access == "IND" else None
+        self.ind = _need_cuda(ind, "ind", torch.int32) if access in ("IND", "IND_TMA") else None
         if self.a is not None and self.a.numel() < n:
             raise ValueError("a shorter than n")
         if self.ind is not None and self.ind.numel() < n:
@@ -80,3 +80,18 @@ class FmaChain:
         L.check(L.load().gbsp_fma_chain(self.n, self.active, self.iters, _vp(self.inp), _vp(self.out),
                                         _stream(stream)), "gbsp_fma_chain")
         return self.out
+
+
+def stage_sweep(b: torch.Tensor, out: torch.Tensor | None = None, status: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """Every SM reads all of ``b`` through shared memory once
+    (``gbsp_stage_sweep``): the floor of a column-panel gather for
+    uniformly random indices.  Returns, per SM, the sum of the first double
+    of every 32 KB chunk."""
+    b = _need_cuda(b, "b", torch.float64)
+    sms = torch.cuda.get_device_properties(b.device).multi_processor_count
+    if out is None:
+        out = torch.empty(sms, dtype=torch.float64, device=b.device)
+    L.check(L.load().gbsp_stage_sweep(_vp(b), b.numel(), _vp(out), out.numel(), _vp(status), _stream(stream)),
+            "gbsp_stage_sweep")
+    return out

@@ -195,6 +195,16 @@ def geometric_indices(n: int, p: float, seed: int, stream: int = 213) -> np.ndar
     return ind.astype(np.int32)
 
 
+def uniform_indices(n: int, length: int, seed: int, stream: int = 219) -> np.ndarray:
+    """n indices uniform on [0, length), int32: the x gathers of a matrix
+    with uniformly random columns (the Zipf-rows workload), as an index
+    array for the basic gather sums."""
+    if length > 2 ** 31:
+        raise ValueError("uniform_indices: length exceeds int32")
+    u = uniform01(seed, stream, np.arange(n))
+    return np.minimum((u * length).astype(np.int64), length - 1).astype(np.int32)
+
+
 def gaussian_indices(n: int, mean: float, var: float, length: int, seed: int,
                      stream: int = 217) -> np.ndarray:
     """Indices whose strides are normal(mean, var) rounded to integers, so

@@ -137,3 +137,56 @@ def test_fma_chain_closed_form():
         want = np.where(lanes < active, 16.0 + 20.0 / 2.0 ** k, 0.0)
         assert np.array_equal(out, want), (n, active, k)
         assert f.flops == 16.0 * k * np.count_nonzero(lanes < active)
+
+
+def _uniform_indices(n, length, seed):
+    ind = np.minimum((S.uniform01(seed, 233, np.arange(n)) * length).astype(np.int64), length - 1)
+    ind[min(5, n - 1)] = length - 1  # the last element (an odd tail is read directly)
+    return ind.astype(np.int32)
+
+
+@pytest.mark.parametrize("op", ["ADD", "SCP"])
+@pytest.mark.parametrize("len_b", [4_000_001, 4_000_000, 3, 2])
+def test_gather_tma_within_bound_and_bit_exact(op, len_b):
+    """IND through TMA gather4 copies: random indices over the whole vector,
+    a ragged number of them, odd and even lengths; within the summation
+    bound on random data and bit-exact on integers."""
+    n = 300_007
+    ind = _uniform_indices(n, len_b, 101 + len_b % 7)
+    b = S.vector(len_b, 102)
+    a = S.vector(n, 103) if op == "SCP" else None
+    s, npart = run(op, "IND_TMA", n, b, a, 1, ind)
+    ref, abs_sum = O.gather_sum_exact(op, "IND", n, b, a=a, ind=ind)
+    assert abs(s - ref) <= bound(n, npart, abs_sum), (s, ref)
+    bi = S.int_vector(len_b, 104, 1000)
+    ai = S.int_vector(n, 105, 1000) if op == "SCP" else None
+    assert run(op, "IND_TMA", n, bi, ai, 1, ind)[0] == O.gather_sum(op, "IND", n, bi, a=ai, ind=ind)
+
+
+def test_gather_tma_bad_index_is_skipped_and_reported():
+    n = 10_000
+    b = S.int_vector(n + 1, 111, 1000)
+    ind = np.arange(n, dtype=np.int32)
+    ind[17] = -5
+    ind[9_000] = n + 1
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s, _ = run("ADD", "IND_TMA", n, b, ind=ind, status=status)
+    keep = np.ones(n, bool)
+    keep[[17, 9_000]] = False
+    assert s == float(b[:n][keep].sum())
+    assert int(host(status)[0]) == -1  # GBSP_ERR_ARG
+
+
+def test_stage_sweep_closed_form():
+    """Every CTA streams the vector's whole 16-byte blocks through shared
+    memory in 32 KB chunks and adds the first double of each: the sum of
+    b[4096 c] over the chunks; all CTAs agree and no wait gives up."""
+    from paper_0910_4836_gb300.gather import stage_sweep
+    for len_b in (1, 2, 4097, 1_000_001):
+        b = S.int_vector(len_b, 121, 1000)
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        out = host(stage_sweep(dev(b), status=status))
+        whole = (len_b * 8) // 16 * 16
+        want = float(sum(b[4096 * c] for c in range((whole + 32767) // 32768)))
+        assert np.all(out == want), (len_b, out[:3], want)
+        assert int(host(status)[0]) == 0
