@@ -308,7 +308,8 @@ def candidates(M, A, x, only=None):
         name = f"SELL symmetric w={w} u={u}"
         if want(name):
             G = M.to_jds("SELL", "symmetric", window=w, unroll=u)
-            out.append(Cand(name, G, G.permute(x), "permuted", jds_method_bytes(A, G.n_blocks + 1), 4 * N))
+            out.append(Cand(name, G, G.permute(x), "permuted", jds_method_bytes(A, G.n_blocks + 1),
+                            4 * N))
     for w, u in ((128, 4), (64, 4)):
         name = f"SELL row_only w={w} u={u} original"
         if want(name) or want(f"SELL row_only w={w} u={u} mixed"):
@@ -317,7 +318,8 @@ def candidates(M, A, x, only=None):
             if want(name):
                 out.append(Cand(name, G, x, "original", mb, 8 * N))
             if w == 128 and want(f"SELL row_only w={w} u={u} mixed"):
-                out.append(Cand(f"SELL row_only w={w} u={u} mixed", G, x, "mixed", mb, 4 * N, credited=False))
+                out.append(Cand(f"SELL row_only w={w} u={u} mixed", G, x, "mixed", mb, 4 * N,
+                                credited=False))
     for w, u in ((64, 2), (128, 4)):
         name = f"PSELL symmetric w={w} u={u}"
         if want(name):
@@ -528,10 +530,10 @@ def run_ours(args):
                          "algorithmic_bytes": alg,
                          "algorithmic_bytes_formula": "12 nnz + 4 (pointer entries) + 8 N_c + 8 N",
                          "format_overhead_bytes": step_c.overhead,
-                         "format_overhead": ("row lengths 4N" + (" + permutation 4N read by the fused basis change"
-                                                                  if step_c.basis == "original" and
-                                                                  not kname.startswith("CRS") else ""))
-                         if not kname.startswith("CRS") else "none",
+                         "format_overhead": ("SELL row lengths 4N" if kname.startswith("SELL") else
+                                             "none" if kname.startswith("CRS") else "JDS-family extras") +
+                                            (" + permutation 4N read by the fused basis change"
+                                             if step_c.basis == "original" and not kname.startswith("CRS") else ""),
                          "peak_source": f"{peak_kind} hbm_gbs (burst)",
                          "kernel_source_hash": h,
                          "cold_ms": round(cold_ms, 5),

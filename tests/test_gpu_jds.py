@@ -390,6 +390,13 @@ def test_full_size_step_kernels(cfg):
     assert_close64(y, ref, s, f"config {cfg} SELL w=128 u=4")
     G.stage_x(12, 32)
     assert np.array_equal(host(G.spmv_original(xd)), y)
+    del G
+    # the bench's step: the symmetric permutation, x and y in the permuted basis
+    Gs = M.to_jds("SELL", "symmetric", window=128, unroll=4)
+    perm = host(Gs.perm)
+    yp = host(Gs.spmv(Gs.permute(xd)))
+    assert_close64(yp, ref[perm], s[perm], f"config {cfg} SELL symmetric w=128 u=4, permuted basis")
+    del Gs
     J = M.to_jds("NUJDS", "symmetric", unroll=2)
     assert_close64(host(J.spmv_original(xd)), ref, s, f"config {cfg} NUJDS u=2")
 
