@@ -867,6 +867,7 @@ def batched_speedups(dev, time_launches):
             X.uniform_(-1, 1)
         g = bt.graph()
         t_batch = statistics.median(time_launches(g.replay, 20))
+        t_cold = statistics.median(cold_times(g.replay, dev, 10))
         plain = [CRSMatrix(h.row_ptr, h.col, h.val, h.n_cols) if isinstance(h, CRSMatrix)
                  else CRSMatrix.from_host(m, device=dev, dtype=dtype) for h, m in zip(handles, mats)]
         for P in plain:
@@ -885,7 +886,7 @@ def batched_speedups(dev, time_launches):
         flops = sum(2.0 * m.nnz * k for m, k in zip(mats, ks))
         nw, grid = bt.info()
         out[f"{'f64' if dtype == torch.float64 else 'f32'}_k{kmode}"] = {
-            "batched_ms": round(t_batch, 4), "plain_ms": round(t_plain, 4),
+            "batched_ms": round(t_batch, 4), "batched_cold_ms": round(t_cold, 4), "plain_ms": round(t_plain, 4),
             "speedup": round(t_plain / t_batch, 2), "batched_gflops": round(flops / (t_batch * 1e-3) / 1e9, 1),
             "launches_plain": int(sum(ks)), "work_items": nw, "ctas": grid,
             "jds_items": sum(1 for h in handles if not isinstance(h, CRSMatrix))}

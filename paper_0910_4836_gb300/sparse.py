@@ -67,7 +67,9 @@ class _Product(_Handle):
 
     def spmm(self, X: torch.Tensor, out: torch.Tensor | None = None, accumulate: bool = False,
              transpose: bool = False, basis: int = L.BASIS_PERMUTED, stream=None) -> torch.Tensor:
-        """Y = op(A) X for row-major X (n x k); a 1-D X is a single vector."""
+        """Y = op(A) X for row-major X (n x k); a 1-D X is a single vector.
+        For k >= 8 a CRS handle is the faster format (its lanes cover one
+        row's right-hand sides); JDS-family handles gather k values a row."""
         if not X.is_cuda or X.dtype != self.dtype:
             raise ValueError(f"X must be a CUDA tensor of dtype {self.dtype}")
         if X.dim() == 1 or X.stride(-1) != 1:
