@@ -302,6 +302,8 @@ def candidates(M, A, x, only=None):
     want = lambda name: only is None or name.startswith(only) or only.startswith(name)
     for l, r in ((4, 4), (8, 2), (16, 2)):
         out.append(Cand(f"CRS vector l{l} r{r}", M, x, "original", crs_b, how=("vector", l, r)))
+    for l, r in ((2, 4), (2, 8), (4, 4), (4, 8), (1, 8)):
+        out.append(Cand(f"CRS runs l{l} r{r}", M, x, "original", crs_b, how=("runs", l, r)))
     for t in (1024, 2048):
         out.append(Cand(f"CRS tiled {t}", M, x, "original", crs_b, how=("tiled", t)))
     for w, u in ((128, 4), (64, 4), (256, 4), (128, 2)):
@@ -349,8 +351,8 @@ def candidates(M, A, x, only=None):
 
 
 def configure(H, how):
-    if how[0] == "vector":
-        H.set_kernel("vector", lanes=how[1], rows_per_warp=how[2])
+    if how[0] in ("vector", "runs"):
+        H.set_kernel(how[0], lanes=how[1], rows_per_warp=how[2])
     elif how[0] == "tiled":
         H.prepare_tiled(how[1])
     elif how[0] == "jds":
@@ -816,6 +818,10 @@ def zipf_candidates(M, A, x, y):
     M.set_kernel("vector", lanes=4, rows_per_warp=4)
     runs.append(("CRS vector l4 r4", lambda: M.spmv(x, out=y), crs_b))
     from paper_0910_4836_gb300 import CRSMatrix
+    for l, r in ((2, 8), (4, 4)):
+        Mr = CRSMatrix(M.row_ptr, M.col, M.val, A.n_cols)
+        Mr.set_kernel("runs", lanes=l, rows_per_warp=r)
+        runs.append((f"CRS runs l{l} r{r}", lambda Mr=Mr: Mr.spmv(x, out=y), crs_b))
     M2 = CRSMatrix(M.row_ptr, M.col, M.val, A.n_cols)
     M2.prepare_tiled(1024)
     runs.append(("CRS tiled 1024", lambda: M2.spmv(x, out=y), crs_b))

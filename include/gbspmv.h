@@ -119,13 +119,24 @@ typedef enum { GBSP_ACC_PLAIN = 0, GBSP_ACC_COMPENSATED = 1 } gbsp_accum;
  * shared memory with bulk asynchronous copies (a producer warp, mbarrier
  * stages) and sums each row with one thread, rows sorted by length inside
  * the tile so that the lanes of a warp do equal work; needs
- * gbsp_crs_prepare.  AUTO picks from the row-length mean. */
-typedef enum { GBSP_KERNEL_AUTO = 0, GBSP_KERNEL_VECTOR = 1, GBSP_KERNEL_TILED = 2 } gbsp_kernel;
+ * gbsp_crs_prepare.  RUNS: like VECTOR, a group of `lanes` threads owns
+ * `rows_per_warp` consecutive rows, but it strides through their entries as
+ * one contiguous run (CRS stores consecutive rows back to back), so a group
+ * issues one FMA slot per entry of the run instead of one per entry of its
+ * longest row; lanes in {1, 2, 4, 8}, rows_per_warp in {4, 8} and at least
+ * `lanes`.  AUTO picks from the row-length mean. */
+typedef enum {
+    GBSP_KERNEL_AUTO = 0,
+    GBSP_KERNEL_VECTOR = 1,
+    GBSP_KERNEL_TILED = 2,
+    GBSP_KERNEL_RUNS = 3
+} gbsp_kernel;
 
 typedef struct {
     int32_t kernel;        /* gbsp_kernel */
-    int32_t lanes;         /* VECTOR: 1, 2, 4, 8, 16 or 32 (0 = auto) */
-    int32_t rows_per_warp; /* VECTOR: rows per lane group handled together, 1..8 (0 = auto) */
+    int32_t lanes;         /* VECTOR: 1, 2, 4, 8, 16 or 32; RUNS: 1, 2, 4 or 8 (0 = auto) */
+    int32_t rows_per_warp; /* VECTOR: rows per lane group handled together, 1, 2 or 4;
+                              RUNS: 4 or 8 (0 = auto) */
     int32_t tile;          /* TILED: merge items (rows + entries) per tile, 1024 or 2048 (0 = auto) */
     int32_t rhs_tile;      /* SpMM: right-hand sides handled per pass, 1..16 (0 = auto) */
     int32_t accum;         /* gbsp_accum (FP32 handles) */

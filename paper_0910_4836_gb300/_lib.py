@@ -27,7 +27,7 @@ PERM = {"symmetric": 0, "row_only": 1}
 OP_N, OP_T = 0, 1
 BASIS_PERMUTED, BASIS_ORIGINAL = 0, 1
 ACC_PLAIN, ACC_COMPENSATED = 0, 1
-KERNELS = {"auto": 0, "vector": 1, "tiled": 2}
+KERNELS = {"auto": 0, "vector": 1, "tiled": 2, "runs": 3}
 
 
 class KernelOpts(ctypes.Structure):

@@ -139,14 +139,21 @@ gbsp_status gbsp_crs_validate(gbsp_handle crs, int32_t *d_status, void *stream) 
 
 gbsp_status gbsp_set_kernel(gbsp_handle h, const gbsp_kernel_opts *o) {
     if (!h || !o) return arg_error("gbsp_set_kernel: NULL argument");
-    if (o->kernel < 0 || o->kernel > GBSP_KERNEL_TILED) return arg_error("gbsp_set_kernel: bad kernel");
+    if (o->kernel < 0 || o->kernel > GBSP_KERNEL_RUNS) return arg_error("gbsp_set_kernel: bad kernel");
     if (o->lanes != 0 && (o->lanes < 1 || o->lanes > 32 || (o->lanes & (o->lanes - 1))))
         return arg_error("gbsp_set_kernel: lanes must be 1, 2, 4, 8, 16 or 32");
-    if (o->rows_per_warp != 0 && o->rows_per_warp != 1 && o->rows_per_warp != 2 &&
-        o->rows_per_warp != 4)
+    if (o->kernel == GBSP_KERNEL_RUNS) {
+        if (o->lanes > 8) return arg_error("gbsp_set_kernel: RUNS lanes must be 1, 2, 4 or 8");
+        if (o->rows_per_warp != 0 && o->rows_per_warp != 4 && o->rows_per_warp != 8)
+            return arg_error("gbsp_set_kernel: RUNS rows_per_warp must be 4 or 8");
+        const int l = o->lanes ? o->lanes : 4, r = o->rows_per_warp ? o->rows_per_warp : (l > 4 ? 8 : 4);
+        if (r < l) return arg_error("gbsp_set_kernel: RUNS needs rows_per_warp >= lanes");
+    } else if (o->rows_per_warp != 0 && o->rows_per_warp != 1 && o->rows_per_warp != 2 &&
+               o->rows_per_warp != 4) {
         return arg_error("gbsp_set_kernel: rows_per_warp must be 1, 2 or 4");
-    if (h->kind == KIND_JDS && o->kernel == GBSP_KERNEL_TILED)
-        return arg_error("gbsp_set_kernel: TILED is a CRS kernel");
+    }
+    if (h->kind == KIND_JDS && (o->kernel == GBSP_KERNEL_TILED || o->kernel == GBSP_KERNEL_RUNS))
+        return arg_error("gbsp_set_kernel: TILED and RUNS are CRS kernels");
     if (o->tile != 0 && o->tile != 1024 && o->tile != 2048)
         return arg_error("gbsp_set_kernel: tile must be 1024 or 2048");
     if (o->rhs_tile != 0 && (o->rhs_tile < 1 || o->rhs_tile > 32))
@@ -156,8 +163,14 @@ gbsp_status gbsp_set_kernel(gbsp_handle h, const gbsp_kernel_opts *o) {
     if (o->kernel == GBSP_KERNEL_TILED && !h->tile_rows)
         return arg_error("gbsp_set_kernel: TILED needs gbsp_crs_prepare first");
     if (o->kernel != 0) h->kopt.kernel = o->kernel;
-    if (o->lanes != 0) h->kopt.lanes = o->lanes;
-    if (o->rows_per_warp != 0) h->kopt.rows_per_warp = o->rows_per_warp;
+    if (o->kernel == GBSP_KERNEL_RUNS) {
+        // every field of the pair is RUNS's own: never a VECTOR leftover
+        h->kopt.lanes = o->lanes ? o->lanes : 4;
+        h->kopt.rows_per_warp = o->rows_per_warp ? o->rows_per_warp : (h->kopt.lanes > 4 ? 8 : 4);
+    } else {
+        if (o->lanes != 0) h->kopt.lanes = o->lanes;
+        if (o->rows_per_warp != 0) h->kopt.rows_per_warp = o->rows_per_warp;
+    }
     if (o->rhs_tile != 0) h->kopt.rhs_tile = o->rhs_tile;
     h->kopt.accum = o->accum;
     if (o->kernel == GBSP_KERNEL_AUTO) crs_default_opts(*h);

@@ -158,6 +158,111 @@ crs_vector_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
     }
 }
 
+// Park a lane's running sum in its row's slot.  Indices are compile-time
+// after unrolling, so the slots stay in registers (selects, no FP64 work).
+template <int VM, int R>
+__device__ __forceinline__ void park(Acc<VM> (&part)[R], int cur, const Acc<VM> &acc) {
+#pragma unroll
+    for (int m = 0; m < R; ++m)
+        if (m == cur) part[m] = acc;
+}
+
+// RUNS: the R rows of a lane group are consecutive, so CRS stores their
+// entries as one contiguous run, and the group's L lanes stride through that
+// whole run (lane l takes run entries l, l+L, ...) instead of through each
+// row up to the longest row's length.  A lane keeps one running FMA chain
+// and parks it in the row's slot when its next entry lies in a later row
+// (each row is one stretch of the run, so a slot is written once); the
+// slots are then combined over the group by the reduce-scatter, after which
+// lane l holds rows (R/L) l .. (R/L) l + R/L - 1.  FP64 lane-slots per warp:
+// 32 x the longest group run / L, plus R (1 - 1/L) additions per lane, where
+// VECTOR pays R x 32 x the longest row / L.  U entries per lane are loaded
+// and gathered before any product is formed (U gathers in flight).
+template <int VM, int L, int R>
+__global__ void __launch_bounds__(kThreads)
+crs_runs_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
+                const int32_t *__restrict__ col, const typename ValT<VM>::T *__restrict__ val,
+                const typename ValT<VM>::T *__restrict__ x, int64_t ldx,
+                typename ValT<VM>::T *__restrict__ y, int64_t ldy, int accumulate) {
+    typedef typename ValT<VM>::T T;
+    static_assert(R >= L && R % L == 0, "a group's rows must divide over its lanes");
+    constexpr int G = 32 / L;
+    constexpr int RW = G * R;
+    constexpr int U = 4;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / L, gl = lane % L;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * RW; base < n_rows; base += nwarp * RW) {
+        const int64_t rg = base + (int64_t)grp * R;
+        int b[R + 1];
+#pragma unroll
+        for (int i = 0; i <= R; ++i) b[i] = __ldg(row_ptr + min(rg + i, n_rows));
+        int longest = 0;
+#pragma unroll
+        for (int i = 0; i < R; ++i) longest = max(longest, b[i + 1] - b[i]);
+        if (__reduce_max_sync(0xffffffffu, (unsigned)longest) > (unsigned)kLongRow) {
+            crs_warp_rows<VM>(base, min((int64_t)RW, n_rows - base), row_ptr, col, val, x, ldx, y, ldy, accumulate);
+            continue;
+        }
+        Acc<VM> part[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) part[i].init();
+        Acc<VM> acc;
+        acc.init();
+        int cur = 0;
+        const int k0 = b[0], n = b[R] - b[0];
+        for (int j = gl; j < n; j += U * L) {
+            int c[U];
+            T v[U], xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool ok = j + u * L < n;
+                c[u] = ok ? __ldg(col + k0 + j + u * L) : -1;
+                v[u] = ok ? __ldg(val + k0 + j + u * L) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? ld_vec(x + (int64_t)c[u] * ldx) : T(0);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (c[u] >= 0) {
+                    const int k = k0 + j + u * L;
+                    int i = 0;
+#pragma unroll
+                    for (int m = 1; m < R; ++m) i += k >= b[m] ? 1 : 0;
+                    if (i != cur) {
+                        park<VM, R>(part, cur, acc);
+                        acc.init();
+                        cur = i;
+                    }
+                    acc.add(v[u], xv[u]);
+                }
+            }
+        }
+        park<VM, R>(part, cur, acc);
+#pragma unroll
+        for (int o = L / 2, h = R / 2; o > 0; o >>= 1, h >>= 1) {
+            const bool up = (gl & o) != 0;
+#pragma unroll
+            for (int k = 0; k < h; ++k) {
+                Acc<VM> send = up ? part[k] : part[k + h];
+                Acc<VM> keep = up ? part[k + h] : part[k];
+                keep.merge_shfl_xor(send, o);
+                part[k] = keep;
+            }
+        }
+        constexpr int Q = R / L;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int64_t r = rg + (int64_t)Q * gl + q;
+            if (r < n_rows) {
+                if (accumulate) part[q].add_value(y[r * ldy]);
+                y[r * ldy] = part[q].result();
+            }
+        }
+    }
+}
+
 template <int VM, int KT>
 __global__ void __launch_bounds__(kThreads)
 crs_spmm_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
@@ -360,6 +465,28 @@ static void launch_vector(const Mat &A, const VecArgs &v, cudaStream_t s) {
     }
 }
 
+template <int VM, int L, int R>
+static void launch_runs_LR(const Mat &A, const VecArgs &v, cudaStream_t s) {
+    typedef typename ValT<VM>::T T;
+    const int grid = (int)limit_grid(grid_for(ceil_div(A.n_rows, (32 / L) * R)), A.grid_limit);
+    crs_runs_kernel<VM, L, R><<<grid, kThreads, 0, s>>>(A.n_rows, A.row_ptr, A.col, static_cast<const T *>(A.val),
+                                                        static_cast<const T *>(v.x), v.ldx,
+                                                        static_cast<T *>(v.y), v.ldy, v.accumulate);
+}
+
+// (lanes, rows) pairs of RUNS; gbsp_set_kernel admits exactly these.
+template <int VM>
+static void launch_runs(const Mat &A, const VecArgs &v, cudaStream_t s) {
+    const int L = A.kopt.lanes, R = A.kopt.rows_per_warp;
+    if (L == 1 && R == 4) launch_runs_LR<VM, 1, 4>(A, v, s);
+    else if (L == 1) launch_runs_LR<VM, 1, 8>(A, v, s);
+    else if (L == 2 && R == 4) launch_runs_LR<VM, 2, 4>(A, v, s);
+    else if (L == 2) launch_runs_LR<VM, 2, 8>(A, v, s);
+    else if (L == 4 && R == 4) launch_runs_LR<VM, 4, 4>(A, v, s);
+    else if (L == 4) launch_runs_LR<VM, 4, 8>(A, v, s);
+    else launch_runs_LR<VM, 8, 8>(A, v, s);
+}
+
 template <int VM>
 static void launch_spmm(const Mat &A, const VecArgs &v, cudaStream_t s) {
     typedef typename ValT<VM>::T T;
@@ -430,7 +557,11 @@ gbsp_status crs_launch(const Mat &A, const VecArgs &v, cudaStream_t s) {
                    : (A.kopt.accum == GBSP_ACC_COMPENSATED ? VM_F32C : VM_F32);
     if (v.k == 1 && A.kopt.kernel == GBSP_KERNEL_TILED && A.tile_rows != nullptr)
         return crs_tiled_launch(A, v, s);
-    if (v.k == 1) {
+    if (v.k == 1 && A.kopt.kernel == GBSP_KERNEL_RUNS) {
+        if (vm == VM_F64) launch_runs<VM_F64>(A, v, s);
+        else if (vm == VM_F32) launch_runs<VM_F32>(A, v, s);
+        else launch_runs<VM_F32C>(A, v, s);
+    } else if (v.k == 1) {
         if (vm == VM_F64) launch_vector<VM_F64>(A, v, s);
         else if (vm == VM_F32) launch_vector<VM_F32>(A, v, s);
         else launch_vector<VM_F32C>(A, v, s);

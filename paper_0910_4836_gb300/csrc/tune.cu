@@ -9,6 +9,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "internal.cuh"
@@ -79,6 +80,14 @@ static std::vector<Cand> candidates(const Mat &A, int k) {
                     c.k.rows_per_warp = r;
                     out.push_back(c);
                 }
+            for (auto lr : {std::make_pair(1, 8), std::make_pair(2, 4), std::make_pair(2, 8),
+                            std::make_pair(4, 4), std::make_pair(4, 8), std::make_pair(8, 8)}) {
+                Cand c = base;
+                c.k.kernel = GBSP_KERNEL_RUNS;
+                c.k.lanes = lr.first;
+                c.k.rows_per_warp = lr.second;
+                out.push_back(c);
+            }
             if (A.tile_rows) {
                 Cand c = base;
                 c.k.kernel = GBSP_KERNEL_TILED;

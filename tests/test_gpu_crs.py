@@ -11,6 +11,7 @@ from paper_0910_4836_gb300 import synth as S
 pytestmark = pytest.mark.gpu
 
 VECTOR_OPTS = [(l, r) for l in (1, 2, 4, 8, 16, 32) for r in (1, 2, 4)]
+RUNS_OPTS = [(1, 4), (1, 8), (2, 4), (2, 8), (4, 4), (4, 8), (8, 8)]
 TILES = (1024, 2048)
 
 
@@ -24,6 +25,8 @@ def kernels(M):
     """Yield (name, configure) for every CRS kernel option."""
     for l, r in VECTOR_OPTS:
         yield f"vector_l{l}_r{r}", lambda M=M, l=l, r=r: M.set_kernel("vector", lanes=l, rows_per_warp=r)
+    for l, r in RUNS_OPTS:
+        yield f"runs_l{l}_r{r}", lambda M=M, l=l, r=r: M.set_kernel("runs", lanes=l, rows_per_warp=r)
     for t in TILES:
         yield f"tiled_{t}", lambda M=M, t=t: M.prepare_tiled(t)
 
@@ -124,11 +127,12 @@ def configure(M, name, compensated=None):
             M.prepare_tiled(int(name.split("_")[1]))
         M.set_kernel("tiled", compensated=compensated)
     else:
-        l, r = name.split("_")[1:]
-        M.set_kernel("vector", lanes=int(l[1:]), rows_per_warp=int(r[1:]), compensated=compensated)
+        kind, l, r = name.split("_")
+        M.set_kernel(kind, lanes=int(l[1:]), rows_per_warp=int(r[1:]), compensated=compensated)
 
 
-KERNEL_NAMES = [f"vector_l{l}_r{r}" for l, r in VECTOR_OPTS] + [f"tiled_{t}" for t in TILES]
+KERNEL_NAMES = ([f"vector_l{l}_r{r}" for l, r in VECTOR_OPTS] + [f"runs_l{l}_r{r}" for l, r in RUNS_OPTS]
+                + [f"tiled_{t}" for t in TILES])
 
 
 def test_fp32_plain_and_compensated():
@@ -188,6 +192,14 @@ def test_argument_errors():
     x = dev(S.vector(40, 1))
     with pytest.raises(GbspError):
         M.set_kernel("vector", lanes=3)
+    for l, r in ((16, 8), (8, 4), (2, 2), (4, 1)):
+        with pytest.raises(GbspError):
+            M.set_kernel("runs", lanes=l, rows_per_warp=r)
+    with pytest.raises(GbspError):
+        M.set_kernel("vector", rows_per_warp=8)  # a RUNS shape only
+    M.set_kernel("vector", lanes=16, rows_per_warp=2)
+    M.set_kernel("runs")  # the pair is RUNS's own default, not VECTOR's leftover
+    assert (M.kernel_opts()["lanes"], M.kernel_opts()["rows_per_warp"]) == (4, 4)
     with pytest.raises(GbspError):
         M.spmv(dev(S.vector(50, 1)), transpose=True)  # no transpose attached
     with pytest.raises(ValueError):
@@ -208,6 +220,25 @@ def test_argument_errors():
         B.prepare_tiled(1024)
 
 
+def test_unaligned_arrays():
+    """Arrays aligned only to their element size (val 8-byte, col 4-byte
+    aligned: borrowed slices of larger buffers) give the same products."""
+    from paper_0910_4836_gb300 import CRSMatrix
+    A = S.zipf_rows(60_000, 21, lmax=3000)
+    x = S.vector(A.n_cols, 21)
+    ref, s = O.crs_spmv_exact(A, x)
+    val_buf = torch.zeros(A.nnz + 1, dtype=torch.float64, device="cuda")
+    val_buf[1:] = dev(A.val)
+    col_buf = torch.zeros(A.nnz + 1, dtype=torch.int32, device="cuda")
+    col_buf[1:] = dev(A.col, torch.int32)
+    xd = dev(x)
+    for vb, cb in ((val_buf[1:], dev(A.col, torch.int32)), (dev(A.val), col_buf[1:]), (val_buf[1:], col_buf[1:])):
+        B = CRSMatrix(dev(A.row_ptr, torch.int32), cb, vb, A.n_cols)
+        for l, r in VECTOR_OPTS:
+            B.set_kernel("vector", lanes=l, rows_per_warp=r)
+            assert_close64(host(B.spmv(xd)), ref, s, f"unaligned vector l{l} r{r}")
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("cfg", [1, 2, 4])
 def test_full_size_configs(cfg):
@@ -218,10 +249,13 @@ def test_full_size_configs(cfg):
     ref, s = O.crs_spmv_exact(A, x)
     M = crs(A)
     xd = dev(x)
-    for name in ("tiled", "vector"):
+    for name in ("tiled", "vector", "vector l4 r4", "runs l2 r8", "runs l4 r4"):
         if name == "tiled":
             M.prepare_tiled(2048)
-        else:
+        elif name == "vector":
             M.set_kernel("vector", lanes=8 if cfg != 4 else 16, rows_per_warp=2)
+        else:
+            kind, l, r = name.split()
+            M.set_kernel(kind, lanes=int(l[1:]), rows_per_warp=int(r[1:]))
         y = host(M.spmv(xd))
         assert_close64(y, ref, s, f"config {cfg} {name}")
