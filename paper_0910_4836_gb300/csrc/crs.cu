@@ -9,8 +9,12 @@
 // butterfly of warp shuffles; when a group holds as many rows as it has
 // lanes, by a reduce-scatter that leaves each lane one row's total (same
 // tree, fewer FP64 additions: on GB300 each one is a full-rate-limited FP64
-// instruction).  A warp whose rows include one longer than kLongRow works
-// on its rows one at a time with the whole warp instead.
+// instruction).  In a warp whose rows include one longer than kLongRow, the
+// groups take their rows one at a time and the long rows are then summed by
+// the whole warp.
+//
+// RUNS: as VECTOR, but a group's rows are consecutive and its lanes stride
+// through their entries as one run (below).
 //
 // SpMM: lanes over right-hand sides -- a group of KT lanes owns one row and
 // lane c accumulates column c of the RHS tile, so each entry (val, col) is
@@ -23,48 +27,119 @@
 namespace gbsp {
 
 constexpr int kThreads = 256;
-// row length beyond which a VECTOR warp gives every row all 32 lanes
+// Row length beyond which a row is summed by the whole warp instead of its
+// lane group: VECTOR (lanes run to the group's longest row) and RUNS (whose
+// groups share one run, so a long row would hold its whole group).
 constexpr int kLongRow = 512;
+constexpr int kRunsLongRow = 64;
 
-// Rows [base, base + n) with the whole warp on each row in turn: lanes
-// stride through the row four loads deep, then a full-warp sum.  Kept out of
-// line so that it does not raise the register count of the common path.
+// Flagged rows with the whole warp on each row in turn.  Every lane passes
+// its group's mask (bit i: row first + i * step is long; only `leader`
+// lanes' masks are read); lanes stride through a row four loads deep, then
+// a full-warp sum.  Kept out of line so that it does not raise the register
+// count of the common path.
 template <int VM>
-__device__ __noinline__ void crs_warp_rows(int64_t base, int64_t n, const int32_t *__restrict__ row_ptr,
-                                           const int32_t *__restrict__ col,
-                                           const typename ValT<VM>::T *__restrict__ val,
-                                           const typename ValT<VM>::T *__restrict__ x, int64_t ldx,
-                                           typename ValT<VM>::T *__restrict__ y, int64_t ldy, int accumulate) {
+__device__ __forceinline__ void crs_warp_long_rows(bool leader, unsigned mask, int64_t first, int64_t step,
+                                                const int32_t *__restrict__ row_ptr,
+                                                const int32_t *__restrict__ col,
+                                                const typename ValT<VM>::T *__restrict__ val,
+                                                const typename ValT<VM>::T *__restrict__ x, int64_t ldx,
+                                                typename ValT<VM>::T *__restrict__ y, int64_t ldy, int accumulate) {
     typedef typename ValT<VM>::T T;
     const int lane = threadIdx.x & 31;
-    for (int64_t q = 0; q < n; ++q) {
-        const int64_t r = base + q;
-        const int s0 = __ldg(row_ptr + r), s1 = __ldg(row_ptr + r + 1);
+    unsigned todo = __ballot_sync(0xffffffffu, leader && mask != 0);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        unsigned m = __shfl_sync(0xffffffffu, mask, src);
+        const int64_t f = __shfl_sync(0xffffffffu, first, src);
+        while (m) {
+            const int64_t r = f + (int64_t)(__ffs(m) - 1) * step;
+            m &= m - 1;
+            const int s0 = __ldg(row_ptr + r), s1 = __ldg(row_ptr + r + 1);
+            Acc<VM> a;
+            a.init();
+            for (int j = s0 + lane; j < s1; j += 4 * 32) {
+                int c[4];
+                T v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool ok = j + 32 * u < s1;
+                    c[u] = ok ? __ldg(col + j + 32 * u) : -1;
+                    v[u] = ok ? __ldg(val + j + 32 * u) : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (c[u] >= 0) a.add(v[u], ld_vec(x + (int64_t)c[u] * ldx));
+            }
+            group_reduce<32, VM>(a);
+            if (lane == 0) {
+                if (accumulate) a.add_value(y[r * ldy]);
+                y[r * ldy] = a.result();
+            }
+        }
+    }
+}
+
+// The step of a warp that holds a very long row (heavy-tailed row lengths),
+// for VECTOR and RUNS alike: group g's rows are first_g + i step, i < R.
+// Rows up to `thr` entries are summed one at a time by their group's L lanes
+// (four loads in flight per lane, then the group's butterfly); longer rows,
+// which would keep their group busy long after the rest of the warp is done,
+// are then summed by the whole warp.  Out of line, and light on registers,
+// so that the common step keeps its own.
+template <int VM, int L>
+__device__ __noinline__ void crs_step_with_long_rows(int R, int64_t first, int64_t step, int thr, int64_t n_rows,
+                                                     const int32_t *__restrict__ row_ptr,
+                                                     const int32_t *__restrict__ col,
+                                                     const typename ValT<VM>::T *__restrict__ val,
+                                                     const typename ValT<VM>::T *__restrict__ x, int64_t ldx,
+                                                     typename ValT<VM>::T *__restrict__ y, int64_t ldy,
+                                                     int accumulate) {
+    typedef typename ValT<VM>::T T;
+    const int gl = (threadIdx.x & 31) % L;
+    unsigned lmask = 0;
+#pragma unroll 1
+    for (int i = 0; i < R; ++i) {
+        const int64_t r = first + i * step;
+        int s0 = 0, s1 = 0;
+        if (r < n_rows) {
+            s0 = __ldg(row_ptr + r);
+            s1 = __ldg(row_ptr + r + 1);
+        }
+        if (s1 - s0 > thr) {
+            lmask |= 1u << i;
+            s1 = s0;
+        }
         Acc<VM> a;
         a.init();
-        for (int j = s0 + lane; j < s1; j += 4 * 32) {
+        for (int j = s0 + gl; j < s1; j += 4 * L) {
             int c[4];
             T v[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const bool ok = j + 32 * u < s1;
-                c[u] = ok ? __ldg(col + j + 32 * u) : -1;
-                v[u] = ok ? __ldg(val + j + 32 * u) : T(0);
+                const bool ok = j + L * u < s1;
+                c[u] = ok ? __ldg(col + j + L * u) : -1;
+                v[u] = ok ? __ldg(val + j + L * u) : T(0);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 if (c[u] >= 0) a.add(v[u], ld_vec(x + (int64_t)c[u] * ldx));
         }
-        group_reduce<32, VM>(a);
-        if (lane == 0) {
+        group_reduce<L, VM>(a);
+        if (gl == 0 && r < n_rows && !((lmask >> i) & 1u)) {
             if (accumulate) a.add_value(y[r * ldy]);
             y[r * ldy] = a.result();
         }
     }
+    crs_warp_long_rows<VM>(gl == 0, lmask, first, step, row_ptr, col, val, x, ldx, y, ldy, accumulate);
 }
 
+// The occupancy hint holds the common step at the registers it needs on its
+// own (48 for four rows a group, 40 for fewer): without it, the call to the
+// long-row step raised some shapes to 60.
 template <int VM, int L, int R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, R == 4 ? 5 : 6)
 crs_vector_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
                   const int32_t *__restrict__ col, const typename ValT<VM>::T *__restrict__ val,
                   const typename ValT<VM>::T *__restrict__ x, int64_t ldx,
@@ -90,12 +165,9 @@ crs_vector_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
             }
             len = max(len, k1[i] - k0[i]);
         }
-        // A warp holding a very long row (heavy-tailed row lengths) would
-        // keep its L lanes on that row long after the rest of the grid is
-        // done.  Such a warp instead takes its rows one at a time with all
-        // 32 lanes, four loads in flight per lane, and a full-warp sum.
         if (__reduce_max_sync(0xffffffffu, (unsigned)len) > (unsigned)kLongRow) {
-            crs_warp_rows<VM>(base, min((int64_t)RW, n_rows - base), row_ptr, col, val, x, ldx, y, ldy, accumulate);
+            crs_step_with_long_rows<VM, L>(R, base + grp, G, kLongRow, n_rows, row_ptr, col, val, x, ldx, y, ldy,
+                                              accumulate);
             continue;
         }
         Acc<VM> acc[R];
@@ -172,14 +244,116 @@ __device__ __forceinline__ void park(Acc<VM> (&part)[R], int cur, const Acc<VM> 
 // whole run (lane l takes run entries l, l+L, ...) instead of through each
 // row up to the longest row's length.  A lane keeps one running FMA chain
 // and parks it in the row's slot when its next entry lies in a later row
-// (each row is one stretch of the run, so a slot is written once); the
-// slots are then combined over the group by the reduce-scatter, after which
-// lane l holds rows (R/L) l .. (R/L) l + R/L - 1.  FP64 lane-slots per warp:
-// 32 x the longest group run / L, plus R (1 - 1/L) additions per lane, where
-// VECTOR pays R x 32 x the longest row / L.  U entries per lane are loaded
-// and gathered before any product is formed (U gathers in flight).
+// (each row is one stretch of the run, so a slot is written once; register
+// selects, no FP64 work); the slots are then combined over the group by the
+// reduce-scatter, after which lane l holds rows (R/L) l .. (R/L) l + R/L - 1.
+// FP64 lane-slots per warp: 32 x the longest group run / L, plus R (1 - 1/L)
+// additions per lane, where VECTOR pays R x 32 x the longest row / L.  U
+// entries per lane are loaded and gathered before any product is formed (U
+// gathers in flight).
+constexpr int kRunsU = 4;
+
+// Reduce-scatter of the R row slots over the group's L lanes, then the
+// stores (rows flagged in lmask are not stored).
 template <int VM, int L, int R>
-__global__ void __launch_bounds__(kThreads)
+__device__ __forceinline__ void runs_store(Acc<VM> (&part)[R], int64_t rg, unsigned lmask, int64_t n_rows,
+                                           typename ValT<VM>::T *__restrict__ y, int64_t ldy, int accumulate) {
+    const int gl = (threadIdx.x & 31) % L;
+#pragma unroll
+    for (int o = L / 2, h = R / 2; o > 0; o >>= 1, h >>= 1) {
+        const bool up = (gl & o) != 0;
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            Acc<VM> send = up ? part[k] : part[k + h];
+            Acc<VM> keep = up ? part[k + h] : part[k];
+            keep.merge_shfl_xor(send, o);
+            part[k] = keep;
+        }
+    }
+    constexpr int Q = R / L;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int64_t r = rg + (int64_t)Q * gl + q;
+        if (r < n_rows && !((lmask >> (Q * gl + q)) & 1u)) {
+            if (accumulate) part[q].add_value(y[r * ldy]);
+            y[r * ldy] = part[q].result();
+        }
+    }
+}
+
+// A RUNS step whose warp holds a row longer than kRunsLongRow: such rows are
+// cut out of their group's run (its index skips them: run index j of row i
+// sits at entry j + b_i - p_i, p_i the run length before row i) and summed
+// afterwards by the whole warp.  Out of line, so that the common step keeps
+// its code.
+template <int VM, int L, int R>
+__device__ __noinline__ void runs_step_cut(int64_t rg, int64_t n_rows, const int32_t *__restrict__ row_ptr,
+                                           const int32_t *__restrict__ col,
+                                           const typename ValT<VM>::T *__restrict__ val,
+                                           const typename ValT<VM>::T *__restrict__ x, int64_t ldx,
+                                           typename ValT<VM>::T *__restrict__ y, int64_t ldy, int accumulate) {
+    typedef typename ValT<VM>::T T;
+    constexpr int U = kRunsU;
+    const int gl = (threadIdx.x & 31) % L;
+    int b[R + 1], p[R];  // row pointers; run index of each row's start
+#pragma unroll
+    for (int i = 0; i <= R; ++i) b[i] = __ldg(row_ptr + min(rg + i, n_rows));
+    unsigned lmask = 0;
+    int n = 0;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        p[i] = n;
+        const int li = b[i + 1] - b[i];
+        if (li > kRunsLongRow) lmask |= 1u << i;
+        else n += li;
+    }
+    Acc<VM> part[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) part[i].init();
+    Acc<VM> acc;
+    acc.init();
+    int cur = 0;
+    for (int j = gl; j < n; j += U * L) {
+        int c[U], row[U];
+        T v[U], xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int jj = j + u * L;
+            // the last row starting at or before jj (a cut-out or empty row
+            // starts where the next one does, which then wins)
+            int i = 0, k = jj + b[0];
+#pragma unroll
+            for (int m = 1; m < R; ++m)
+                if (jj >= p[m]) {
+                    i = m;
+                    k = jj + b[m] - p[m];
+                }
+            row[u] = i;
+            const bool ok = jj < n;
+            c[u] = ok ? __ldg(col + k) : -1;
+            v[u] = ok ? __ldg(val + k) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? ld_vec(x + (int64_t)c[u] * ldx) : T(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (c[u] >= 0) {
+                if (row[u] != cur) {
+                    park<VM, R>(part, cur, acc);
+                    acc.init();
+                    cur = row[u];
+                }
+                acc.add(v[u], xv[u]);
+            }
+        }
+    }
+    park<VM, R>(part, cur, acc);
+    runs_store<VM, L, R>(part, rg, lmask, n_rows, y, ldy, accumulate);
+    crs_warp_long_rows<VM>(gl == 0, lmask, rg, 1, row_ptr, col, val, x, ldx, y, ldy, accumulate);
+}
+
+template <int VM, int L, int R>
+__global__ void __launch_bounds__(kThreads, R == 4 ? 5 : 4)
 crs_runs_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
                 const int32_t *__restrict__ col, const typename ValT<VM>::T *__restrict__ val,
                 const typename ValT<VM>::T *__restrict__ x, int64_t ldx,
@@ -188,7 +362,7 @@ crs_runs_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
     static_assert(R >= L && R % L == 0, "a group's rows must divide over its lanes");
     constexpr int G = 32 / L;
     constexpr int RW = G * R;
-    constexpr int U = 4;
+    constexpr int U = kRunsU;
     const int lane = threadIdx.x & 31;
     const int grp = lane / L, gl = lane % L;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -201,8 +375,8 @@ crs_runs_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
         int longest = 0;
 #pragma unroll
         for (int i = 0; i < R; ++i) longest = max(longest, b[i + 1] - b[i]);
-        if (__reduce_max_sync(0xffffffffu, (unsigned)longest) > (unsigned)kLongRow) {
-            crs_warp_rows<VM>(base, min((int64_t)RW, n_rows - base), row_ptr, col, val, x, ldx, y, ldy, accumulate);
+        if (__reduce_max_sync(0xffffffffu, (unsigned)longest) > (unsigned)kRunsLongRow) {
+            runs_step_cut<VM, L, R>(rg, n_rows, row_ptr, col, val, x, ldx, y, ldy, accumulate);
             continue;
         }
         Acc<VM> part[R];
@@ -240,26 +414,7 @@ crs_runs_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
             }
         }
         park<VM, R>(part, cur, acc);
-#pragma unroll
-        for (int o = L / 2, h = R / 2; o > 0; o >>= 1, h >>= 1) {
-            const bool up = (gl & o) != 0;
-#pragma unroll
-            for (int k = 0; k < h; ++k) {
-                Acc<VM> send = up ? part[k] : part[k + h];
-                Acc<VM> keep = up ? part[k + h] : part[k];
-                keep.merge_shfl_xor(send, o);
-                part[k] = keep;
-            }
-        }
-        constexpr int Q = R / L;
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int64_t r = rg + (int64_t)Q * gl + q;
-            if (r < n_rows) {
-                if (accumulate) part[q].add_value(y[r * ldy]);
-                y[r * ldy] = part[q].result();
-            }
-        }
+        runs_store<VM, L, R>(part, rg, 0u, n_rows, y, ldy, accumulate);
     }
 }
 

@@ -73,4 +73,14 @@ def adversarial_matrices():
     out.append(S.small_random(300, 77, 7, density=0.1, empty_rows=0.3))
     out.append(S.small_random(64, 300, 8, density=0.05, empty_rows=0.1))
     out.append(S.zipf_rows(20000, 9, lmax=3000))
+    # lengths on both sides of the kernels' long-row thresholds (64 for
+    # RUNS, 512 for VECTOR) in random order: long rows at every position of
+    # a lane group, several in one warp, next to empty rows
+    pick = np.array([0, 1, 5, 63, 64, 65, 100, 511, 512, 513, 800])
+    lens = pick[S.randint(10, 1, np.arange(3000), 0, len(pick) - 1)]
+    rows = np.repeat(np.arange(3000), lens)
+    t = np.arange(rows.size)
+    pos = t - np.repeat(np.cumsum(lens) - lens, lens)  # position in the row
+    cols = (rows * 37 + pos * 13) % 4000                # distinct within a row
+    out.append(S.from_coo(3000, 4000, rows, cols, S.uniform(10, 3, t, -1, 1), name="long_row_thresholds"))
     return out

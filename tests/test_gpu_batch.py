@@ -104,7 +104,7 @@ def test_autotune_keeps_a_valid_fast_choice():
     M = crs(A)
     M.prepare_tiled(1024)
     opts, ms = M.autotune(1)
-    assert ms > 0 and opts["kernel"] in (1, 2)
+    assert ms > 0 and opts["kernel"] in (1, 2, 3)  # VECTOR, TILED or RUNS
     assert_close64(host(M.spmv(dev(x))), ref, s, f"tuned {opts}")
     J = M.to_jds("JDS", "symmetric")
     jopts, jms = J.autotune(1)

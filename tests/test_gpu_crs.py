@@ -45,7 +45,7 @@ def test_laplace_config0_all_kernels():
         assert np.all(np.abs(y - dense) <= 2 * TOL64 * s)
 
 
-@pytest.mark.parametrize("idx", range(8))
+@pytest.mark.parametrize("idx", range(9))
 def test_adversarial_all_kernels(idx):
     A = adversarial_matrices()[idx]
     x = S.vector(A.n_cols, 10 + idx)

@@ -257,7 +257,7 @@ def test_jds_spmm():
                 assert_close64(Y[:, c], Yref[:, c], Sref[:, c], f"{fmt} k={k} col {c}")
 
 
-@pytest.mark.parametrize("idx", range(8))
+@pytest.mark.parametrize("idx", range(9))
 def test_adversarial(idx):
     A = adversarial_matrices()[idx]
     perm = "symmetric" if A.n_rows == A.n_cols else "row_only"
