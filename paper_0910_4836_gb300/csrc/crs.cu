@@ -471,11 +471,12 @@ crs_spmm_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
 // chunks of 32: lane l takes entry c + l of chunk c, so every col load and
 // dval store is one contiguous warp-wide access.
 //   m = 1 (crs_dval_kernel): kDvalU chunks in flight together (their
-//     gathers are what the kernel waits for); the warp's 32 row pointers sit
-//     one per lane and a lane finds its entry's row by a five-step binary
-//     search over them with shuffles; dval is written evict-first (it is not
-//     read again here), which leaves L2 to the gathered vectors.  HH-like
-//     6M: 285 us against 405 us for one chunk at a time.
+//     gathers are what the kernel waits for); the warp's 32 row starts and
+//     ends sit one per lane, and a lane finds its entry's row from one
+//     warp-wide OR of the rows' start positions in the chunk and one ballot
+//     (no shuffles: a five-step shuffle search per chunk took 42% of the
+//     L1TEX data-pipe wavefronts); dval is written evict-first (it is not
+//     read again here), which leaves L2 to the gathered vectors.
 //   m > 1 (crs_dval_multi_kernel): one chunk at a time, rows found by
 //     stepping forward through the row pointers in shared memory.  With
 //     the loop over t inside, several chunks in flight took 72 registers
@@ -498,21 +499,48 @@ crs_dval_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
         const int32_t e1 = __ldg(row_ptr + min(r0 + 32, n_rows));
         const int32_t eb = __shfl_sync(0xffffffffu, rpl, 0);
         const T *Gw = G + r0 * g_row;
+        // lane i: end of row r0 + i
+        const int32_t rpn = __ldg(row_ptr + min(r0 + lane + 1, n_rows));
         for (int32_t c = eb; c < e1; c += 32 * kDvalU) {
             int32_t cj[kDvalU], rl[kDvalU];
             T d[kDvalU];
 #pragma unroll
             for (int u = 0; u < kDvalU; ++u) {
-                const int32_t e = c + 32 * u + lane;
-                // the last row i (of the warp's 32) with start <= e; every
-                // lane takes part, so the shuffles see the whole warp
-                int lo = 0;
+                const int32_t cb = c + 32 * u;
+                const int32_t e = cb + lane;
+                // Entry e belongs to the last nonempty row starting at or
+                // before it.  Row i marks position max(start_i - cb, 0) of
+                // the 32-entry chunk when it is nonempty there (the row
+                // holding entry cb marks 0; rows ending by cb, empty rows and
+                // rows starting past the chunk mark nothing), so each marked
+                // position has exactly one row.  B: the marked positions;
+                // C: the marking rows.  Both are in increasing order, so
+                // lane e - cb's row is the k-th set bit of C, k the number
+                // of marks at or below its position, less one.
+                const int32_t ds = max(rpl - cb, 0), de = max(rpn - cb, 0);
+                const bool mark = ds < 32 && de > ds;
+                const unsigned B = __reduce_or_sync(0xffffffffu, mark ? 1u << ds : 0u);
+                const unsigned C = __ballot_sync(0xffffffffu, mark);
+                int k = __popc(B & (0xffffffffu >> (31 - lane))) - 1;
+                int r = C ? __ffs(C) - 1 : 0;  // no marks: a chunk past the warp's entries
+                if ((C >> r) & ((C >> r) + 1)) {
+                    // rows without entries among the marking ones: select
+                    // the k-th set bit of C by halving
+                    unsigned m = C;
+                    r = 0;
 #pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const int32_t v = __shfl_sync(0xffffffffu, rpl, lo + step);
-                    if (v <= e) lo += step;
+                    for (int w = 16; w > 0; w >>= 1) {
+                        const int n = __popc(m & ((1u << w) - 1u));
+                        if (n <= k) {
+                            k -= n;
+                            m >>= w;
+                            r += w;
+                        }
+                    }
+                } else {
+                    r += k;  // consecutive marking rows
                 }
-                rl[u] = lo;
+                rl[u] = r;
                 cj[u] = e < e1 ? ld_stream(col + e) : -1;
             }
 #pragma unroll

@@ -107,6 +107,27 @@ def test_dval_and_multi():
     assert np.array_equal(dc.view(np.int64), dm.view(np.int64))
 
 
+@pytest.mark.parametrize("idx", range(9))
+def test_dval_edge_matrices(idx):
+    """The one-step value gradient finds each entry's row from the warp's
+    row starts: empty rows, rows of one entry, rows longer than a warp's
+    chunks, a ragged last block and rectangular shapes, bit for bit."""
+    from gpu_util import adversarial_matrices
+    A = adversarial_matrices()[idx]
+    if A.nnz == 0:
+        return
+    g = S.vector(A.n_rows, 300 + idx)
+    x = S.vector(A.n_cols, 310 + idx)
+    M = crs(A)
+    assert np.array_equal(host(M.dval(dev(g), dev(x))), O.dval(A, g, x)), A.name
+    d0 = S.vector(A.nnz, 320 + idx)
+    d2 = host(M.dval(dev(g), dev(x), out=dev(d0), accumulate=True))
+    rid = A.row_ids()
+    # one fma onto the old value against a product and a sum, each rounded
+    # (|g x|, |d0| <= 1): within half an ulp of 1 plus one ulp of 2
+    np.testing.assert_allclose(d2, d0 + g[rid] * x[A.col], rtol=0, atol=6e-16, err_msg=A.name)
+
+
 def _pattern(A, **kw):
     from paper_0910_4836_gb300.autograd import Pattern
     return Pattern.from_host(A, **kw)
