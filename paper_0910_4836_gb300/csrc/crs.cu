@@ -464,6 +464,41 @@ crs_spmm_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
     }
 }
 
+// The row (0..31, of a warp's 32 rows) of entry cb + lane, for a warp that
+// holds its rows' starts (rs) and ends (re) one per lane; every lane takes
+// part.  An entry belongs to the last nonempty row starting at or before
+// it.  Row i marks position max(start_i - cb, 0) of the 32-entry chunk at
+// cb when it is nonempty there (the row holding entry cb marks 0; rows
+// ending by cb, empty rows and rows starting past the chunk mark nothing),
+// so each marked position has exactly one row.  B: the marked positions,
+// from one warp-wide OR; C: the marking rows, from one ballot.  Both are in
+// increasing order, so the lane's row is the k-th set bit of C, k the
+// number of marks at or below its position, less one: the first marking row
+// plus k when they are consecutive (no empty rows among them), else a
+// popcount halving.  No shuffles: they share the L1TEX data pipe with the
+// loads.  Lanes past the warp's last entry get an unspecified row.
+__device__ __forceinline__ int chunk_row(int32_t rs, int32_t re, int32_t cb, int lane) {
+    const int32_t ds = max(rs - cb, 0), de = max(re - cb, 0);
+    const bool mark = ds < 32 && de > ds;
+    const unsigned B = __reduce_or_sync(0xffffffffu, mark ? 1u << ds : 0u);
+    const unsigned C = __ballot_sync(0xffffffffu, mark);
+    int k = __popc(B & (0xffffffffu >> (31 - lane))) - 1;
+    int r = C ? __ffs(C) - 1 : 0;  // no marks: a chunk past the warp's entries
+    if (!((C >> r) & ((C >> r) + 1))) return r + k;
+    unsigned m = C;
+    r = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const int n = __popc(m & ((1u << w) - 1u));
+        if (n <= k) {
+            k -= n;
+            m >>= w;
+            r += w;
+        }
+    }
+    return r;
+}
+
 // dval_k: d = (accumulate ? dval_k : 0), then d = fma(G[row_k, t], X[col_k, t], d)
 // for t = 0, 1, ..., m-1 (m = 1: g[row] x[col]).  One running sum in a fixed
 // order, so splitting the t range over several calls changes nothing.
@@ -480,7 +515,9 @@ crs_spmm_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
 //   m > 1 (crs_dval_multi_kernel): one chunk at a time, rows found by
 //     stepping forward through the row pointers in shared memory.  With
 //     the loop over t inside, several chunks in flight took 72 registers
-//     and ran slower (27-point stencil, m = 5: 287 us against 249 us).
+//     and ran slower (27-point stencil, m = 5: 287 us against 249 us); so did
+//     the shuffle-free row lookup with one or two chunks in flight and one or
+//     two steps loaded together (294-490 us against 259 us).
 constexpr int kDvalWarps = kThreads / 32;
 constexpr int kDvalU = 4;
 
@@ -508,39 +545,7 @@ crs_dval_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
             for (int u = 0; u < kDvalU; ++u) {
                 const int32_t cb = c + 32 * u;
                 const int32_t e = cb + lane;
-                // Entry e belongs to the last nonempty row starting at or
-                // before it.  Row i marks position max(start_i - cb, 0) of
-                // the 32-entry chunk when it is nonempty there (the row
-                // holding entry cb marks 0; rows ending by cb, empty rows and
-                // rows starting past the chunk mark nothing), so each marked
-                // position has exactly one row.  B: the marked positions;
-                // C: the marking rows.  Both are in increasing order, so
-                // lane e - cb's row is the k-th set bit of C, k the number
-                // of marks at or below its position, less one.
-                const int32_t ds = max(rpl - cb, 0), de = max(rpn - cb, 0);
-                const bool mark = ds < 32 && de > ds;
-                const unsigned B = __reduce_or_sync(0xffffffffu, mark ? 1u << ds : 0u);
-                const unsigned C = __ballot_sync(0xffffffffu, mark);
-                int k = __popc(B & (0xffffffffu >> (31 - lane))) - 1;
-                int r = C ? __ffs(C) - 1 : 0;  // no marks: a chunk past the warp's entries
-                if ((C >> r) & ((C >> r) + 1)) {
-                    // rows without entries among the marking ones: select
-                    // the k-th set bit of C by halving
-                    unsigned m = C;
-                    r = 0;
-#pragma unroll
-                    for (int w = 16; w > 0; w >>= 1) {
-                        const int n = __popc(m & ((1u << w) - 1u));
-                        if (n <= k) {
-                            k -= n;
-                            m >>= w;
-                            r += w;
-                        }
-                    }
-                } else {
-                    r += k;  // consecutive marking rows
-                }
-                rl[u] = r;
+                rl[u] = chunk_row(rpl, rpn, cb, lane);
                 cj[u] = e < e1 ? ld_stream(col + e) : -1;
             }
 #pragma unroll
