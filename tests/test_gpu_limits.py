@@ -89,6 +89,23 @@ def test_index_limit_matrix_all_formats():
     assert torch.equal(M.spmv(x), y), "CRS tiled"
     M.set_kernel("vector", lanes=4, rows_per_warp=4)
     assert torch.equal(M.spmv(x), y), "CRS vector 4x4"
+    # rows of 8..248 entries: most warps take the runs kernel's cut-out step
+    for l, r in ((4, 4), (2, 8)):
+        M.set_kernel("runs", lanes=l, rows_per_warp=r)
+        assert torch.equal(M.spmv(x), y), f"CRS runs {l}x{r}"
+    # the value gradient at the top of the int32 entry range, on the sampled
+    # rows: dval_k = g[row_k] x[col_k], exact for these integers
+    g = S.limit_x(i + 5).to(torch.float64)
+    d = M.dval(g, x)
+    rt = torch.as_tensor(rows, device="cuda")
+    k0 = M.row_ptr[rt].to(torch.int64).cpu().numpy()
+    lens = S.limit_lengths(rows.astype(np.int64))
+    ks = np.concatenate([np.arange(a, a + n) for a, n in zip(k0, lens)])
+    rk = np.repeat(rows.astype(np.int64), lens)
+    jk = ks - np.repeat(k0, lens)
+    want = S.limit_x(rk + 5).astype(np.float64) * S.limit_x(S.limit_cols(rk, jk)).astype(np.float64)
+    assert np.array_equal(host(d[torch.as_tensor(ks, device="cuda")]), want), "dval"
+    del d
     for fmt, perm, kw in (("SELL", "row_only", dict(window=128, unroll=4)),
                           ("NUJDS", "symmetric", dict(unroll=2))):
         G = M.to_jds(fmt, perm, **kw)
