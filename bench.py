@@ -1226,7 +1226,7 @@ def run_analysis(args):
     scaling("NUJDS u=2 (256-thread CTAs)", J, x, (38, 76, 152, 304, 608, 1216, 2432, 0))
     del J
     M.set_kernel("vector", lanes=4, rows_per_warp=4)
-    scaling("CRS vector l4 r4 (256-thread CTAs)", M, x, (38, 76, 152, 304, 608, 1216, 2432, 0))
+    scaling("CRS vector l4 r4 (64-thread CTAs)", M, x, (152, 304, 608, 1216, 2432, 4864, 9728, 0))
     torch.cuda.empty_cache()
 
     strides("CRS", M.col)

@@ -287,7 +287,8 @@ gbsp_status gbsp_jds_build(gbsp_handle crs, const gbsp_jds_opts *opts,
  * CRS VECTOR product kernels at max_ctas (0 removes the cap).  A measurement
  * knob, the GPU counterpart of running the paper's OpenMP kernels on fewer
  * threads (Sect. 5.1, "Intra-socket performance"): the SELL kernel places at most
- * two 1024-thread CTAs per SM, the others up to eight 256-thread CTAs.
+ * two 1024-thread CTAs per SM, the JDS / NUJDS walk up to eight 256-thread
+ * CTAs, CRS VECTOR up to 21 CTAs of 64 threads (two warps, 48 registers).
  * Host-side only.  Errors: GBSP_ERR_ARG for a negative cap. */
 gbsp_status gbsp_set_grid_limit(gbsp_handle h, int32_t max_ctas);
 
