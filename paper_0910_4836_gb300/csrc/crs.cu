@@ -19,6 +19,9 @@
 // SpMM: lanes over right-hand sides -- a group of KT lanes owns one row and
 // lane c accumulates column c of the RHS tile, so each entry (val, col) is
 // read once per tile and X's row slice is read as one contiguous segment.
+//
+// All three run in CTAs of two warps, one CTA per two warps' worth of rows
+// (row_grid below).
 #include <algorithm>
 
 #include "accum.cuh"
@@ -135,9 +138,10 @@ __device__ __noinline__ void crs_step_with_long_rows(int R, int64_t first, int64
     crs_warp_long_rows<VM>(gl == 0, lmask, first, step, row_ptr, col, val, x, ldx, y, ldy, accumulate);
 }
 
-// The occupancy hint holds the common step at the registers it needs on its
-// own (48 for four rows a group, 40 for fewer): without it, the call to the
-// long-row step raised some shapes to 60.
+// The occupancy hint (stated for 256-thread CTAs; the kernel is launched in
+// two-warp CTAs, see row_grid) holds the common step at the registers it
+// needs on its own (48 for four rows a group, 40 for fewer): without it, the
+// call to the long-row step raised some shapes to 60.
 template <int VM, int L, int R>
 __global__ void __launch_bounds__(kThreads, R == 4 ? 5 : 6)
 crs_vector_kernel(int64_t n_rows, const int32_t *__restrict__ row_ptr,
