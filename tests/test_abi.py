@@ -65,6 +65,47 @@ def test_host_side_checks_without_gpu():
     assert L.gbsp_destroy(None) == 0
 
 
+def test_kernel_option_checks_without_gpu():
+    """gbsp_set_kernel's checks are host logic: a handle over placeholder
+    device addresses (never dereferenced on the host) takes every VECTOR and
+    RUNS shape the header admits and refuses the rest, and a RUNS request
+    without a shape gets RUNS's own default, not a VECTOR leftover."""
+    from paper_0910_4836_gb300 import _lib
+    L = _lib.load()
+    h = ctypes.c_void_p()
+    p = ctypes.c_void_p(256)
+    assert L.gbsp_crs_create(64, 64, 0, p, None, None, 0, ctypes.byref(h)) == 0
+    try:
+        def opts(kernel, lanes=0, rows=0):
+            return _lib.KernelOpts(_lib.KERNELS[kernel], lanes, rows, 0, 0, 0)
+
+        def get():
+            o = _lib.KernelOpts()
+            assert L.gbsp_get_kernel(h, ctypes.byref(o)) == 0
+            return o.kernel, o.lanes, o.rows_per_warp
+        for lanes in (1, 2, 4, 8, 16, 32):
+            for rows in (1, 2, 4):
+                assert L.gbsp_set_kernel(h, ctypes.byref(opts("vector", lanes, rows))) == 0
+                assert get() == (1, lanes, rows)
+        for lanes, rows in ((1, 4), (1, 8), (2, 4), (2, 8), (4, 4), (4, 8), (8, 8)):
+            assert L.gbsp_set_kernel(h, ctypes.byref(opts("runs", lanes, rows))) == 0
+            assert get() == (3, lanes, rows)
+        for lanes, rows in ((16, 8), (32, 8), (8, 4), (4, 2), (2, 1), (3, 4)):
+            assert L.gbsp_set_kernel(h, ctypes.byref(opts("runs", lanes, rows))) == -1, (lanes, rows)
+        assert L.gbsp_set_kernel(h, ctypes.byref(opts("vector", 4, 8))) == -1  # a RUNS shape only
+        assert L.gbsp_set_kernel(h, ctypes.byref(opts("vector", 3, 4))) == -1
+        assert L.gbsp_set_kernel(h, ctypes.byref(opts("tiled"))) == -1        # no tile table prepared
+        assert L.gbsp_set_kernel(h, ctypes.byref(opts("vector", 16, 2))) == 0
+        assert L.gbsp_set_kernel(h, ctypes.byref(opts("runs"))) == 0
+        assert get() == (3, 4, 4)
+        assert L.gbsp_set_kernel(h, ctypes.byref(opts("runs", 8))) == 0
+        assert get() == (3, 8, 8)
+        bad = _lib.KernelOpts(4, 0, 0, 0, 0, 0)                                 # no such kernel
+        assert L.gbsp_set_kernel(h, ctypes.byref(bad)) == -1
+    finally:
+        assert L.gbsp_destroy(h) == 0
+
+
 def test_oracle_shares_no_code_with_the_library():
     """The oracle is independent: no include, import or link either way."""
     csrc = os.path.join(ROOT, "paper_0910_4836_gb300")
