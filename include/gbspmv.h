@@ -123,8 +123,10 @@ typedef enum { GBSP_ACC_PLAIN = 0, GBSP_ACC_COMPENSATED = 1 } gbsp_accum;
  * `rows_per_warp` consecutive rows, but it strides through their entries as
  * one contiguous run (CRS stores consecutive rows back to back), so a group
  * issues one FMA slot per entry of the run instead of one per entry of its
- * longest row; lanes in {1, 2, 4, 8}, rows_per_warp in {4, 8} and at least
- * `lanes`.  AUTO picks from the row-length mean. */
+ * longest row; rows longer than 64 entries are cut out of the runs and
+ * summed by the whole warp.  Suits irregular row lengths; lanes in
+ * {1, 2, 4, 8}, rows_per_warp in {4, 8} and at least `lanes`.  AUTO picks
+ * VECTOR from the row-length mean. */
 typedef enum {
     GBSP_KERNEL_AUTO = 0,
     GBSP_KERNEL_VECTOR = 1,
@@ -744,8 +746,9 @@ gbsp_status gbsp_warp_sectors(gbsp_handle A, int32_t lanes, int32_t elem_bytes, 
  * Time the candidate kernels for `A` with k right-hand sides on the device
  * (CUDA events on `stream`, a few repetitions each, X and Y are scratch
  * vectors of the right sizes) and keep the fastest option set on the handle.
- * For CRS handles the candidates are VECTOR with every lanes/rows_per_warp
- * pair and TILED (when prepared); for JDS-family handles the formats sharing
+ * For CRS handles the candidates are VECTOR with lanes 2..32 and every
+ * rows_per_warp, RUNS in six shapes, and TILED (when prepared); for
+ * JDS-family handles the formats sharing
  * the handle's storage and their block/unroll values.  *best receives the
  * choice and *best_ms its time.  Synchronises `stream`. */
 gbsp_status gbsp_autotune(gbsp_handle A, int32_t k, const void *d_X, void *d_Y, void *stream,
