@@ -39,8 +39,8 @@ constexpr int kRunsLongRow = 64;
 // Flagged rows with the whole warp on each row in turn.  Every lane passes
 // its group's mask (bit i: row first + i * step is long; only `leader`
 // lanes' masks are read); lanes stride through a row four loads deep, then
-// a full-warp sum.  Kept out of line so that it does not raise the register
-// count of the common path.
+// a full-warp sum.  Called only from the out-of-line long-row steps below,
+// so it does not weigh on the common path's registers.
 template <int VM>
 __device__ __forceinline__ void crs_warp_long_rows(bool leader, unsigned mask, int64_t first, int64_t step,
                                                 const int32_t *__restrict__ row_ptr,
